@@ -1,0 +1,192 @@
+"""Seeded synthetic series shaped like the paper's labelling workloads.
+
+The paper evaluates on TSSB, a solar-power series and PAMAP (Section 5.1.1);
+none of them ships here, so these generators stand in for them with
+planted-regime series of the same kind (several activities, each a repeated
+pattern, plus noise).  This module holds no MPdist arithmetic: it only draws
+inputs, and both the CUDA path and the CPU oracle consume what it returns.
+
+Every series is float64, little-endian, contiguous; every draw comes from
+``numpy.random.default_rng(seed)`` (PCG64), so the same seed gives the same
+bytes on every machine.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# regime shapes: amplitude about 1, phase restarting at the regime start
+# ----------------------------------------------------------------------------
+
+
+def _sine(length: int, period: float) -> np.ndarray:
+    i = np.arange(length, dtype=np.float64)
+    return np.sin(2.0 * np.pi * i / period)
+
+
+def _square(length: int, period: int) -> np.ndarray:
+    # +1 on the first half-period, -1 on the second
+    i = np.arange(length)
+    return np.where((i % period) < (period // 2), 1.0, -1.0)
+
+
+def _sawtooth(length: int, period: int) -> np.ndarray:
+    i = np.arange(length)
+    return 2.0 * (i % period) / period - 1.0
+
+
+def _bumps(length: int, spacing: int, width: float = 5.0) -> np.ndarray:
+    # Gaussian bumps centred at spacing/2 + q*spacing
+    i = np.arange(length, dtype=np.float64)
+    out = np.zeros(length)
+    c = spacing / 2.0
+    while c < length + 4 * width:
+        out += np.exp(-0.5 * ((i - c) / width) ** 2)
+        c += spacing
+    return out
+
+
+def _chirp(length: int, f0: float = 1.0 / 80, f1: float = 1.0 / 20) -> np.ndarray:
+    # instantaneous frequency rises linearly from f0 to f1 over the regime
+    i = np.arange(length, dtype=np.float64)
+    f = f0 + (f1 - f0) * i / max(length - 1, 1)
+    phase = 2.0 * np.pi * np.cumsum(f)
+    return np.sin(phase - phase[0])
+
+
+def _ar1(length: int, rng: np.random.Generator, phi: float = 0.9) -> np.ndarray:
+    # unit-variance AR(1): innovations N(0, 1 - phi^2)
+    e = rng.normal(0.0, np.sqrt(1.0 - phi * phi), size=length)
+    out = np.empty(length)
+    acc = rng.normal()
+    for t in range(length):
+        acc = phi * acc + e[t]
+        out[t] = acc
+    return out
+
+
+REGIME_TYPES = ("sine", "square", "sawtooth", "bump", "chirp", "ar1")
+
+
+def _regime(kind: str, length: int, period: float, rng: np.random.Generator) -> np.ndarray:
+    if kind == "sine":
+        return _sine(length, period)
+    if kind == "square":
+        return _square(length, int(round(period)))
+    if kind == "sawtooth":
+        return _sawtooth(length, int(round(period)))
+    if kind == "bump":
+        return _bumps(length, int(round(period)))
+    if kind == "chirp":
+        return _chirp(length)
+    if kind == "ar1":
+        return _ar1(length, rng)
+    raise ValueError(kind)
+
+
+@dataclasses.dataclass
+class Series:
+    """A synthetic series with its planted ground truth."""
+
+    T: np.ndarray                 # float64 values
+    bounds: list                  # [(start, stop, kind)] of each planted regime
+    name: str
+
+    def regime_of(self, i: int) -> int:
+        for q, (a, b, _) in enumerate(self.bounds):
+            if a <= i < b:
+                return q
+        return len(self.bounds) - 1
+
+
+def _assemble(kinds, lengths, periods, rng, noise_sd, name):
+    parts, bounds, start = [], [], 0
+    for kind, ln, per in zip(kinds, lengths, periods):
+        parts.append(_regime(kind, int(ln), per, rng))
+        bounds.append((start, start + int(ln), kind))
+        start += int(ln)
+    T = np.concatenate(parts)
+    if noise_sd > 0:
+        T = T + rng.normal(0.0, noise_sd, size=T.shape[0])
+    return Series(np.ascontiguousarray(T, dtype=np.float64), bounds, name)
+
+
+# ----------------------------------------------------------------------------
+# the workload recipes (sizes, seeds and parameters are the documented ones)
+# ----------------------------------------------------------------------------
+
+
+def four_regimes(seed: int = 0, per_regime: int = 1024, noise_sd: float = 0.1) -> Series:
+    """n = 4 x 1024: sine (period 50), square (64), sawtooth (40), bumps every 80,
+    in that order, plus N(0, 0.1^2) noise."""
+    rng = np.random.default_rng(seed)
+    kinds = ("sine", "square", "sawtooth", "bump")
+    periods = (50, 64, 40, 80)
+    return _assemble(kinds, [per_regime] * 4, periods, rng, noise_sd, "four_regimes_n4096")
+
+
+def six_regime_sweep(seed: int = 1, n: int = 100_000, min_len: int = 5000,
+                     noise_sd: float = 0.05) -> Series:
+    """n = 100,000: six regimes (sine, square, sawtooth, bump, chirp, AR(1) phi=0.9)
+    in random order, lengths min_len + Dirichlet(1,...,1)*(n - 6*min_len),
+    plus N(0, 0.05^2) noise."""
+    rng = np.random.default_rng(seed)
+    kinds = list(REGIME_TYPES)
+    order = rng.permutation(len(kinds))
+    kinds = [kinds[q] for q in order]
+    w = rng.dirichlet(np.ones(len(kinds)))
+    free = n - len(kinds) * min_len
+    lengths = (min_len + np.floor(w * free)).astype(np.int64)
+    lengths[-1] = n - lengths[:-1].sum()
+    base_period = {"sine": 50, "square": 64, "sawtooth": 40, "bump": 80, "chirp": 0, "ar1": 0}
+    periods = [base_period[k] for k in kinds]
+    return _assemble(kinds, lengths, periods, rng, noise_sd, "six_regime_sweep_n100000")
+
+
+def large_drift(seed: int = 2, n: int = 1_000_000, n_regimes: int = 8,
+                drift_sd: float = 0.01) -> Series:
+    """n = 1,000,000: 8 regimes with lengths U[50k, 250k] rescaled to sum n, kinds
+    drawn from the six-regime set, periodic kinds with period U[30, 120];
+    plus a random-walk drift cumsum(N(0, 0.01^2)) and no white noise."""
+    rng = np.random.default_rng(seed)
+    raw = rng.uniform(50_000, 250_000, size=n_regimes)
+    lengths = np.floor(raw / raw.sum() * n).astype(np.int64)
+    lengths[-1] = n - lengths[:-1].sum()
+    kinds = [REGIME_TYPES[q] for q in rng.integers(0, len(REGIME_TYPES), size=n_regimes)]
+    periods = rng.uniform(30, 120, size=n_regimes)
+    s = _assemble(kinds, lengths, periods, rng, 0.0, "large_drift_n1000000")
+    s.T = np.ascontiguousarray(s.T + np.cumsum(rng.normal(0.0, drift_sd, size=n)))
+    return s
+
+
+def random_planted(rng: np.random.Generator, n: int, n_regimes: int, noise_sd: float = 0.05,
+                   name: str = "planted") -> Series:
+    """A series of length n from n_regimes random kinds with random periods in
+    [30, 120] and random lengths (each at least n / (4 n_regimes))."""
+    kinds = [REGIME_TYPES[q] for q in rng.integers(0, len(REGIME_TYPES), size=n_regimes)]
+    w = rng.dirichlet(np.ones(n_regimes))
+    min_len = n // (4 * n_regimes)
+    lengths = (min_len + np.floor(w * (n - n_regimes * min_len))).astype(np.int64)
+    lengths[-1] = n - lengths[:-1].sum()
+    periods = rng.uniform(30, 120, size=n_regimes)
+    return _assemble(kinds, lengths, periods, rng, noise_sd, name)
+
+
+def sweep_lengths(lo: int = 64, hi: int = 512, step: int = 32) -> list:
+    """The snippet lengths m of the six-regime sweep: 64, 96, ..., 512."""
+    return list(range(lo, hi + 1, step))
+
+
+def default_ell(m: int) -> int:
+    """Inner subsequence length used by every workload here: ell = m / 2."""
+    return m // 2
+
+
+def default_k(m: int) -> int:
+    """MPdist rank: ceil(0.05 * 2m) in integer arithmetic, i.e. (m + 9) // 10."""
+    return (m + 9) // 10
+
+
+def white_noise(seed: int, n: int, sd: float = 1.0) -> np.ndarray:
+    return np.random.default_rng(seed).normal(0.0, sd, size=n)
