@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the MPdist-profile engine on the six-regime length sweep.
+
+Workload (one "step" = the whole hot path once): a seeded six-regime series of
+n = 100,000 points, snippet lengths m = 64, 96, ..., 512 (15 lengths), ell = m/2,
+k = ceil(0.05 * 2m), K = 4 snippets: window statistics per ell, the profile set
+D of every length, greedy snippets, neighbour shares and the length criterion,
+ending in m_best -- one ``pastila_select_length`` call through the C ABI.
+
+Metric: MPdist profile cells per second, a cell being one D_s(p) (sum over the
+sweep of floor(n/m) * (n - m + 1) per step).  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the paper's definitions, PSF
+steps) on a bounded sample of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+import synth  # noqa: E402
+
+METRIC = "MPdist profile cells/s"
+UNIT = "cells/s"
+K_SNIPPETS = 4
+SM_COUNT_B300 = 148
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2032.0
+# algorithmic FP32 FLOPs per ED cell (eq. 9 matrix entry): 2 FMA of the covariance
+# recurrence (4 FLOP), 2 multiplications by the inverse norms (2 FLOP), and the
+# exact seed of every diagonal (ell FMA per R cells, about 2 FLOP at ell = m/2)
+FLOP_PER_ED_CELL = 8.0
+
+
+def workload():
+    return synth.six_regime_sweep(), synth.sweep_lengths()
+
+
+def cells(n, ms):
+    prof = sum((n // m) * (n - m + 1) for m in ms)
+    ed = sum((n // m) * (m - m // 2 + 1) * (n - m // 2 + 1) for m in ms)
+    return prof, ed
+
+
+def config_dict(n, ms):
+    return {"workload": "six-regime sweep, n=100000, m=64..512 step 32, ell=m/2, k=ceil(0.1m), K=4",
+            "n": n, "m_list": ms, "K": K_SNIPPETS, "l2": "flushed (256 MiB write) between timed steps",
+            "parallelism": "replicas"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = ""
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(T, ms, block: int, seed: int, cores: int):
+    """Oracle (PSF steps, FP64) on a bounded sample: for every m of the sweep,
+    ceil(cores * 64 / m) seeded segments over one seeded block of `block`
+    positions.  Returns (profile cells, seconds, description)."""
+    import oracle
+    oracle.set_threads(cores)
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    n = T.shape[0]
+    tot_cells, tot_s = 0, 0.0
+    for m in ms:
+        S, P = n // m, n - m + 1
+        nseg = min(S, -(-cores * 64 // m))
+        segs = rng.choice(S, nseg, replace=False)
+        p_lo = int(rng.integers(0, P - block))
+        t0 = time.perf_counter()
+        oracle.profiles_range(T, m, m // 2, (m + 9) // 10, segs, p_lo, p_lo + block)
+        tot_s += time.perf_counter() - t0
+        tot_cells += nseg * block
+    desc = (f"every m of the sweep: ceil({cores}*64/m) seeded segments x {block} consecutive positions "
+            f"({tot_cells} profile cells), PSF steps in FP64, OpenMP over segments")
+    return tot_cells, tot_s, desc
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    s, ms = workload()
+    cores = os.cpu_count() or 1
+    block = 512
+    for w in range(args.warmup):
+        oracle_sample(s.T, ms, block, 1000 + w, cores)
+    times, tot_cells, desc = [], 0, ""
+    for st in range(args.steps):
+        c, sec, desc = oracle_sample(s.T, ms, block, 2000 + st, cores)
+        times.append(sec)
+        tot_cells += c
+    value = tot_cells / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(s.T.shape[0], ms),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+    from paper_2401_13680_b300 import pastila
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    s, ms = workload()
+    T = s.T
+    n = T.shape[0]
+    prof_cells, ed_cells = cells(n, ms)
+
+    # CPU baseline first (rank 0, N = 1 only), before the GPU is busy
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        c, sec, desc = oracle_sample(T, ms, 2048, 7, cores)
+        cpu = {"value": c / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": sec}
+
+    stream = torch.cuda.Stream(device=dev)
+    T_dev = torch.from_numpy(T).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    torch.cuda.synchronize()
+    h = pastila.Series(None, device=local, precision=pastila.FP32, device_ptr=T_dev.data_ptr(), n=n,
+                       stream=stream.cuda_stream)
+
+    def step():
+        h.reload_device(T_dev.data_ptr())
+        return h.select_length(ms, K_SNIPPETS)
+
+    warm = max(3, args.warmup)
+    for _ in range(warm):
+        result = step()
+
+    # ---- timed region: device time of each step, L2 flushed in between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    h.set_timing(True)
+    l0 = h.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                starts[i].record(stream)
+            result = step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    launches = h.kernel_launches() - l0
+    tile_ms, tile_launches, tile_cells_halo = h.tile_time()
+    h.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    tot_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([tot_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    value = world * prof_cells * args.steps / tot_s
+    clocks = clk.summary()
+
+    # ---- end to end through the C ABI: host series in, host results out
+    T_host = torch.from_numpy(T).pin_memory().numpy()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h.reload(T_host)
+        h.select_length(ms, K_SNIPPETS)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    d2h = 4 + 8 * len(ms) + len(ms) * K_SNIPPETS * 24
+    e2e = {"value": world * prof_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
+
+    # ---- roofline of the dominant kernel (profile tiles), from its own events
+    ed_alg_per_launch = ed_cells / len(ms)
+    tile_avg_s = (tile_ms / 1e3) / max(tile_launches, 1)
+    achieved = FLOP_PER_ED_CELL * ed_alg_per_launch / tile_avg_s / 1e12
+    peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "profile_tiles_kernel<float,8>",
+                "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (max SM clock), derived",
+                "ed_cells_per_s": ed_alg_per_launch / tile_avg_s,
+                "tile_share_of_step": (tile_ms / 1e3) / tot_s if world == 1 else None,
+                "halo_factor": tile_cells_halo / (ed_alg_per_launch * max(tile_launches, 1))}
+
+    # ---- the plain FP64 one-job GPU path on the same workload (one step)
+    fp64 = None
+    if not args.no_fp64:
+        h64 = pastila.Series(None, device=local, precision=pastila.FP64, device_ptr=T_dev.data_ptr(), n=n,
+                             stream=stream.cuda_stream)
+        h64.reload_device(T_dev.data_ptr())
+        h64.select_length(ms, K_SNIPPETS)  # warm-up: allocations
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(-1.0)
+            e0.record(stream)
+        h64.reload_device(T_dev.data_ptr())
+        r64 = h64.select_length(ms, K_SNIPPETS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64 = {"value": prof_cells / t64, "unit": UNIT, "ms_per_step": 1e3 * t64, "m_best": r64[0],
+                "speedup_fp32_over_fp64": (prof_cells / (tot_s / args.steps)) / (prof_cells / t64)}
+        h64.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": warm, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(n, ms), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps, "roofline": roofline,
+            "ed_cells_per_s": world * ed_cells * args.steps / tot_s,
+            "m_best": result[0], "criterion": [float(x) for x in result[1]],
+            "step_ms": step_ms, "fp64_path": fp64}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    h.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

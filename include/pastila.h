@@ -1,0 +1,177 @@
+/*
+ * pastila.h -- C ABI of the single-GPU MPdist-profile / snippet / length-selection
+ * library (PaSTiLa, arXiv 2401.13680, Sections 3.2 and 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Indices are 0-based.  For a series T of n values and a snippet length m:
+ *      segments   S_s = T[s*m .. s*m+m),  s = 0 .. S-1,  S = floor(n / m)   (eq. 4)
+ *      positions  p = 0 .. P-1,  P = n - m + 1                            (eq. 14)
+ *      ell        inner subsequence length, 2 <= ell <= m                 (eq. 9)
+ *      R          = m - ell + 1 ell-subsequences per length-m window
+ *      k          MPdist rank, k >= 1 (eq. 13)
+ *  - D_s(p) = MPdist(S_s, T[p .. p+m)) (eqs. 14-15): the k-th smallest (1-based)
+ *    of the 2R values of P_ABBA, or their largest when 2R <= k (eq. 13).
+ *    P_ABBA joins, for the R x R block of z-normalised ell-subsequence distances
+ *    between S_s and T[p .. p+m), its R row minima (eq. 11, window of R columns)
+ *    and its R column minima (eq. 10).
+ *  - Flat ell-windows (centred sum of squares <= 1e-24 * ell * max(1, mean^2)) have
+ *    no z-normalisation: two flat windows are at distance 0, a flat and a
+ *    non-flat window at sqrt(2 ell).  (The paper is silent; this is the library's
+ *    reading.)
+ *  - Every call returns a pastila_status and validates its arguments before any
+ *    device work; on error nothing is written to the outputs and
+ *    pastila_last_error() describes the failure.  No C++ exception crosses the ABI.
+ *  - The library owns every handle and all device memory it allocates.  The
+ *    caller owns every output buffer; "host" buffers are ordinary (pageable or
+ *    pinned) host memory, "device" buffers are device pointers on the handle's
+ *    device.  Calls on one handle are not thread-safe; separate handles are.
+ *  - Results are deterministic: the same inputs give bit-identical outputs on
+ *    the same device, alone or batched with other work.
+ */
+#ifndef PASTILA_H_
+#define PASTILA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pastila_series pastila_series; /* opaque: resident series + cached statistics */
+
+typedef enum {
+    PASTILA_OK = 0,
+    PASTILA_EINVAL = 1,     /* an argument is out of range (message says which)          */
+    PASTILA_ENOMEM = 2,     /* the work does not fit the memory budget or device memory  */
+    PASTILA_ECUDA = 3,      /* a CUDA runtime call failed (message carries its string)   */
+    PASTILA_ETIMEOUT = 4,   /* a bounded device-side wait ran out                        */
+    PASTILA_ECANCELLED = 5, /* the job was cancelled before it finished                   */
+    PASTILA_EBUSY = 6       /* the engine queue is full                                   */
+} pastila_status;
+
+typedef enum {
+    PASTILA_FP32 = 0, /* FP32 covariance recurrence, exact FP32 seed per segment row 0 */
+    PASTILA_FP64 = 1  /* the same algorithm in FP64 throughout (plain comparator path)  */
+} pastila_precision;
+
+/* MPdist parameters of one snippet length m.  ell = 0 selects m / 2 and k = 0
+ * selects ceil(0.05 * 2m) = (m + 9) / 10, the paper's "5 % of 2m" (Section 4.1). */
+typedef struct {
+    int32_t ell;
+    int32_t k;
+} pastila_mparams;
+
+/* One snippet (eqs. 5-8): index is the segment number C.index; frac is the share
+ * of positions whose nearest snippet it is (eq. 7); area_after is ProfileArea
+ * (eq. 17) right after the greedy step that chose it; rank is that step (0-based). */
+typedef struct {
+    int32_t index;
+    int32_t rank;
+    double frac;
+    double area_after;
+} pastila_snippet;
+
+/* ---------------------------------------------------------------- handle ---- */
+
+/* Copies the n FP64 values of a host series T to device `device` and computes
+ * nothing yet (window statistics are computed per ell on first use).
+ * mem_budget_bytes bounds the device memory the handle may hold (0: no bound
+ * beyond what the device has).  Errors: EINVAL (NULL out/T, n < 4, a non-finite
+ * value, bad device or precision), ENOMEM, ECUDA. */
+pastila_status pastila_create(pastila_series** out, const double* T, int64_t n, int device,
+                              size_t mem_budget_bytes, pastila_precision prec);
+
+/* As pastila_create, but T_dev is a device pointer (n FP64 values on `device`)
+ * that the handle copies on `stream` (a cudaStream_t; NULL = a stream the handle
+ * creates); the handle then issues all its work on that stream. */
+pastila_status pastila_create_device(pastila_series** out, const double* T_dev, int64_t n,
+                                     int device, size_t mem_budget_bytes,
+                                     pastila_precision prec, void* stream);
+
+/* Replaces the n resident values with new ones (same n) and marks every cached
+ * ell-window statistic stale, so the next call recomputes it: for series that
+ * are updated in place.  T: n host doubles; T_dev: n device doubles on the
+ * handle's device, copied on the handle's stream.  Errors: EINVAL, ECUDA. */
+pastila_status pastila_reload(pastila_series* h, const double* T);
+pastila_status pastila_reload_device(pastila_series* h, const double* T_dev);
+
+/* Frees the handle and every device buffer it owns (waits for its stream). */
+void pastila_destroy(pastila_series* h);
+
+/* Message of the last failed call on this thread ("" if none).  The pointer stays
+ * valid until the next call on this thread. */
+const char* pastila_last_error(void);
+
+/* ----------------------------------------------------- profiles (eq. 15) ---- */
+
+/* The profile set D = (D_0 .. D_{S-1}) for one m (eqs. 9-15) and its largest
+ * value max_{s,p} D_s(p) (the denominator of eq. 18).
+ * D_out: NULL, or a host buffer of S * P elements, row-major (segment-major),
+ *        float for PASTILA_FP32 handles and double for PASTILA_FP64 handles.
+ * D_max_out: NULL or one double.
+ * Errors: EINVAL (m < 4 or m > n, ell or k out of range), ENOMEM, ECUDA. */
+pastila_status pastila_profiles(pastila_series* h, int32_t m, pastila_mparams mp, void* D_out,
+                                double* D_max_out);
+
+/* As pastila_profiles with a device output buffer (same layout and element
+ * type), written on the handle's stream; returns once the work is enqueued.
+ * D_max_dev: NULL or a device double written on the same stream. */
+pastila_status pastila_profiles_device(pastila_series* h, int32_t m, pastila_mparams mp,
+                                       void* D_dev, double* D_max_dev);
+
+/* --------------------------------------------- snippets (eqs. 5-8, 16-17) ---- */
+
+/* The K snippets of length m: greedy minimisation of ProfileArea (eqs. 16-17;
+ * M starts at +inf, each step picks the unchosen segment minimising
+ * sum_p min(M_p, D_s(p)), lowest index on ties, sums in FP64), then nearest-
+ * snippet labels (eq. 6, argmin over the K chosen profiles, lowest segment index
+ * on ties), frac (eq. 7) and the eq. 8 order (frac descending, then index).
+ * out: K records in eq. 8 order (host).
+ * labels_out: NULL or P int32 (host): the nearest snippet's segment index per position.
+ * snippet_profiles_out: NULL or K * P elements (host, float or double per
+ *   precision): the chosen profiles in greedy order.
+ * Errors: EINVAL (K < 1 or K > min(S, 64), bad m/ell/k), ENOMEM, ECUDA. */
+pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp, int32_t K,
+                                pastila_snippet* out, int32_t* labels_out,
+                                void* snippet_profiles_out);
+
+/* --------------------------------------------- length selection (eq. 18) ---- */
+
+/* PaSTiLa's length criterion over a sweep (Section 4.2, eq. 18): for every m in
+ * m_list, the greedy K snippets and
+ *     crit(m) = sum over ordered pairs p != q of sum_i |D_{c_p}(i) - D_{c_q}(i)|
+ *               / max_{s,i} D_s(i)      (0 when that maximum is 0),
+ * then m_best = argmax crit (smallest m on ties).  rule gives ell and k per m
+ * (0 fields = the defaults m / 2 and (m + 9) / 10; a non-zero ell is used for
+ * every m and must be <= min m).
+ * m_best: one int32 (host).  crit_out: NULL or n_m doubles (host, m_list order).
+ * best_out: NULL or K snippets of length m_best in eq. 8 order (host).
+ * Errors: EINVAL (n_m < 1, a bad m, K < 2 or K > min(floor(n / max m), 64)),
+ * ENOMEM, ECUDA. */
+pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, int32_t n_m,
+                                     pastila_mparams rule, int32_t K, int32_t* m_best,
+                                     double* crit_out, pastila_snippet* best_out);
+
+/* ------------------------------------------------------------- tracing ---- */
+
+/* Kernel launches the handle has issued since it was created. */
+uint64_t pastila_kernel_launches(const pastila_series* h);
+
+/* Turns per-launch timing of the profile tile kernel on (1) or off (0).  While
+ * on, every launch is bracketed by CUDA events on the handle's stream; the
+ * accumulated device time is read (after the stream is idle) with
+ * pastila_tile_time.  Errors: EINVAL, ECUDA. */
+pastila_status pastila_set_timing(pastila_series* h, int on);
+
+/* Total device milliseconds and number of timed launches of the profile tile
+ * kernel since timing was turned on, and the ED cells (entries of the eq. 9
+ * matrix, the halo columns of each tile included) those launches computed.
+ * Waits for the handle's stream.  Any output may be NULL. */
+pastila_status pastila_tile_time(pastila_series* h, double* ms, int64_t* launches, double* ed_cells);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PASTILA_H_ */

@@ -50,6 +50,9 @@ def _load():
                                           ctypes.c_int, _i32p, _i64p, ctypes.c_int64, _f64p]
         lib.ora_profiles_psf.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, _i32p, ctypes.c_int, _f64p]
+        lib.ora_profiles_psf_range.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, _i32p, ctypes.c_int, ctypes.c_int64,
+                                               ctypes.c_int64, _f64p]
         lib.ora_greedy.argtypes = [_f64p, ctypes.c_int, ctypes.c_int64, ctypes.c_int, _i32p, _f64p]
         lib.ora_neighbors.argtypes = [_f64p, ctypes.c_int64, _i32p, ctypes.c_int, _i32p, _f64p,
                                       _i32p]
@@ -120,6 +123,16 @@ def profiles(T, m, ell, k, segs=None):
     D = np.empty((segs.shape[0], P))
     _load().ora_profiles_psf(_p64(T), n, m, ell, k, segs.ctypes.data_as(_i32p), segs.shape[0],
                              _p64(D))
+    return D
+
+
+def profiles_range(T, m, ell, k, segs, p_lo, p_hi):
+    """Profiles of the listed segments at positions p_lo .. p_hi-1 (PSF steps)."""
+    T = _f64(T)
+    segs = _i32(segs)
+    D = np.empty((segs.shape[0], p_hi - p_lo))
+    _load().ora_profiles_psf_range(_p64(T), T.shape[0], m, ell, k, segs.ctypes.data_as(_i32p),
+                                   segs.shape[0], p_lo, p_hi, _p64(D))
     return D
 
 

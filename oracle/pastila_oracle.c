@@ -128,48 +128,56 @@ void ora_profile_cells(const double* T, int64_t n, int m, int ell, int k,
         out[q] = ora_mpdist_pair(T + (int64_t)segs[q] * m, T + pos[q], m, ell, k);
 }
 
-/* Full profiles D_s for the listed segments, following the PSF steps of
- * Section 4.1 in order:
- *   eq. 9   ED_matr(r, j) = ED_norm(seg_{r,ell}, T_{j,ell}), r < R, j < C
+/* Profiles D_s(p) for the listed segments and the positions p_lo .. p_hi-1,
+ * following the PSF steps of Section 4.1 in order (only the columns those
+ * positions need, j = p_lo .. p_hi-1+m-ell):
+ *   eq. 9   ED_matr(r, j) = ED_norm(seg_{r,ell}, T_{j,ell}), r < R
  *   eq. 10  allP_BA(j)    = min_r ED_matr(r, j)
  *   eq. 11  allP_AB(r, p) = min_{p <= c <= p+m-ell} ED_matr(r, c)
  *   eq. 12  P_ABBA(p)     = {allP_AB(r, p)}_r  ++  {allP_BA(j)}_{p <= j <= p+m-ell}
  *   eq. 13  D_s(p)        = k-th smallest of P_ABBA(p), or its max if |P_ABBA| <= k
- * Output D is nsegs x P row-major. */
-void ora_profiles_psf(const double* T, int64_t n, int m, int ell, int k,
-                      const int32_t* segs, int nsegs, double* D) {
+ * Output D is nsegs x (p_hi - p_lo) row-major. */
+void ora_profiles_psf_range(const double* T, int64_t n, int m, int ell, int k,
+                            const int32_t* segs, int nsegs, int64_t p_lo, int64_t p_hi, double* D) {
+    (void)n;
     int R = m - ell + 1;
-    int64_t C = n - ell + 1, P = n - m + 1;
+    int64_t np = p_hi - p_lo, nc = np + R - 1;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < nsegs; ++q) {
         const double* seg = T + (int64_t)segs[q] * m;
-        double* ED = (double*)malloc(sizeof(double) * (size_t)R * (size_t)C);
-        double* pBA = (double*)malloc(sizeof(double) * (size_t)C);
-        double* pAB = (double*)malloc(sizeof(double) * (size_t)R * (size_t)P);
+        double* ED = (double*)malloc(sizeof(double) * (size_t)R * (size_t)nc);
+        double* pBA = (double*)malloc(sizeof(double) * (size_t)nc);
+        double* pAB = (double*)malloc(sizeof(double) * (size_t)R * (size_t)np);
         double* pabba = (double*)malloc(sizeof(double) * 2 * (size_t)R);
         for (int r = 0; r < R; ++r)
-            for (int64_t j = 0; j < C; ++j) ED[(size_t)r * C + j] = ora_zdist(seg + r, T + j, ell);
-        for (int64_t j = 0; j < C; ++j) {
+            for (int64_t c = 0; c < nc; ++c) ED[(size_t)r * nc + c] = ora_zdist(seg + r, T + p_lo + c, ell);
+        for (int64_t c = 0; c < nc; ++c) {
             double best = INFINITY;
-            for (int r = 0; r < R; ++r) best = fmin(best, ED[(size_t)r * C + j]);
-            pBA[j] = best;
+            for (int r = 0; r < R; ++r) best = fmin(best, ED[(size_t)r * nc + c]);
+            pBA[c] = best;
         }
         for (int r = 0; r < R; ++r)
-            for (int64_t p = 0; p < P; ++p) {
+            for (int64_t p = 0; p < np; ++p) {
                 double best = INFINITY;
-                for (int c = 0; c < R; ++c) best = fmin(best, ED[(size_t)r * C + p + c]);
-                pAB[(size_t)r * P + p] = best;
+                for (int c = 0; c < R; ++c) best = fmin(best, ED[(size_t)r * nc + p + c]);
+                pAB[(size_t)r * np + p] = best;
             }
-        for (int64_t p = 0; p < P; ++p) {
-            for (int r = 0; r < R; ++r) pabba[r] = pAB[(size_t)r * P + p];
+        for (int64_t p = 0; p < np; ++p) {
+            for (int r = 0; r < R; ++r) pabba[r] = pAB[(size_t)r * np + p];
             for (int c = 0; c < R; ++c) pabba[R + c] = pBA[p + c];
-            D[(size_t)q * P + p] = ora_select(pabba, 2 * R, k);
+            D[(size_t)q * np + p] = ora_select(pabba, 2 * R, k);
         }
         free(ED);
         free(pBA);
         free(pAB);
         free(pabba);
     }
+}
+
+/* Full profiles of the listed segments: all P = n - m + 1 positions. */
+void ora_profiles_psf(const double* T, int64_t n, int m, int ell, int k,
+                      const int32_t* segs, int nsegs, double* D) {
+    ora_profiles_psf_range(T, n, m, ell, k, segs, nsegs, 0, n - m + 1, D);
 }
 
 /* Greedy snippet search on ProfileArea (eqs. 16-17).  M starts at +inf; step t

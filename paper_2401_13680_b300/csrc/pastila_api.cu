@@ -1,0 +1,638 @@
+// C-ABI implementation (include/pastila.h): handles, device memory, launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pastila.h"
+#include "keys.cuh"
+#include "snippets.cuh"
+#include "stats.cuh"
+#include "tile.cuh"
+
+using namespace pastila;
+
+namespace {
+
+thread_local std::string g_err;
+
+pastila_status fail(pastila_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(PASTILA_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+#define TRY(...)                                \
+    do {                                        \
+        pastila_status st_ = (__VA_ARGS__);     \
+        if (st_ != PASTILA_OK) return st_;      \
+    } while (0)
+
+constexpr int V_F32 = 8;
+constexpr int V_F64 = 4;
+constexpr int MAX_NT = 512;
+
+struct Stats {
+    bool stale = false;
+    int64_t C = 0;
+    double* mu = nullptr;
+    void* a = nullptr;
+    void* df = nullptr;
+    void* dg = nullptr;
+};
+
+struct Buf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct pastila_series {
+    int device = 0;
+    pastila_precision prec = PASTILA_FP32;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t n = 0;
+    double* T = nullptr;
+    size_t budget = 0;
+    size_t held = 0;
+    int smem_optin = 0;
+    uint64_t launches = 0;
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<cudaEvent_t> ev_free;
+    double tile_ms = 0.0;
+    int64_t tile_launches = 0;
+    double tile_cells = 0.0;
+    std::map<int, Stats> stats;
+    std::map<std::string, Buf> bufs;
+};
+
+namespace {
+
+size_t real_size(const pastila_series* h) { return h->prec == PASTILA_FP64 ? 8 : 4; }
+
+pastila_status dev_alloc(pastila_series* h, void** p, size_t bytes) {
+    if (h->budget && h->held + bytes > h->budget)
+        return fail(PASTILA_ENOMEM, "memory budget exceeded: need %zu more bytes, hold %zu of %zu",
+                    bytes, h->held, h->budget);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(PASTILA_ENOMEM, "cudaMalloc(%zu) failed: out of device memory", bytes);
+    }
+    if (e != cudaSuccess) return fail(PASTILA_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    h->held += bytes;
+    return PASTILA_OK;
+}
+
+void dev_free(pastila_series* h, void* p, size_t bytes) {
+    if (p) {
+        cudaFree(p);
+        h->held -= bytes;
+    }
+}
+
+// Named scratch buffer that only grows.
+pastila_status scratch(pastila_series* h, const char* name, size_t bytes, void** out) {
+    Buf& b = h->bufs[name];
+    if (b.n < bytes) {
+        CK(cudaStreamSynchronize(h->stream));
+        dev_free(h, b.p, b.n);
+        b.p = nullptr;
+        b.n = 0;
+        TRY(dev_alloc(h, &b.p, bytes));
+        b.n = bytes;
+    }
+    *out = b.p;
+    return PASTILA_OK;
+}
+
+pastila_status set_device(const pastila_series* h) {
+    CK(cudaSetDevice(h->device));
+    return PASTILA_OK;
+}
+
+void invalidate_stats(pastila_series* h) {
+    for (auto& kv : h->stats) kv.second.stale = true;
+}
+
+pastila_status ensure_stats(pastila_series* h, int ell, Stats** out) {
+    auto it = h->stats.find(ell);
+    if (it != h->stats.end() && !it->second.stale) {
+        *out = &it->second;
+        return PASTILA_OK;
+    }
+    Stats st;
+    st.C = h->n - ell + 1;
+    const size_t rs = real_size(h);
+    void *mu, *inv, *flat, *a, *df, *dg;
+    if (it != h->stats.end()) {  // stale: recompute into the same buffers
+        mu = it->second.mu;
+        a = it->second.a;
+        df = it->second.df;
+        dg = it->second.dg;
+    } else {
+        TRY(dev_alloc(h, &mu, 8 * st.C));
+        TRY(dev_alloc(h, &a, rs * st.C));
+        TRY(dev_alloc(h, &df, rs * st.C));
+        TRY(dev_alloc(h, &dg, rs * st.C));
+    }
+    TRY(scratch(h, "stats_inv", 8 * st.C, &inv));
+    TRY(scratch(h, "stats_flat", 4 * st.C, &flat));
+    const int64_t nthr = (st.C + STATS_RUN - 1) / STATS_RUN;
+    stats_mu_a_kernel<<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
+        h->T, st.C, ell, (double*)mu, (double*)inv, (int32_t*)flat);
+    CK(cudaGetLastError());
+    const unsigned nb = (unsigned)((st.C + 255) / 256);
+    if (h->prec == PASTILA_FP64)
+        stats_terms_kernel<double><<<nb, 256, 0, h->stream>>>(h->T, st.C, ell, (double*)mu, (double*)inv,
+                                                              (double*)a, (double*)df, (double*)dg);
+    else
+        stats_terms_kernel<float><<<nb, 256, 0, h->stream>>>(h->T, st.C, ell, (double*)mu, (double*)inv,
+                                                             (float*)a, (float*)df, (float*)dg);
+    CK(cudaGetLastError());
+    h->launches += 2;
+    st.mu = (double*)mu;
+    st.a = a;
+    st.df = df;
+    st.dg = dg;
+    h->stats[ell] = st;
+    *out = &h->stats[ell];
+    return PASTILA_OK;
+}
+
+struct MParams {
+    int m, ell, k, R, S;
+    int64_t P, C;
+};
+
+pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, MParams* o) {
+    if (m < 4) return fail(PASTILA_EINVAL, "m = %d: must be at least 4", m);
+    if ((int64_t)m > h->n) return fail(PASTILA_EINVAL, "m = %d exceeds the series length %lld", m, (long long)h->n);
+    const int ell = mp.ell ? mp.ell : m / 2;
+    const int k = mp.k ? mp.k : (m + 9) / 10;
+    if (ell < 2 || ell > m) return fail(PASTILA_EINVAL, "ell = %d: must satisfy 2 <= ell <= m = %d", ell, m);
+    if (k < 1) return fail(PASTILA_EINVAL, "k = %d: must be at least 1", k);
+    o->m = m;
+    o->ell = ell;
+    o->k = k;
+    o->R = m - ell + 1;
+    o->S = (int)(h->n / m);
+    o->P = h->n - m + 1;
+    o->C = h->n - ell + 1;
+    return PASTILA_OK;
+}
+
+template <typename real, int V>
+pastila_status choose_tile(const pastila_series* h, const MParams& q, TileGeom* g) {
+    const size_t limit = (size_t)h->smem_optin;
+    const int64_t Pmax = ((q.P + 31) / 32) * 32;
+    int best = 0;
+    for (int W = 32; W <= MAX_NT * V; W += 32) {
+        if (W > Pmax) break;
+        TileGeom t = tile_geom<real>(q.m, q.ell, W, V);
+        if (t.NT > MAX_NT || t.bytes > limit) break;
+        best = W;
+    }
+    if (!best)
+        return fail(PASTILA_EINVAL, "m = %d, ell = %d: the tile does not fit in shared memory", q.m, q.ell);
+    *g = tile_geom<real>(q.m, q.ell, best, V);
+    return PASTILA_OK;
+}
+
+pastila_status get_event(pastila_series* h, cudaEvent_t* e) {
+    if (!h->ev_free.empty()) {
+        *e = h->ev_free.back();
+        h->ev_free.pop_back();
+        return PASTILA_OK;
+    }
+    CK(cudaEventCreate(e));
+    return PASTILA_OK;
+}
+
+pastila_status drain_events(pastila_series* h) {
+    for (auto& pr : h->ev_pending) {
+        CK(cudaEventSynchronize(pr.second));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        h->tile_ms += ms;
+        h->ev_free.push_back(pr.first);
+        h->ev_free.push_back(pr.second);
+    }
+    h->ev_pending.clear();
+    return PASTILA_OK;
+}
+
+__global__ void init_dmax_kernel(unsigned long long* k) { *k = KeyOf<double>::enc(0.0); }
+__global__ void dec_dmax_kernel(const unsigned long long* k, double* o) { *o = KeyOf<double>::dec(*k); }
+
+template <typename real, int V>
+pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st, real* D,
+                                 unsigned long long* dmax) {
+    TileGeom g;
+    TRY(choose_tile<real, V>(h, q, &g));
+    ProfileArgs<real> A;
+    A.T = h->T;
+    A.mu = st->mu;
+    A.a = (const real*)st->a;
+    A.df = (const real*)st->df;
+    A.dg = (const real*)st->dg;
+    A.n = h->n;
+    A.C = q.C;
+    A.P = q.P;
+    A.m = q.m;
+    A.ell = q.ell;
+    A.k = q.k;
+    A.R = q.R;
+    A.S = q.S;
+    A.W = g.W;
+    A.ntiles = (int)((q.P + g.W - 1) / g.W);
+    A.D = D;
+    A.dmax_key = dmax;
+    CK(cudaFuncSetAttribute(profile_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)g.bytes));
+    init_dmax_kernel<<<1, 1, 0, h->stream>>>(dmax);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing) {
+        TRY(get_event(h, &e0));
+        TRY(get_event(h, &e1));
+        CK(cudaEventRecord(e0, h->stream));
+    }
+    profile_tiles_kernel<real, V><<<dim3(A.ntiles, q.S), g.NT, g.bytes, h->stream>>>(A, g);
+    CK(cudaGetLastError());
+    h->launches += 2;
+    if (h->timing) {
+        CK(cudaEventRecord(e1, h->stream));
+        h->ev_pending.push_back({e0, e1});
+        h->tile_launches += 1;
+        h->tile_cells += (double)q.S * A.ntiles * (double)q.R * (double)g.Wb;
+    }
+    return PASTILA_OK;
+}
+
+pastila_status launch_profiles(pastila_series* h, const MParams& q, void* D, unsigned long long* dmax) {
+    Stats* st;
+    TRY(ensure_stats(h, q.ell, &st));
+    if (h->prec == PASTILA_FP64) return launch_profiles_t<double, V_F64>(h, q, st, (double*)D, dmax);
+    return launch_profiles_t<float, V_F32>(h, q, st, (float*)D, dmax);
+}
+
+// Greedy (eqs. 16-17) + neighbours (eqs. 6-8) on a resident D.  Results stay on
+// the device in the named scratch buffers "sn_*"; criterion optional.
+template <typename real>
+pastila_status snippets_on_device_t(pastila_series* h, const MParams& q, const real* D, int K,
+                                    int32_t* labels_dev, const unsigned long long* dmax,
+                                    double* crit_dev) {
+    void *area, *M, *chosen, *aafter, *counts, *oi, *orank, *ofrac, *oarea, *part;
+    TRY(scratch(h, "sn_area", 8 * (size_t)q.S, &area));
+    TRY(scratch(h, "sn_M", sizeof(real) * (size_t)q.P, &M));
+    TRY(scratch(h, "sn_chosen", 4 * 64, &chosen));
+    TRY(scratch(h, "sn_aafter", 8 * 64, &aafter));
+    TRY(scratch(h, "sn_counts", 8 * 64, &counts));
+    TRY(scratch(h, "sn_oi", 4 * 64, &oi));
+    TRY(scratch(h, "sn_orank", 4 * 64, &orank));
+    TRY(scratch(h, "sn_ofrac", 8 * 64, &ofrac));
+    TRY(scratch(h, "sn_oarea", 8 * 64, &oarea));
+    const unsigned pb = (unsigned)((q.P + 255) / 256);
+    for (int t = 0; t < K; ++t) {
+        area_kernel<real><<<q.S, AREA_THREADS, 0, h->stream>>>(D, q.S, q.P, t ? (const real*)M : nullptr,
+                                                               (const int32_t*)chosen, t, (double*)area);
+        argmin_area_kernel<<<1, 1024, 0, h->stream>>>((const double*)area, q.S, (int32_t*)chosen,
+                                                      (double*)aafter, t);
+        if (t + 1 < K)
+            update_curve_kernel<real><<<pb, 256, 0, h->stream>>>(D, q.P, (const int32_t*)chosen, t, (real*)M);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(counts, 0, 8 * 64, h->stream));
+    neighbors_kernel<real><<<pb, 256, 0, h->stream>>>(D, q.P, (const int32_t*)chosen, K, labels_dev,
+                                                      (unsigned long long*)counts);
+    finalize_snippets_kernel<<<1, 1, 0, h->stream>>>((const int32_t*)chosen, (const double*)aafter,
+                                                     (const unsigned long long*)counts, K, q.P, (int32_t*)oi,
+                                                     (int32_t*)orank, (double*)ofrac, (double*)oarea);
+    CK(cudaGetLastError());
+    h->launches += 3 * K - 1 + 2;
+    if (crit_dev) {
+        const int nb = 296;
+        TRY(scratch(h, "crit_part", 8 * nb, &part));
+        criterion_partial_kernel<real><<<nb, AREA_THREADS, 0, h->stream>>>(D, q.P, (const int32_t*)chosen, K,
+                                                                          (double*)part);
+        criterion_final_kernel<<<1, 1, 0, h->stream>>>((const double*)part, nb, dmax, crit_dev);
+        CK(cudaGetLastError());
+        h->launches += 2;
+    }
+    return PASTILA_OK;
+}
+
+pastila_status snippets_on_device(pastila_series* h, const MParams& q, const void* D, int K, int32_t* labels_dev,
+                                  const unsigned long long* dmax, double* crit_dev) {
+    if (h->prec == PASTILA_FP64)
+        return snippets_on_device_t<double>(h, q, (const double*)D, K, labels_dev, dmax, crit_dev);
+    return snippets_on_device_t<float>(h, q, (const float*)D, K, labels_dev, dmax, crit_dev);
+}
+
+pastila_status read_snippets(pastila_series* h, int K, pastila_snippet* out) {
+    std::vector<int32_t> oi(K), orank(K);
+    std::vector<double> ofrac(K), oarea(K);
+    CK(cudaMemcpyAsync(oi.data(), h->bufs["sn_oi"].p, 4 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(orank.data(), h->bufs["sn_orank"].p, 4 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(ofrac.data(), h->bufs["sn_ofrac"].p, 8 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(oarea.data(), h->bufs["sn_oarea"].p, 8 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < K; ++i) {
+        out[i].index = oi[i];
+        out[i].rank = orank[i];
+        out[i].frac = ofrac[i];
+        out[i].area_after = oarea[i];
+    }
+    return PASTILA_OK;
+}
+
+pastila_status create_common(pastila_series** out, int64_t n, int device, size_t budget,
+                             pastila_precision prec, cudaStream_t stream, pastila_series** hp) {
+    if (!out) return fail(PASTILA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 4) return fail(PASTILA_EINVAL, "n = %lld: the series needs at least 4 values", (long long)n);
+    if (prec != PASTILA_FP32 && prec != PASTILA_FP64) return fail(PASTILA_EINVAL, "unknown precision %d", (int)prec);
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(PASTILA_EINVAL, "device %d: %d device(s) visible", device, ndev);
+    CK(cudaSetDevice(device));
+    int smem = 0;
+    CK(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    pastila_series* h = new pastila_series();
+    h->device = device;
+    h->prec = prec;
+    h->n = n;
+    h->budget = budget;
+    h->smem_optin = smem - 1024;  // headroom for static shared memory
+    if (stream) {
+        h->stream = stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail(PASTILA_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+    }
+    pastila_status st = dev_alloc(h, (void**)&h->T, 8 * (size_t)n);
+    if (st != PASTILA_OK) {
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return st;
+    }
+    *hp = h;
+    return PASTILA_OK;
+}
+
+pastila_status check_finite(const double* T, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(T[i])) return fail(PASTILA_EINVAL, "T[%lld] is not finite", (long long)i);
+    return PASTILA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pastila_last_error(void) { return g_err.c_str(); }
+
+pastila_status pastila_create(pastila_series** out, const double* T, int64_t n, int device,
+                              size_t mem_budget_bytes, pastila_precision prec) {
+    g_err.clear();
+    if (!T) return fail(PASTILA_EINVAL, "T is NULL");
+    if (!out) return fail(PASTILA_EINVAL, "out is NULL");
+    TRY(check_finite(T, n));
+    pastila_series* h = nullptr;
+    TRY(create_common(out, n, device, mem_budget_bytes, prec, nullptr, &h));
+    cudaError_t e = cudaMemcpyAsync(h->T, T, 8 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        pastila_destroy(h);
+        return fail(PASTILA_ECUDA, "copying T: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return PASTILA_OK;
+}
+
+pastila_status pastila_create_device(pastila_series** out, const double* T_dev, int64_t n, int device,
+                                     size_t mem_budget_bytes, pastila_precision prec, void* stream) {
+    g_err.clear();
+    if (!T_dev) return fail(PASTILA_EINVAL, "T_dev is NULL");
+    pastila_series* h = nullptr;
+    TRY(create_common(out, n, device, mem_budget_bytes, prec, (cudaStream_t)stream, &h));
+    cudaError_t e = cudaMemcpyAsync(h->T, T_dev, 8 * (size_t)n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) {
+        pastila_destroy(h);
+        return fail(PASTILA_ECUDA, "copying T: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return PASTILA_OK;
+}
+
+pastila_status pastila_reload(pastila_series* h, const double* T) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!T) return fail(PASTILA_EINVAL, "T is NULL");
+    TRY(check_finite(T, h->n));
+    TRY(set_device(h));
+    CK(cudaMemcpyAsync(h->T, T, 8 * (size_t)h->n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    invalidate_stats(h);
+    return PASTILA_OK;
+}
+
+pastila_status pastila_reload_device(pastila_series* h, const double* T_dev) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!T_dev) return fail(PASTILA_EINVAL, "T_dev is NULL");
+    TRY(set_device(h));
+    CK(cudaMemcpyAsync(h->T, T_dev, 8 * (size_t)h->n, cudaMemcpyDeviceToDevice, h->stream));
+    invalidate_stats(h);
+    return PASTILA_OK;
+}
+
+void pastila_destroy(pastila_series* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto& pr : h->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto e : h->ev_free) cudaEventDestroy(e);
+    for (auto& kv : h->stats) {
+        cudaFree(kv.second.mu);
+        cudaFree(kv.second.a);
+        cudaFree(kv.second.df);
+        cudaFree(kv.second.dg);
+    }
+    for (auto& kv : h->bufs) cudaFree(kv.second.p);
+    cudaFree(h->T);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+uint64_t pastila_kernel_launches(const pastila_series* h) { return h ? h->launches : 0; }
+
+pastila_status pastila_set_timing(pastila_series* h, int on) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    TRY(set_device(h));
+    TRY(drain_events(h));
+    h->timing = on != 0;
+    h->tile_ms = 0.0;
+    h->tile_launches = 0;
+    h->tile_cells = 0.0;
+    return PASTILA_OK;
+}
+
+pastila_status pastila_tile_time(pastila_series* h, double* ms, int64_t* launches, double* ed_cells) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    TRY(set_device(h));
+    TRY(drain_events(h));
+    if (ms) *ms = h->tile_ms;
+    if (launches) *launches = h->tile_launches;
+    if (ed_cells) *ed_cells = h->tile_cells;
+    return PASTILA_OK;
+}
+
+pastila_status pastila_profiles_device(pastila_series* h, int32_t m, pastila_mparams mp, void* D_dev,
+                                       double* D_max_dev) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!D_dev) return fail(PASTILA_EINVAL, "D_dev is NULL");
+    TRY(set_device(h));
+    MParams q;
+    TRY(resolve(h, m, mp, &q));
+    void* dk;
+    TRY(scratch(h, "dmax", 8, &dk));
+    TRY(launch_profiles(h, q, D_dev, (unsigned long long*)dk));
+    if (D_max_dev) {
+        dec_dmax_kernel<<<1, 1, 0, h->stream>>>((const unsigned long long*)dk, D_max_dev);
+        CK(cudaGetLastError());
+        h->launches += 1;
+    }
+    return PASTILA_OK;
+}
+
+pastila_status pastila_profiles(pastila_series* h, int32_t m, pastila_mparams mp, void* D_out,
+                                double* D_max_out) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    TRY(set_device(h));
+    MParams q;
+    TRY(resolve(h, m, mp, &q));
+    const size_t bytes = real_size(h) * (size_t)q.S * (size_t)q.P;
+    void *D, *dk;
+    TRY(scratch(h, "D", bytes, &D));
+    TRY(scratch(h, "dmax", 8, &dk));
+    TRY(launch_profiles(h, q, D, (unsigned long long*)dk));
+    if (D_out) CK(cudaMemcpyAsync(D_out, D, bytes, cudaMemcpyDeviceToHost, h->stream));
+    unsigned long long key = 0;
+    CK(cudaMemcpyAsync(&key, dk, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (D_max_out) *D_max_out = KeyOf<double>::dec(key);
+    return PASTILA_OK;
+}
+
+pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp, int32_t K,
+                                pastila_snippet* out, int32_t* labels_out, void* snippet_profiles_out) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!out) return fail(PASTILA_EINVAL, "out is NULL");
+    TRY(set_device(h));
+    MParams q;
+    TRY(resolve(h, m, mp, &q));
+    if (K < 1 || K > q.S || K > 64)
+        return fail(PASTILA_EINVAL, "K = %d: must satisfy 1 <= K <= min(n / m, 64) = %d", K, q.S < 64 ? q.S : 64);
+    const size_t rs = real_size(h);
+    const size_t bytes = rs * (size_t)q.S * (size_t)q.P;
+    void *D, *dk, *lab = nullptr;
+    TRY(scratch(h, "D", bytes, &D));
+    TRY(scratch(h, "dmax", 8, &dk));
+    if (labels_out) TRY(scratch(h, "labels", 4 * (size_t)q.P, &lab));
+    TRY(launch_profiles(h, q, D, (unsigned long long*)dk));
+    TRY(snippets_on_device(h, q, D, K, (int32_t*)lab, (const unsigned long long*)dk, nullptr));
+    if (labels_out) CK(cudaMemcpyAsync(labels_out, lab, 4 * (size_t)q.P, cudaMemcpyDeviceToHost, h->stream));
+    if (snippet_profiles_out) {
+        std::vector<int32_t> chosen(K);
+        CK(cudaMemcpyAsync(chosen.data(), h->bufs["sn_chosen"].p, 4 * K, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int t = 0; t < K; ++t)
+            CK(cudaMemcpyAsync((char*)snippet_profiles_out + rs * (size_t)t * q.P,
+                               (const char*)D + rs * (size_t)chosen[t] * q.P, rs * (size_t)q.P,
+                               cudaMemcpyDeviceToHost, h->stream));
+    }
+    TRY(read_snippets(h, K, out));
+    return PASTILA_OK;
+}
+
+pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, int32_t n_m, pastila_mparams rule,
+                                     int32_t K, int32_t* m_best, double* crit_out, pastila_snippet* best_out) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!m_list || n_m < 1) return fail(PASTILA_EINVAL, "m_list is empty");
+    if (!m_best) return fail(PASTILA_EINVAL, "m_best is NULL");
+    TRY(set_device(h));
+    std::vector<MParams> qs(n_m);
+    int min_S = 1 << 30;
+    for (int i = 0; i < n_m; ++i) {
+        TRY(resolve(h, m_list[i], rule, &qs[i]));
+        min_S = qs[i].S < min_S ? qs[i].S : min_S;
+    }
+    if (K < 2 || K > min_S || K > 64)
+        return fail(PASTILA_EINVAL, "K = %d: must satisfy 2 <= K <= min(n / max m, 64) = %d", K,
+                    min_S < 64 ? min_S : 64);
+    const size_t rs = real_size(h);
+    void *crit, *ms, *bi, *dk;
+    TRY(scratch(h, "sel_crit", 8 * (size_t)n_m, &crit));
+    TRY(scratch(h, "sel_ms", 4 * (size_t)n_m, &ms));
+    TRY(scratch(h, "sel_best", 4, &bi));
+    TRY(scratch(h, "dmax", 8, &dk));
+    CK(cudaMemcpyAsync(ms, m_list, 4 * (size_t)n_m, cudaMemcpyHostToDevice, h->stream));
+    std::vector<pastila_snippet> per_m((size_t)n_m * K);
+    for (int i = 0; i < n_m; ++i) {
+        const MParams& q = qs[i];
+        void* D;
+        TRY(scratch(h, "D", rs * (size_t)q.S * (size_t)q.P, &D));
+        TRY(launch_profiles(h, q, D, (unsigned long long*)dk));
+        TRY(snippets_on_device(h, q, D, K, nullptr, (const unsigned long long*)dk, (double*)crit + i));
+        TRY(read_snippets(h, K, per_m.data() + (size_t)i * K));
+    }
+    select_best_kernel<<<1, 1, 0, h->stream>>>((const double*)crit, (const int32_t*)ms, n_m, (int32_t*)bi);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    int32_t b = 0;
+    std::vector<double> cv(n_m);
+    CK(cudaMemcpyAsync(&b, bi, 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(cv.data(), crit, 8 * (size_t)n_m, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *m_best = m_list[b];
+    if (crit_out) memcpy(crit_out, cv.data(), 8 * (size_t)n_m);
+    if (best_out) memcpy(best_out, per_m.data() + (size_t)b * K, sizeof(pastila_snippet) * K);
+    return PASTILA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Snippet search on the profile set D (S x P, row-major), Section 4.1 eqs. 16-17,
+// the neighbour shares of eqs. 6-8, and the length criterion of eq. 18.
+// All sums are FP64 with a fixed reduction order, so results are bit-identical
+// from run to run.
+#pragma once
+#include <cstdint>
+
+#include "keys.cuh"
+
+namespace pastila {
+
+constexpr int AREA_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// area[s] = sum_p min(M_p, D_s(p)) for every segment s (M = +inf on the first
+// step, so the area is the row sum).  One CTA per segment; chosen segments are
+// skipped and get +inf.  Grid: (S).
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS)
+area_kernel(const real* __restrict__ D, int S, int64_t P, const real* __restrict__ M,
+            const int32_t* __restrict__ chosen, int nchosen, double* __restrict__ area) {
+    __shared__ double red[AREA_THREADS / 32];
+    const int s = blockIdx.x;
+    bool skip = false;
+    for (int t = 0; t < nchosen; ++t) skip |= chosen[t] == s;
+    if (skip) {
+        if (threadIdx.x == 0) area[s] = __longlong_as_double(0x7ff0000000000000ll);
+        return;
+    }
+    const real* row = D + (int64_t)s * P;
+    double acc = 0.0;
+    if (M == nullptr) {
+        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += (double)row[p];
+    } else {
+        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) {
+            const real d = row[p], mm = M[p];
+            acc += (double)(d < mm ? d : mm);
+        }
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) area[s] = tot;
+}
+
+// Greedy step: the unchosen segment with the smallest area (lowest index on
+// ties) becomes chosen[t]; area_after[t] records its area.  One CTA of 1024.
+__global__ void argmin_area_kernel(const double* __restrict__ area, int S, int32_t* __restrict__ chosen,
+                                   double* __restrict__ area_after, int t) {
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    double best = __longlong_as_double(0x7ff0000000000000ll);
+    int bidx = 0x7fffffff;
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        const double a = area[s];
+        bool chosen_already = false;
+        for (int u = 0; u < t; ++u) chosen_already |= chosen[u] == s;
+        if (chosen_already) continue;
+        if (a < best || (a == best && s < bidx)) { best = a; bidx = s; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            const double ov = bv[threadIdx.x + w];
+            const int oi = bi[threadIdx.x + w];
+            if (ov < bv[threadIdx.x] || (ov == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+                bv[threadIdx.x] = ov;
+                bi[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        chosen[t] = bi[0];
+        area_after[t] = bv[0];
+    }
+}
+
+// M <- min(M, D_{chosen[t]}) (M = D_{chosen[0]} on the first step).
+template <typename real>
+__global__ void update_curve_kernel(const real* __restrict__ D, int64_t P, const int32_t* __restrict__ chosen,
+                                    int t, real* __restrict__ M) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const real d = D[(int64_t)chosen[t] * P + p];
+    if (t == 0) {
+        M[p] = d;
+    } else {
+        const real mm = M[p];
+        M[p] = d < mm ? d : mm;
+    }
+}
+
+// Nearest snippet per position (eq. 6, argmin over the K chosen profiles, lowest
+// segment index on ties) and per-snippet counts.  counts[] must start at 0.
+template <typename real>
+__global__ void neighbors_kernel(const real* __restrict__ D, int64_t P, const int32_t* __restrict__ chosen,
+                                 int K, int32_t* __restrict__ labels,
+                                 unsigned long long* __restrict__ counts) {
+    __shared__ unsigned int local[64];
+    if (threadIdx.x < 64) local[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) {
+        int bt = 0;
+        real bv = D[(int64_t)chosen[0] * P + p];
+        for (int t = 1; t < K; ++t) {
+            const real v = D[(int64_t)chosen[t] * P + p];
+            if (v < bv || (v == bv && chosen[t] < chosen[bt])) { bv = v; bt = t; }
+        }
+        if (labels) labels[p] = chosen[bt];
+        atomicAdd(&local[bt], 1u);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < K && local[threadIdx.x])
+        atomicAdd(&counts[threadIdx.x], (unsigned long long)local[threadIdx.x]);
+}
+
+// frac (eq. 7) and the eq. 8 order (frac descending, segment index ascending).
+// out_* are K records in eq. 8 order.  One thread.
+__global__ void finalize_snippets_kernel(const int32_t* __restrict__ chosen, const double* __restrict__ area_after,
+                                         const unsigned long long* __restrict__ counts, int K, int64_t P,
+                                         int32_t* __restrict__ out_index, int32_t* __restrict__ out_rank,
+                                         double* __restrict__ out_frac, double* __restrict__ out_area) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int order[64];
+    for (int t = 0; t < K; ++t) order[t] = t;
+    for (int i = 1; i < K; ++i) {
+        const int x = order[i];
+        int j = i - 1;
+        while (j >= 0) {
+            const int y = order[j];
+            const bool before = counts[x] > counts[y] || (counts[x] == counts[y] && chosen[x] < chosen[y]);
+            if (!before) break;
+            order[j + 1] = y;
+            --j;
+        }
+        order[j + 1] = x;
+    }
+    for (int i = 0; i < K; ++i) {
+        const int t = order[i];
+        out_index[i] = chosen[t];
+        out_rank[i] = t;
+        out_frac[i] = (double)counts[t] / (double)P;
+        out_area[i] = area_after[t];
+    }
+}
+
+// Numerator of eq. 18: partial[b] = sum over ordered pairs p != q of the chosen
+// profiles of sum_{i in block b's range} |D_p(i) - D_q(i)|  (each unordered pair
+// counted twice).  Grid: (nblocks); fixed ranges, fixed order.
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS)
+criterion_partial_kernel(const real* __restrict__ D, int64_t P, const int32_t* __restrict__ chosen, int K,
+                         double* __restrict__ partial) {
+    __shared__ double red[AREA_THREADS / 32];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * AREA_THREADS;
+    for (int64_t i = (int64_t)blockIdx.x * AREA_THREADS + threadIdx.x; i < P; i += stride) {
+        for (int a = 0; a < K; ++a) {
+            const double x = (double)D[(int64_t)chosen[a] * P + i];
+            for (int b = a + 1; b < K; ++b) {
+                const double y = (double)D[(int64_t)chosen[b] * P + i];
+                acc += fabs(x - y);
+            }
+        }
+    }
+    const double tot = block_sum(2.0 * acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// crit = sum(partial) / D_max (0 when D_max == 0).  One thread.
+__global__ void criterion_final_kernel(const double* __restrict__ partial, int nb,
+                                       const unsigned long long* __restrict__ dmax_key, double* __restrict__ crit) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double num = 0.0;
+    for (int b = 0; b < nb; ++b) num += partial[b];
+    const double den = KeyOf<double>::dec(*dmax_key);
+    *crit = den > 0.0 ? num / den : 0.0;
+}
+
+// m_best = argmax crit (smallest m on ties).  One thread.
+__global__ void select_best_kernel(const double* __restrict__ crit, const int32_t* __restrict__ ms, int n,
+                                   int32_t* __restrict__ best_idx) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int b = 0;
+    for (int i = 1; i < n; ++i)
+        if (crit[i] > crit[b] || (crit[i] == crit[b] && ms[i] < ms[b])) b = i;
+    *best_idx = b;
+}
+
+}  // namespace pastila

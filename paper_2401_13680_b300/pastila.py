@@ -1,0 +1,201 @@
+"""ctypes binding of ``libpastila.so`` (C ABI in ``include/pastila.h``).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  The names follow the C entry points.  There is no CPU fallback:
+``load()`` raises if the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECANCELLED, EBUSY = range(7)
+FP32, FP64 = 0, 1
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ECANCELLED", 6: "EBUSY"}
+
+
+class PastilaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class MParams(ctypes.Structure):
+    _fields_ = [("ell", ctypes.c_int32), ("k", ctypes.c_int32)]
+
+
+class Snippet(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int32), ("rank", ctypes.c_int32), ("frac", ctypes.c_double),
+                ("area_after", ctypes.c_double)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load(path: str | None = None):
+    """Build (if stale) and load the library; returns the ctypes handle."""
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(path or _build.build())
+        S = ctypes.c_int
+        lib.pastila_create.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_int64, ctypes.c_int,
+                                       ctypes.c_size_t, ctypes.c_int]
+        lib.pastila_create.restype = S
+        lib.pastila_create_device.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_size_t, ctypes.c_int, _vp]
+        lib.pastila_create_device.restype = S
+        lib.pastila_destroy.argtypes = [_vp]
+        lib.pastila_destroy.restype = None
+        lib.pastila_last_error.argtypes = []
+        lib.pastila_last_error.restype = ctypes.c_char_p
+        lib.pastila_profiles.argtypes = [_vp, ctypes.c_int32, MParams, _vp, ctypes.POINTER(ctypes.c_double)]
+        lib.pastila_profiles.restype = S
+        lib.pastila_profiles_device.argtypes = [_vp, ctypes.c_int32, MParams, _vp, _vp]
+        lib.pastila_profiles_device.restype = S
+        lib.pastila_snippets.argtypes = [_vp, ctypes.c_int32, MParams, ctypes.c_int32,
+                                         ctypes.POINTER(Snippet), _vp, _vp]
+        lib.pastila_snippets.restype = S
+        lib.pastila_select_length.argtypes = [_vp, _vp, ctypes.c_int32, MParams, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32), _vp, ctypes.POINTER(Snippet)]
+        lib.pastila_select_length.restype = S
+        lib.pastila_reload.argtypes = [_vp, _vp]
+        lib.pastila_reload.restype = S
+        lib.pastila_reload_device.argtypes = [_vp, _vp]
+        lib.pastila_reload_device.restype = S
+        lib.pastila_kernel_launches.argtypes = [_vp]
+        lib.pastila_kernel_launches.restype = ctypes.c_uint64
+        lib.pastila_set_timing.argtypes = [_vp, ctypes.c_int]
+        lib.pastila_set_timing.restype = S
+        lib.pastila_tile_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        lib.pastila_tile_time.restype = S
+        _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load().pastila_last_error().decode()
+
+
+def _check(st: int):
+    if st != OK:
+        raise PastilaError(st, last_error())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_vp)
+
+
+def _recs(out):
+    return [(s.index, s.rank, s.frac, s.area_after) for s in out]
+
+
+class Series:
+    """A series resident on one GPU (``pastila_create`` / ``pastila_create_device``)."""
+
+    def __init__(self, T, device: int = 0, precision: int = FP32, mem_budget: int = 0,
+                 *, device_ptr: int | None = None, n: int | None = None, stream: int | None = None):
+        lib = load()
+        h = _vp()
+        self.precision = precision
+        if device_ptr is not None:
+            _check(lib.pastila_create_device(ctypes.byref(h), _vp(device_ptr), int(n), device,
+                                             mem_budget, precision, _vp(stream or 0)))
+            self.n = int(n)
+        else:
+            T = np.ascontiguousarray(T, dtype=np.float64)
+            _check(lib.pastila_create(ctypes.byref(h), _ptr(T), T.shape[0], device, mem_budget, precision))
+            self.n = T.shape[0]
+        self._h = h
+
+    @property
+    def dtype(self):
+        return np.float64 if self.precision == FP64 else np.float32
+
+    def close(self):
+        if self._h:
+            load().pastila_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reload(self, T):
+        """``pastila_reload``: new host values, statistics marked stale."""
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        assert T.shape[0] == self.n
+        _check(load().pastila_reload(self._h, _ptr(T)))
+
+    def reload_device(self, ptr: int):
+        """``pastila_reload_device``: new values from a device buffer."""
+        _check(load().pastila_reload_device(self._h, _vp(ptr)))
+
+    def kernel_launches(self) -> int:
+        return int(load().pastila_kernel_launches(self._h))
+
+    def set_timing(self, on: bool):
+        _check(load().pastila_set_timing(self._h, 1 if on else 0))
+
+    def tile_time(self):
+        """(device ms, launches, ED cells) of the timed tile-kernel launches."""
+        ms, n, cells = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(load().pastila_tile_time(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(cells)))
+        return ms.value, n.value, cells.value
+
+    def profiles(self, m: int, ell: int = 0, k: int = 0, want_D: bool = True):
+        """(D as an S x P array or None, D_max)  -- ``pastila_profiles``."""
+        S, P = self.n // m, self.n - m + 1
+        D = np.empty((S, P), dtype=self.dtype) if want_D else None
+        dmax = ctypes.c_double()
+        _check(load().pastila_profiles(self._h, m, MParams(ell, k), _ptr(D) if want_D else None,
+                                       ctypes.byref(dmax)))
+        return D, dmax.value
+
+    def profiles_device(self, m: int, D_ptr: int, dmax_ptr: int | None = None, ell: int = 0, k: int = 0):
+        """Enqueue D into a device buffer (``pastila_profiles_device``)."""
+        _check(load().pastila_profiles_device(self._h, m, MParams(ell, k), _vp(D_ptr),
+                                              _vp(dmax_ptr) if dmax_ptr else None))
+
+    def snippets(self, m: int, K: int, ell: int = 0, k: int = 0, want_labels: bool = False,
+                 want_profiles: bool = False):
+        """(records in eq. 8 order, labels or None, chosen profiles or None) --
+        ``pastila_snippets``; a record is (index, rank, frac, area_after)."""
+        P = self.n - m + 1
+        out = (Snippet * K)()
+        labels = np.empty(P, dtype=np.int32) if want_labels else None
+        prof = np.empty((K, P), dtype=self.dtype) if want_profiles else None
+        _check(load().pastila_snippets(self._h, m, MParams(ell, k), K, out,
+                                       _ptr(labels) if want_labels else None,
+                                       _ptr(prof) if want_profiles else None))
+        return _recs(out), labels, prof
+
+    def select_length(self, ms, K: int, ell: int = 0, k: int = 0):
+        """(m_best, crit per m, K records of m_best) -- ``pastila_select_length``."""
+        ms = np.ascontiguousarray(ms, dtype=np.int32)
+        crit = np.empty(ms.shape[0], dtype=np.float64)
+        best = ctypes.c_int32()
+        out = (Snippet * K)()
+        _check(load().pastila_select_length(self._h, _ptr(ms), ms.shape[0], MParams(ell, k), K,
+                                            ctypes.byref(best), _ptr(crit), out))
+        return best.value, crit, _recs(out)
+
+
+def exported_symbols():
+    """Names of the entry points declared in include/pastila.h."""
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "pastila.h")
+    return sorted(set(re.findall(r"\b(pastila_[a-z_]+)\s*\(", open(hdr).read())))

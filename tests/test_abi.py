@@ -1,0 +1,45 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/pastila.h.  CPU only: no call here reaches a kernel."""
+import ctypes
+import subprocess
+
+import numpy as np
+
+from paper_2401_13680_b300 import build, pastila
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    declared = pastila.exported_symbols()
+    assert len(declared) >= 13
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    lib = pastila.load()
+    for s in declared:
+        assert getattr(lib, s) is not None
+
+
+def test_host_side_argument_validation():
+    lib = pastila.load()
+    h = ctypes.c_void_p()
+    # NULL series is rejected before any device call
+    assert lib.pastila_create(ctypes.byref(h), None, 100, 0, 0, pastila.FP32) == pastila.EINVAL
+    assert "T is NULL" in pastila.last_error()
+    T = np.array([0.0, 1.0, np.nan, 3.0, 4.0])
+    assert lib.pastila_create(ctypes.byref(h), T.ctypes.data_as(ctypes.c_void_p), 5, 0, 0,
+                              pastila.FP32) == pastila.EINVAL
+    assert "not finite" in pastila.last_error()
+    assert lib.pastila_create(None, T.ctypes.data_as(ctypes.c_void_p), 5, 0, 0, pastila.FP32) \
+        == pastila.EINVAL
+    # a NULL handle is an argument error on every entry point
+    assert lib.pastila_profiles(None, 64, pastila.MParams(0, 0), None, None) == pastila.EINVAL
+    assert lib.pastila_snippets(None, 64, pastila.MParams(0, 0), 2, None, None, None) == pastila.EINVAL
+    assert lib.pastila_select_length(None, None, 0, pastila.MParams(0, 0), 2, None, None, None) \
+        == pastila.EINVAL
+    assert lib.pastila_reload(None, None) == pastila.EINVAL
+    assert lib.pastila_set_timing(None, 1) == pastila.EINVAL
+    assert lib.pastila_kernel_launches(None) == 0
+    lib.pastila_destroy(None)  # no-op

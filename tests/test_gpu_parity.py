@@ -1,0 +1,173 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  FP32 profiles within 1e-4, FP64 within 1e-9, under the
+floor rule of tests/tolerance.py; snippet indices bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tolerance import assert_profiles_close
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 1: 1e-9}
+
+
+def _series(T, prec):
+    from paper_2401_13680_b300 import pastila
+    return pastila.Series(T, precision=prec)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_four_regime_profiles(lib, prec):
+    s = synth.four_regimes()
+    m, ell, k = 128, 64, 13
+    ref = oracle.profiles(s.T, m, ell, k)
+    with _series(s.T, prec) as h:
+        D, dmax = h.profiles(m)
+    assert D.shape == ref.shape
+    assert_profiles_close(D, ref, ell, TOL[prec])
+    assert dmax == pytest.approx(ref.max(), rel=TOL[prec])
+
+
+# (n, m, ell, k): several tiles with a ragged last tile and a tail segment
+# (n % m != 0); R < V (ell close to m); R = 1 (ell = m); k >= 2R (max branch);
+# k = 1 (min branch); odd sizes
+CASES = [
+    (3000, 64, 32, 7),
+    (2501, 50, 25, 5),
+    (1800, 40, 37, 3),
+    (1500, 30, 30, 3),
+    (1200, 24, 20, 12),
+    (1700, 48, 16, 1),
+    (5003, 100, 50, 10),
+    (900, 8, 4, 2),
+]
+
+
+@pytest.mark.parametrize("n,m,ell,k", CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_profiles_shapes_and_edges(lib, n, m, ell, k, prec):
+    rng = np.random.default_rng(n + m)
+    T = synth.random_planted(rng, n, 3).T
+    ref = oracle.profiles(T, m, ell, k)
+    with _series(T, prec) as h:
+        D, dmax = h.profiles(m, ell=ell, k=k)
+    assert_profiles_close(D, ref, ell, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_random_walk_with_drift(lib, prec):
+    # wandering mean (the drift workload's character) stresses the shifted seeds
+    rng = np.random.default_rng(5)
+    T = np.cumsum(rng.normal(0, 0.3, 6000)) + 50.0
+    m, ell, k = 96, 48, 10
+    ref = oracle.profiles(T, m, ell, k)
+    with _series(T, prec) as h:
+        D, _ = h.profiles(m)
+    assert_profiles_close(D, ref, ell, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_flat_windows(lib, prec):
+    rng = np.random.default_rng(9)
+    T = rng.normal(size=1200)
+    T[300:420] = 2.5      # flat stretch longer than ell: flat windows on both sides
+    T[800:860] = -1.0
+    m, ell, k = 40, 20, 4
+    ref = oracle.profiles(T, m, ell, k)
+    with _series(T, prec) as h:
+        D, _ = h.profiles(m)
+    assert_profiles_close(D, ref, ell, TOL[prec])
+
+
+def test_fp32_own_offset_is_zero(lib):
+    s = synth.four_regimes()
+    with _series(s.T, 0) as h:
+        D, _ = h.profiles(128)
+    own = D[np.arange(D.shape[0]), np.arange(D.shape[0]) * 128]
+    assert np.all(own == 0.0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_deterministic(lib, prec):
+    s = synth.four_regimes()
+    with _series(s.T, prec) as h:
+        D1, m1 = h.profiles(128)
+        D2, m2 = h.profiles(128)
+    assert np.array_equal(D1, D2) and m1 == m2
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_snippets_fp64_bit_exact(lib, K):
+    s = synth.four_regimes()
+    m, ell, k = 128, 64, 13
+    chosen, area, labels, frac, order, D = oracle.snippets(s.T, m, ell, k, K)
+    with _series(s.T, 1) as h:
+        recs, lab, prof = h.snippets(m, K, want_labels=True, want_profiles=True)
+    assert [r[0] for r in recs] == [int(chosen[o]) for o in order]
+    assert [r[1] for r in recs] == [int(o) for o in order]
+    np.testing.assert_allclose([r[2] for r in recs], [frac[o] for o in order], rtol=0, atol=0)
+    np.testing.assert_allclose([r[3] for r in recs], [area[o] for o in order], rtol=1e-9)
+    assert np.array_equal(lab, labels)
+    np.testing.assert_allclose(prof, D[chosen], rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_snippets_fp32(lib, K):
+    """FP32: (1) the GPU greedy equals the oracle greedy run on the GPU's own D
+    (decision taken in the same precision); (2) against the FP64 oracle D the
+    chosen indices agree, or every disagreement is a near-tie inside the FP32
+    error bound."""
+    s = synth.four_regimes()
+    m, ell, k = 128, 64, 13
+    with _series(s.T, 0) as h:
+        Dg, _ = h.profiles(m)
+        recs, lab, prof = h.snippets(m, K, want_labels=True, want_profiles=True)
+    c_same, a_same = oracle.greedy(Dg.astype(np.float64), K)
+    lab_same, frac_same, order_same = oracle.neighbors(Dg.astype(np.float64), c_same)
+    assert [r[0] for r in recs] == [int(c_same[o]) for o in order_same]
+    np.testing.assert_allclose([r[3] for r in recs], [a_same[o] for o in order_same], rtol=1e-12)
+    assert np.array_equal(lab, lab_same)
+    c_ref, a_ref, *_ = oracle.snippets(s.T, m, ell, k, K)
+    if list(c_ref) != list(c_same):
+        Dr = oracle.profiles(s.T, m, ell, k)
+        M = np.full(Dr.shape[1], np.inf)
+        for t in range(K):
+            areas = np.minimum(M[None, :], Dr).sum(axis=1)
+            assert areas[c_same[t]] - areas[c_ref[t]] <= 2e-4 * areas[c_ref[t]]
+            M = np.minimum(M, Dr[c_same[t]])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_select_length_small_sweep(lib, prec):
+    s = synth.four_regimes(per_regime=512)
+    ms = [32, 48, 64, 80]
+    K = 3
+    m_best, crit, chosen = oracle.select_length(s.T, ms, K, lambda m: m // 2, lambda m: (m + 9) // 10)
+    with _series(s.T, prec) as h:
+        gb, gcrit, recs = h.select_length(ms, K)
+    # criterion: relative error of a sum of |differences| of profiles, each within tol
+    np.testing.assert_allclose(gcrit, crit, rtol=1e-3 if prec == 0 else 1e-8)
+    assert gb == m_best
+    assert sorted(r[0] for r in recs) == sorted(int(c) for c in chosen[m_best])
+
+
+def test_sweep_full_size_sampled_cells(lib):
+    """The n = 100,000 six-regime sweep at full size, in the FP32 configuration the
+    benchmark times: 200 sampled (segment, position) cells per m checked against
+    the pair definition, for three lengths of the sweep."""
+    s = synth.six_regime_sweep()
+    rng = np.random.default_rng(123)
+    with _series(s.T, 0) as h:
+        for m in (64, 256, 512):
+            ell, k = m // 2, (m + 9) // 10
+            D, dmax = h.profiles(m)
+            S, P = D.shape
+            segs = rng.integers(0, S, 200)
+            pos = rng.integers(0, P, 200)
+            pos[:8] = [0, P - 1, P - 2, 1, segs[0] * m, segs[1] * m, P // 2, P // 3]
+            ref = oracle.profile_cells(s.T, m, ell, k, segs, pos)
+            assert_profiles_close(D[segs, pos], ref, ell, TOL[0])
+            assert np.all(D >= 0) and np.all(D <= 2 * np.sqrt(ell) * (1 + 1e-6))
+            assert dmax == pytest.approx(float(D.max()), rel=1e-7)

@@ -267,3 +267,10 @@ def test_golden_fixtures_reproduce():
     T = synth.white_noise(77, 120).cumsum()
     np.testing.assert_allclose(oracle.profiles(T, t["m"], t["ell"], t["k"]), np.array(t["D"]),
                                rtol=1e-12, atol=1e-12)
+
+
+def test_profiles_range_matches_full():
+    T = synth.white_noise(21, 400).cumsum()
+    D = oracle.profiles(T, 32, 16, 4)
+    segs = [0, 5, 11]
+    np.testing.assert_array_equal(oracle.profiles_range(T, 32, 16, 4, segs, 17, 201), D[segs, 17:201])

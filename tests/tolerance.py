@@ -1,0 +1,37 @@
+"""Tolerance rule for MPdist values (FP32: 1e-4, FP64: 1e-9).
+
+Relative error is ill-posed near d = 0 because d = sqrt(2 ell (1 - rho)) turns a
+fixed error in rho into an error in d that grows like ell * d_rho / d.  So the
+rule uses a floor d_floor = 0.1 * sqrt(2 ell) (1/20 of the largest possible
+distance 2 sqrt(ell)):
+    d_ref >= d_floor:  |d - d_ref| <= tol * d_ref
+    d_ref <  d_floor:  |d^2 - d_ref^2| <= tol * d_floor^2
+(an error of tol * d_floor^2 / (2 ell) = tol / 100 in rho below the floor).
+"""
+import numpy as np
+
+
+def d_floor(ell: int) -> float:
+    return 0.1 * np.sqrt(2.0 * ell)
+
+
+def profile_errors(d, d_ref, ell: int):
+    """Per-cell error ratio under the rule above (compare with tol)."""
+    d = np.asarray(d, dtype=np.float64)
+    d_ref = np.asarray(d_ref, dtype=np.float64)
+    fl = d_floor(ell)
+    above = d_ref >= fl
+    ratio = np.empty_like(d_ref)
+    ratio[above] = np.abs(d[above] - d_ref[above]) / d_ref[above]
+    ratio[~above] = np.abs(d[~above] ** 2 - d_ref[~above] ** 2) / fl ** 2
+    return ratio
+
+
+def assert_profiles_close(d, d_ref, ell: int, tol: float):
+    r = profile_errors(d, d_ref, ell) / tol
+    worst = int(np.argmax(r)) if r.size else 0
+    assert r.size == 0 or r.max() <= 1.0, (
+        f"worst cell {np.unravel_index(worst, np.shape(d_ref))}: got {np.ravel(d)[worst]!r}, "
+        f"oracle {np.ravel(d_ref)[worst]!r}, error/tol = {r.ravel()[worst]:.3g}, "
+        f"cells over: {int((r > 1).sum())} of {r.size}")
+    return float(r.max()) if r.size else 0.0
