@@ -14,7 +14,8 @@
 // Phases:
 //   1  seeds: exact dot products cov(0, x) for every column (top row) and
 //      cov(r, 0) for every row (left edge), in the working precision, from
-//      series values shifted by a local reference (covariance is shift-invariant)
+//      series values held as hi + lo pairs about a tile reference and centred
+//      locally before they are multiplied (covariance is shift-invariant)
 //   2  rows r = 0 .. R-1: centred recurrence along diagonals
 //        cov(r, x) = cov(r-1, x-1) + df_i dg_j + df_j dg_i
 //      thread t owns the V columns tV .. tV+V-1.  The covariance is carried as
@@ -64,8 +65,8 @@ struct ProfileArgs {
 // Shared-memory layout of one tile; identical on host and device.
 struct TileGeom {
     int R, W, Wb, V, NT, NW, LA, RS, LP, ell, m;
-    size_t off_AB, off_CB, off_PRE, off_CM, off_XCH, off_row, off_left, off_top, off_Tc, off_Ts,
-        off_q, bytes;
+    size_t off_AB, off_CB, off_PRE, off_CM, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
+        off_Ts, off_Tsl, off_q, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -101,11 +102,13 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V) {
     g.off_PRE = o;  o = align16(o + sizeof(real) * 2 * (size_t)V * g.LP);
     g.off_CM = o;   o = align16(o + sizeof(real) * 2 * (size_t)(g.NT + 1));
     g.off_XCH = o;  o = align16(o + sizeof(real) * 4 * (size_t)g.NW);
-    g.off_row = o;  o = align16(o + sizeof(real) * 4 * (size_t)g.R);
+    g.off_row = o;  o = align16(o + sizeof(real) * 5 * (size_t)g.R);
     g.off_left = o; o = align16(o + sizeof(real) * (size_t)g.R);
     g.off_top = o;  o = align16(o + sizeof(real) * (size_t)(g.NT * V));
     g.off_Tc = o;   o = align16(o + sizeof(real) * (size_t)(g.NT * V + ell + 64));
+    g.off_Tcl = o;  o = align16(o + sizeof(real) * (size_t)(g.NT * V + ell + 64));
     g.off_Ts = o;   o = align16(o + sizeof(real) * (size_t)m);
+    g.off_Tsl = o;  o = align16(o + sizeof(real) * (size_t)m);
     g.off_q = o;    o = align16(o + sizeof(real) * (size_t)(ell + 1));
     g.bytes = o;
     return g;
@@ -164,55 +167,82 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     real* rdf = (real*)(sm + G.off_row);
     real* rdg = rdf + R;
     real* ra = rdg + R;
-    real* rmu = ra + R;
+    real* rmu = ra + R;   // hi part of mu_i - refs
+    real* rmul = rmu + R; // lo part
     real* lseed = (real*)(sm + G.off_left);
     real* top = (real*)(sm + G.off_top);
-    real* Tc = (real*)(sm + G.off_Tc);
+    real* Tc = (real*)(sm + G.off_Tc);    // T - refc as hi + lo pairs: exact to about
+    real* Tcl = (real*)(sm + G.off_Tcl);  // twice the working precision
     real* Ts = (real*)(sm + G.off_Ts);
+    real* Tsl = (real*)(sm + G.off_Tsl);
     real* q = (real*)(sm + G.off_q);
 
     // ---------------------------------------------------------------- stage
     const double refc = A.mu[p0];
     const double refs = A.mu[i0];
     const int nTc = Wb + ell - 1;
-    for (int y = tid; y < NT * V + ell + 64; y += NT)
-        Tc[y] = y < nTc ? (real)(A.T[p0 + y] - refc) : (real)0;
-    for (int u = tid; u < m; u += NT) Ts[u] = (real)(A.T[i0 + u] - refs);
+    for (int y = tid; y < NT * V + ell + 64; y += NT) {
+        const double d = y < nTc ? A.T[p0 + y] - refc : 0.0;
+        const real h = (real)d;
+        Tc[y] = h;
+        Tcl[y] = (real)(d - (double)h);
+    }
+    for (int u = tid; u < m; u += NT) {
+        const double d = A.T[i0 + u] - refs;
+        const real h = (real)d;
+        Ts[u] = h;
+        Tsl[u] = (real)(d - (double)h);
+    }
     for (int r = tid; r < R; r += NT) {
         rdf[r] = A.df[i0 + r];
         rdg[r] = A.dg[i0 + r];
         ra[r] = A.a[i0 + r];
-        rmu[r] = (real)(A.mu[i0 + r] - refs);
+        const double d = A.mu[i0 + r] - refs;
+        rmu[r] = (real)d;
+        rmul[r] = (real)(d - (double)rmu[r]);
     }
     for (int t = tid; t < ell; t += NT) q[t] = (real)(A.T[i0 + t] - A.mu[i0]);
     __syncthreads();
-    if (warp == 0) {
-        real acc = 0;
-        for (int t = lane; t < ell; t += 32) acc += q[t];
+    if (warp == 0) {  // sum of the rounded q, accumulated in FP64
+        double acc = 0;
+        for (int t = lane; t < ell; t += 32) acc += (double)q[t];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (lane == 0) q[ell] = acc;
+        if (lane == 0) q[ell] = (real)acc;
     }
 
     // ---------------------------------------------------------------- seeds
-    // left edge: cov(r, 0) = sum_t (Ts[r+t] - rmu[r]) * Tc[t]   (mu of column 0 is the reference)
+    // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0); the row
+    // values are centred term by term from their hi + lo parts, and mu of
+    // column 0 is the reference of Tc
     for (int r = 1 + tid; r < R; r += NT) {
-        const real mr = rmu[r];
+        const real mh = rmu[r], ml = rmul[r];
         real acc = 0;
-        for (int t = 0; t < ell; ++t) acc += (Ts[r + t] - mr) * Tc[t];
+        for (int t = 0; t < ell; ++t) acc += ((Ts[r + t] - mh) + (Tsl[r + t] - ml)) * (Tc[t] + Tcl[t]);
         lseed[r] = acc;
     }
     __syncthreads();
-    // top row: cov(0, x) = sum_t q[t] * Tc[x+t] - (mu_x - ref) * sum_t q[t]
-    // lane-contiguous blocks of 9 columns (odd stride: conflict-free sliding loads)
+    // top row: cov(0, x) = sum_t q[t] * (T[x+t] - c) - (mu_x - c) * sum_t q[t] for any
+    // constant c (the centred q sums to 0 up to rounding, and its rounded sum is
+    // taken exactly).  c is the mean of each block's first column: the series
+    // values of a block are centred once, from their hi + lo parts, as they enter
+    // a sliding register window, so the products never carry the level of the
+    // series, only its local deviations.  Lane-contiguous blocks of 9 columns
+    // (odd stride: conflict-free sliding loads).
     {
         constexpr int J = 9;
         const int nblk = (NT * V + J - 1) / J;
+        const real sq = q[ell];
         for (int b = tid; b < nblk; b += NT) {
             const int x0 = b * J;
+            const double cb = x0 < Wb ? A.mu[p0 + x0] - refc : 0.0;
+            const real cbh = (real)cb, cbl = (real)(cb - (double)cbh);
             real acc[J], win[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) { acc[j] = 0; win[j] = Tc[x0 + j]; }
+            for (int j = 0; j < J; ++j) {
+                acc[j] = 0;
+                win[j] = (Tc[x0 + j] - cbh) + (Tcl[x0 + j] - cbl);
+            }
             int t = 0;
             for (; t + J <= ell; t += J) {
 #pragma unroll
@@ -220,21 +250,24 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     const real qt = q[t + u];
 #pragma unroll
                     for (int j = 0; j < J; ++j) acc[j] += qt * win[(j + u) % J];
-                    win[u] = Tc[x0 + t + u + J];
+                    const int e = x0 + t + u + J;
+                    win[u] = (Tc[e] - cbh) + (Tcl[e] - cbl);
                 }
             }
             for (; t < ell; ++t) {
                 const real qt = q[t];
 #pragma unroll
-                for (int j = 0; j < J; ++j) acc[j] += qt * Tc[x0 + t + j];
+                for (int j = 0; j < J; ++j) {
+                    const int e = x0 + t + j;
+                    acc[j] += qt * ((Tc[e] - cbh) + (Tcl[e] - cbl));
+                }
             }
-            const real sq = q[ell];
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const int x = x0 + j;
                 if (x < Wb) {
-                    const real cm = (real)(A.mu[p0 + x] - refc);
-                    top[x] = acc[j] - cm * sq;
+                    const real dm = (real)(A.mu[p0 + x] - refc - cb);
+                    top[x] = acc[j] - dm * sq;
                 } else if (x < NT * V) {
                     top[x] = 0;
                 }

@@ -5,8 +5,11 @@ fixed error in rho into an error in d that grows like ell * d_rho / d.  So the
 rule uses a floor d_floor = 0.1 * sqrt(2 ell) (1/20 of the largest possible
 distance 2 sqrt(ell)):
     d_ref >= d_floor:  |d - d_ref| <= tol * d_ref
-    d_ref <  d_floor:  |d^2 - d_ref^2| <= tol * d_floor^2
-(an error of tol * d_floor^2 / (2 ell) = tol / 100 in rho below the floor).
+    d_ref <  d_floor:  |d^2 - d_ref^2| <= 2 tol * d_floor^2
+The second line is the first one carried into the squared domain at the floor
+(a relative error e in d is a relative error 2e in d^2), so the rule is
+continuous there; below the floor it allows an error of
+2 tol * d_floor^2 / (2 ell) = tol / 50 in rho.
 """
 import numpy as np
 
@@ -23,7 +26,7 @@ def profile_errors(d, d_ref, ell: int):
     above = d_ref >= fl
     ratio = np.empty_like(d_ref)
     ratio[above] = np.abs(d[above] - d_ref[above]) / d_ref[above]
-    ratio[~above] = np.abs(d[~above] ** 2 - d_ref[~above] ** 2) / fl ** 2
+    ratio[~above] = np.abs(d[~above] ** 2 - d_ref[~above] ** 2) / (2.0 * fl ** 2)
     return ratio
 
 
