@@ -154,6 +154,32 @@ pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, i
                                      pastila_mparams rule, int32_t K, int32_t* m_best,
                                      double* crit_out, pastila_snippet* best_out);
 
+/* --------------------------------------------- allocation-free variant ---- */
+
+/* The greedy snippet search of pastila_snippets (same kernels, same results),
+ * for callers that cannot allocate device memory: code whose device memory
+ * belongs to another allocator (a framework's caching pool, a process with a
+ * fixed memory partition) or that may not allocate once its hot loop runs.
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * Inputs and outputs are the caller's device buffers on the current device:
+ *   D_dev            S x P FP32 profile set, row-major (as pastila_profiles_device writes it)
+ *   chosen_dev       K int32: the chosen segments in greedy order
+ *   area_after_dev   K doubles: ProfileArea after each step
+ * The working storage (S areas, the P-point curve M) lives in one fixed device
+ * array of the library, 4.125 MiB, that every GPU loading the library holds
+ * until the process exits; hence S <= 16384 and P <= 1048576, and larger sizes
+ * are rejected with EINVAL.  The call allocates nothing and frees nothing.
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream) and the call returns without waiting.  The first call on a device,
+ * with that device current, looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race; order them on one stream or synchronise between them.
+ * Errors: EINVAL (NULL pointer, S, P or K out of range), ECUDA. */
+pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, int64_t P, int32_t K,
+                                      int32_t* chosen_dev, double* area_after_dev, void* stream);
+
 /* ------------------------------------------------------------- tracing ---- */
 
 /* Kernel launches the handle has issued since it was created. */

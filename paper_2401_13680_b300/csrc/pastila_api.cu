@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -636,3 +637,82 @@ pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free greedy snippet search.
+//
+// Some callers cannot call cudaMalloc: code running where device memory is
+// owned by another allocator (a framework's caching pool, a memory-capped or
+// pre-partitioned process) or where allocation is not allowed once the hot loop
+// has started.  For them, pastila_greedy_noalloc runs the greedy search of
+// eqs. 16-17 on a profile set they already hold in device memory, with its
+// working storage (the per-segment areas and the representativeness curve M)
+// in the fixed device array below instead of in allocated buffers.
+//
+// The array is defined once for the whole library and every GPU that loads
+// the library holds it until the process exits.  Host code may not use its
+// name as a device address: the address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int NOALLOC_MAX_S = 16384;              // segments
+constexpr int64_t NOALLOC_MAX_P = 1 << 20;        // positions
+constexpr size_t NOALLOC_AREA_BYTES = 8 * (size_t)NOALLOC_MAX_S;
+constexpr size_t NOALLOC_BYTES = NOALLOC_AREA_BYTES + 4 * (size_t)NOALLOC_MAX_P;  // 4.125 MiB
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 128;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device; looked up on the
+// first call made with that device current.
+pastila_status noalloc_scratch(void** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return fail(PASTILA_EINVAL, "device %d: the allocation-free entry point supports devices 0..%d", dev,
+                    NOALLOC_MAX_DEVICES - 1);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PASTILA_OK;
+}
+}  // namespace
+
+extern "C" pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, int64_t P, int32_t K,
+                                                 int32_t* chosen_dev, double* area_after_dev, void* stream) {
+    g_err.clear();
+    if (!D_dev || !chosen_dev || !area_after_dev)
+        return fail(PASTILA_EINVAL, "D_dev, chosen_dev and area_after_dev must be device pointers");
+    if (S < 1 || P < 1) return fail(PASTILA_EINVAL, "S = %d, P = %lld: both must be positive", S, (long long)P);
+    if (S > NOALLOC_MAX_S)
+        return fail(PASTILA_EINVAL, "S = %d exceeds the %d segments the fixed scratch holds", S, NOALLOC_MAX_S);
+    if (P > NOALLOC_MAX_P)
+        return fail(PASTILA_EINVAL, "P = %lld exceeds the %lld positions the fixed scratch holds", (long long)P,
+                    (long long)NOALLOC_MAX_P);
+    if (K < 1 || K > S || K > 64)
+        return fail(PASTILA_EINVAL, "K = %d: must satisfy 1 <= K <= min(S, 64) = %d", K, S < 64 ? S : 64);
+    void* base = nullptr;
+    TRY(noalloc_scratch(&base));
+    double* area = (double*)base;
+    float* M = (float*)((unsigned char*)base + NOALLOC_AREA_BYTES);
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned pb = (unsigned)((P + 255) / 256);
+    // every step writes all S areas and step 0 writes all of M before it is
+    // read, so nothing left in the array by an earlier call is ever used
+    for (int t = 0; t < K; ++t) {
+        area_kernel<float><<<S, AREA_THREADS, 0, st>>>(D_dev, S, P, t ? M : nullptr, chosen_dev, t, area);
+        argmin_area_kernel<<<1, 1024, 0, st>>>(area, S, chosen_dev, area_after_dev, t);
+        if (t + 1 < K) update_curve_kernel<float><<<pb, 256, 0, st>>>(D_dev, P, chosen_dev, t, M);
+    }
+    CK(cudaGetLastError());
+    return PASTILA_OK;
+}

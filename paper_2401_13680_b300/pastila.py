@@ -75,6 +75,8 @@ def load(path: str | None = None):
         lib.pastila_tile_time.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
         lib.pastila_tile_time.restype = S
+        lib.pastila_greedy_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp]
+        lib.pastila_greedy_noalloc.restype = S
         _lib = lib
     return _lib
 
@@ -193,6 +195,14 @@ class Series:
         _check(load().pastila_select_length(self._h, _ptr(ms), ms.shape[0], MParams(ell, k), K,
                                             ctypes.byref(best), _ptr(crit), out))
         return best.value, crit, _recs(out)
+
+
+def greedy_noalloc(D_ptr: int, S: int, P: int, K: int, chosen_ptr: int, area_ptr: int,
+                   stream: int | None = None):
+    """``pastila_greedy_noalloc``: greedy search on a device profile set, with
+    the library's fixed scratch; enqueued on ``stream``, not waited for."""
+    _check(load().pastila_greedy_noalloc(_vp(D_ptr), S, P, K, _vp(chosen_ptr), _vp(area_ptr),
+                                         _vp(stream or 0)))
 
 
 def exported_symbols():
