@@ -204,20 +204,40 @@ pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, M
     return PASTILA_OK;
 }
 
+// Tile width W and row groups NG: the smallest modelled cost per ED cell of the
+// eq. 9 matrix among the layouts that fit the shared memory and 512 threads.
+// Rows and seeds are paid on the Wb = W + R - 1 columns of a tile (the R - 1
+// halo columns are recomputed by the next tile), the selection on its W
+// positions; NG row groups add NG seed rows of ell products per column, and
+// fewer than 12 resident warps leave latency exposed.
 template <typename real, int V>
 pastila_status choose_tile(const pastila_series* h, const MParams& q, TileGeom* g) {
     const size_t limit = (size_t)h->smem_optin;
     const int64_t Pmax = ((q.P + 31) / 32) * 32;
-    int best = 0;
-    for (int W = 32; W <= MAX_NT * V; W += 32) {
-        if (W > Pmax) break;
-        TileGeom t = tile_geom<real>(q.m, q.ell, W, V);
-        if (t.NT > MAX_NT || t.bytes > limit) break;
-        best = W;
+    double best_cost = 1e300;
+    TileGeom best{};
+    for (int W = 32; W <= MAX_NT * V && W <= Pmax; W += 32) {
+        const int Wb = W + q.R - 1;
+        const int NTc = ((Wb + V - 1) / V + 31) / 32 * 32;
+        if (NTc > MAX_NT) break;
+        const int ng_max = MAX_NT / NTc;
+        for (int ngw = 1; ngw <= ng_max; ++ngw) {
+            TileGeom t = tile_geom<real>(q.m, q.ell, W, V, ngw);
+            if (t.NT > MAX_NT || t.bytes > limit) continue;
+            if (t.NG > 1 && t.Rg < 4) continue;
+            const double rows = 17.0 + 2.0 * t.NG * (double)q.ell / q.R;
+            const double sel = 23.0;
+            const double eff = t.NT >= 384 ? 1.0 : t.NT / 384.0;
+            const double cost = ((double)Wb / W * rows + sel) / eff;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = t;
+            }
+        }
     }
-    if (!best)
+    if (best_cost >= 1e300)
         return fail(PASTILA_EINVAL, "m = %d, ell = %d: the tile does not fit in shared memory", q.m, q.ell);
-    *g = tile_geom<real>(q.m, q.ell, best, V);
+    *g = best;
     return PASTILA_OK;
 }
 

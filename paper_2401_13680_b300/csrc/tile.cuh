@@ -11,24 +11,31 @@
 //   rows     r = 0 .. R-1   (ell-subsequence i = s*m + r of the segment)
 //   columns  x = 0 .. Wb-1  (ell-subsequence j = p0 + x of T), Wb = Wp + R - 1
 //   position p uses the R x R block rows 0..R-1, columns p .. p+R-1.
+// Threads: NG row groups x NTc column threads.  Row group g walks rows
+// g*Rg .. g*Rg+Rg-1; column thread t owns the V columns tV .. tV+V-1.  All
+// groups step through their rows together, one barrier per step.
 // Phases:
-//   1  seeds: exact dot products cov(0, x) for every column (top row) and
-//      cov(r, 0) for every row (left edge), in the working precision, from
-//      series values held as hi + lo pairs about a tile reference and centred
-//      locally before they are multiplied (covariance is shift-invariant)
-//   2  rows r = 0 .. R-1: centred recurrence along diagonals
+//   1  seeds: exact dot products cov(g*Rg, x) for every column at the first row
+//      of every row group, and cov(r, 0) for every row (left edge), in the
+//      working precision, from series values held as hi + lo pairs about a tile
+//      reference and centred locally before they are multiplied (covariance is
+//      shift-invariant)
+//   2  rows: centred recurrence along diagonals
 //        cov(r, x) = cov(r-1, x-1) + df_i dg_j + df_j dg_i
-//      thread t owns the V columns tV .. tV+V-1.  The covariance is carried as
-//      hi + lo: the updates of the last few rows accumulate in the small term lo,
-//      which is folded into hi every FOLD rows, so hi is rounded FOLD times less
-//      often than a plain running sum.  rho = (hi + lo) * a_i * a_j, and rho = 1
-//      exactly where the row and column subsequences coincide (i == j).  Column
-//      maxima (allP_BA, eq. 10) stay in registers; the row maxima over each
-//      position's R-column window (allP_AB, eq. 11) come from van Herk /
-//      Gil-Werman style prefix/suffix maxima over V-column chunks plus the maxima
-//      of the whole chunks in between; one barrier per row
-//   3  per position, the k-th largest of the 2R values of P_ABBA (eqs. 12-13)
-//      by bisection on order-preserving integer keys; D = sqrt(2 ell max(0, 1-rho*))
+//      The covariance is carried as hi + lo: the updates of up to V rows
+//      accumulate in the small term lo, folded into hi every V rows.  The V
+//      registers of a thread hold consecutive columns; the diagonal shift from
+//      row to row is a renaming of those registers inside an unrolled chunk of
+//      V rows, plus one shuffle between lanes and a shared-memory exchange
+//      between warps.  rho = (hi + lo) * a_i * a_j, and rho = 1 exactly where
+//      the row and column subsequences coincide (i == j).  Column maxima
+//      (allP_BA, eq. 10) stay in registers; the row maxima over each position's
+//      R-column window (allP_AB, eq. 11) come from van Herk / Gil-Werman style
+//      prefix/suffix maxima over V-column chunks plus the maxima of the whole
+//      chunks in between.
+//   3  per position, the k-th largest of the 2R values of P_ABBA (eqs. 12-13) on
+//      order-preserving integer keys, tracked from position to position by
+//      groups of lanes (select_track); D = sqrt(2 ell max(0, 1-rho*))
 #pragma once
 #include <cstdint>
 #include <cfloat>
@@ -36,8 +43,6 @@
 #include "keys.cuh"
 
 namespace pastila {
-
-constexpr int FOLD = 8;  // rows between folds of the small covariance term
 
 template <typename real> struct RealLimits;
 template <> struct RealLimits<float> {
@@ -62,27 +67,19 @@ struct ProfileArgs {
     unsigned long long* dmax_key;  // KeyOf<double>::enc(max D), combined with atomicMax
 };
 
-// Shared-memory layout of one tile; identical on host and device.
+// Shared-memory layout and thread layout of one tile; identical on host and device.
 struct TileGeom {
-    int R, W, Wb, V, NT, NW, LA, RS, LP, ell, m;
+    int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, LP, ell, m;
     size_t off_AB, off_CB, off_PRE, off_CM, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
         off_Ts, off_Tsl, off_q, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Smallest L >= need with L == 32 / V (mod 32): makes the chunk-swizzled layout
-// (element e at (e mod V) * L + e / V) conflict-free both for a warp whose lanes
-// stride by V and for a warp reading 32 consecutive elements from an aligned base.
-__host__ __device__ inline int swz_len(int need, int V) {
-    const int r = 32 / V;
-    int L = need;
-    while ((L & 31) != (r & 31)) ++L;
-    return L;
-}
-
+// NG_want row groups are asked for; the geometry uses Rg = ceil(R / NG_want)
+// rows per group and as many groups as that needs.
 template <typename real>
-__host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V) {
+__host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int NG_want) {
     typedef typename KeyOf<real>::type key_t;
     TileGeom g;
     g.m = m;
@@ -91,25 +88,32 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V) {
     g.W = W;
     g.Wb = W + g.R - 1;
     g.V = V;
-    g.NT = ((g.Wb + V - 1) / V + 31) / 32 * 32;
-    g.NW = g.NT / 32;
-    g.LA = swz_len((W + V - 1) / V, V);
-    g.RS = V * g.LA + 1;  // odd row stride: rows of one column fall in distinct banks
-    g.LP = swz_len(g.NT, V);
+    g.NTc = ((g.Wb + V - 1) / V + 31) / 32 * 32;
+    g.NWc = g.NTc / 32;
+    g.Rg = (g.R + NG_want - 1) / NG_want;
+    g.NG = (g.R + g.Rg - 1) / g.Rg;
+    g.NT = g.NG * g.NTc;
+    // AB row: position p at (p mod V) * LA + p / V, so the V-strided writes of a
+    // row (thread t writes tV + i) are consecutive; an odd row stride keeps the
+    // column reads of the selection (one position, many rows) in distinct banks
+    g.LA = (W + V - 1) / V;
+    g.RS = (V * g.LA) | 1;
+    g.LP = g.NTc + 1;  // chunk prefix maxima: [V][LP], thread t at t (+ chunk offset)
+    const size_t NG = (size_t)g.NG;
     size_t o = 0;
     g.off_AB = o;   o = align16(o + sizeof(key_t) * (size_t)g.R * g.RS);
     g.off_CB = o;   o = align16(o + sizeof(key_t) * (size_t)(g.Wb + 32));
-    g.off_PRE = o;  o = align16(o + sizeof(real) * 2 * (size_t)V * g.LP);
-    g.off_CM = o;   o = align16(o + sizeof(real) * 2 * (size_t)(g.NT + 1));
-    g.off_XCH = o;  o = align16(o + sizeof(real) * 4 * (size_t)g.NW);
+    g.off_PRE = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)V * g.LP);
+    g.off_CM = o;   o = align16(o + sizeof(real) * NG * 2 * (size_t)(g.NTc + 1));
+    g.off_XCH = o;  o = align16(o + sizeof(real) * NG * 4 * (size_t)g.NWc);
     g.off_row = o;  o = align16(o + sizeof(real) * 5 * (size_t)g.R);
     g.off_left = o; o = align16(o + sizeof(real) * (size_t)g.R);
-    g.off_top = o;  o = align16(o + sizeof(real) * (size_t)(g.NT * V));
-    g.off_Tc = o;   o = align16(o + sizeof(real) * (size_t)(g.NT * V + ell + 64));
-    g.off_Tcl = o;  o = align16(o + sizeof(real) * (size_t)(g.NT * V + ell + 64));
+    g.off_top = o;  o = align16(o + sizeof(real) * NG * (size_t)(g.NTc * V));
+    g.off_Tc = o;   o = align16(o + sizeof(real) * (size_t)(g.NTc * V + ell + 64));
+    g.off_Tcl = o;  o = align16(o + sizeof(real) * (size_t)(g.NTc * V + ell + 64));
     g.off_Ts = o;   o = align16(o + sizeof(real) * (size_t)m);
     g.off_Tsl = o;  o = align16(o + sizeof(real) * (size_t)m);
-    g.off_q = o;    o = align16(o + sizeof(real) * (size_t)(ell + 1));
+    g.off_q = o;    o = align16(o + sizeof(real) * NG * (size_t)(ell + 1));
     g.bytes = o;
     return g;
 }
@@ -117,32 +121,123 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V) {
 template <typename real>
 __device__ __forceinline__ real rmax(real a, real b) { return a > b ? a : b; }
 
-// Exact k-th largest key of the 2R values of P_ABBA at tile position p
-// (AB column p and CB[p .. p+R-1]) by bisection over the key range.
-template <typename key_t>
-__device__ __forceinline__ key_t select_kth_bisect(const key_t* __restrict__ AB, int RS, int swp,
-                                                   const key_t* __restrict__ CB, int p, int R,
-                                                   int kk) {
-    key_t lo = ~(key_t)0, hi = 0;
-    for (int r = 0; r < R; ++r) {
-        const key_t v = AB[r * RS + swp];
-        lo = v < lo ? v : lo;
-        hi = v > hi ? v : hi;
+// Group-wide reductions over G consecutive lanes (G = 8, 16 or 32; `mask`
+// holds exactly those lanes).
+__device__ __forceinline__ uint32_t grp_add(unsigned mask, int, uint32_t v) { return __reduce_add_sync(mask, v); }
+__device__ __forceinline__ uint32_t grp_min(unsigned mask, int, uint32_t v) { return __reduce_min_sync(mask, v); }
+__device__ __forceinline__ uint32_t grp_max(unsigned mask, int, uint32_t v) { return __reduce_max_sync(mask, v); }
+__device__ __forceinline__ unsigned long long grp_min(unsigned mask, int G, unsigned long long v) {
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(mask, v, o, G);
+        v = w < v ? w : v;
     }
-    for (int j = 0; j < R; ++j) {
-        const key_t v = CB[p + j];
-        lo = v < lo ? v : lo;
-        hi = v > hi ? v : hi;
+    return v;
+}
+__device__ __forceinline__ unsigned long long grp_max(unsigned mask, int G, unsigned long long v) {
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(mask, v, o, G);
+        v = w > v ? w : v;
     }
-    // invariant: count(>= lo) >= kk, count(>= hi + 1) < kk
-    while (lo < hi) {
-        const key_t mid = lo + (key_t)((hi - lo) >> 1) + 1;
-        int c = 0;
-        for (int r = 0; r < R; ++r) c += AB[r * RS + swp] >= mid;
-        for (int j = 0; j < R; ++j) c += CB[p + j] >= mid;
-        if (c >= kk) lo = mid; else hi = mid - 1;
+    return v;
+}
+
+// k-th largest key (kk-th, 1-based) of P_ABBA for the positions p_begin .. p_end-1
+// of a tile, walked in order by one group of G lanes: lane gl of the group holds
+// rows gl, gl+G, ... of AB column p and the window entries CB[p+gl], CB[p+gl+G], ...
+// The first position is found by bisection over the key range; every later one
+// starts from the previous answer tau (consecutive positions share all but a
+// few of their 2R values, so the rank of tau moves little): one pass counts the
+// keys >= tau and > tau and finds the nearest keys below and above tau, which
+// settles the answer whenever its rank moved by at most one; otherwise tau steps
+// to that neighbour and the pass repeats, and after a few steps the search
+// falls back to bisection inside the bracket already known.
+template <typename key_t, typename Out>
+__device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int RS, int LA, int V,
+                                             const key_t* __restrict__ CB, int R, int kk, int p_begin,
+                                             int p_end, int G, unsigned mask, int gl, Out out) {
+    const key_t KMAX = ~(key_t)0;
+    key_t tau = 0;
+    bool have = false;
+    for (int p = p_begin; p < p_end; ++p) {
+        const key_t* col = AB + (p % V) * LA + p / V;
+        const key_t* win = CB + p;
+        key_t lo = 0, hi = KMAX;  // answer in [lo, hi]
+        bool done = false;
+        int steps = 0;
+        if (have) {
+            while (!done) {
+                uint32_t cge = 0, cgt = 0;
+                key_t xb = KMAX, ya = KMAX;  // tau-1-key (keys below), key-tau-1 (keys above)
+                for (int r = gl; r < R; r += G) {
+                    const key_t v = col[r * RS];
+                    cge += v >= tau;
+                    cgt += v > tau;
+                    const key_t x = tau - (key_t)1 - v, y = v - tau - (key_t)1;
+                    xb = x < xb ? x : xb;
+                    ya = y < ya ? y : ya;
+                }
+                for (int j = gl; j < R; j += G) {
+                    const key_t v = win[j];
+                    cge += v >= tau;
+                    cgt += v > tau;
+                    const key_t x = tau - (key_t)1 - v, y = v - tau - (key_t)1;
+                    xb = x < xb ? x : xb;
+                    ya = y < ya ? y : ya;
+                }
+                cge = grp_add(mask, G, cge);
+                cgt = grp_add(mask, G, cgt);
+                xb = grp_min(mask, G, xb);
+                ya = grp_min(mask, G, ya);
+                if ((int)cgt < kk && kk <= (int)cge) {
+                    done = true;  // tau is the answer
+                } else if ((int)cge < kk) {  // answer below tau: nearest key below exists
+                    const key_t below = tau - (key_t)1 - xb;
+                    hi = below;
+                    if ((int)cge == kk - 1) {
+                        tau = below;
+                        done = true;
+                    } else {
+                        tau = below;
+                    }
+                } else {  // cgt >= kk: answer above tau: nearest key above exists
+                    const key_t above = tau + (key_t)1 + ya;
+                    lo = above;
+                    if ((int)cgt == kk) {
+                        tau = above;
+                        done = true;
+                    } else {
+                        tau = above;
+                    }
+                }
+                if (!done && ++steps >= 3) break;
+            }
+        }
+        if (!done) {
+            // bisection in [lo, hi], tightened to the keys present
+            key_t mn = KMAX, mx = 0;
+            for (int r = gl; r < R; r += G) {
+                const key_t v = col[r * RS];
+                if (v >= lo && v <= hi) { mn = v < mn ? v : mn; mx = v > mx ? v : mx; }
+            }
+            for (int j = gl; j < R; j += G) {
+                const key_t v = win[j];
+                if (v >= lo && v <= hi) { mn = v < mn ? v : mn; mx = v > mx ? v : mx; }
+            }
+            lo = grp_min(mask, G, mn);
+            hi = grp_max(mask, G, mx);
+            while (lo < hi) {
+                const key_t mid = lo + (key_t)((hi - lo) >> 1) + 1;
+                uint32_t c = 0;
+                for (int r = gl; r < R; r += G) c += col[r * RS] >= mid;
+                for (int j = gl; j < R; j += G) c += win[j] >= mid;
+                c = grp_add(mask, G, c);
+                if ((int)c >= kk) lo = mid; else hi = mid - 1;
+            }
+            tau = lo;
+        }
+        have = true;
+        if (gl == 0) out(p, tau);
     }
-    return lo;
 }
 
 template <typename real, int V>
@@ -151,9 +246,11 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     typedef KeyOf<real> K;
     typedef typename K::type key_t;
     const unsigned FULL = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int NT = G.NT, NW = G.NW;
-    const int R = A.R, ell = A.ell, m = A.m;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int NT = G.NT, NTc = G.NTc, NWc = G.NWc;
+    const int g = tid / NTc, t = tid % NTc, wc = t >> 5;  // row group, column thread, warp in group
+    const int R = A.R, ell = A.ell, m = A.m, Rg = G.Rg;
+    const int r0 = g * Rg;
     const int64_t p0 = (int64_t)tt * A.W;
     const int Wp = (int)((A.P - p0) < (int64_t)A.W ? (A.P - p0) : (int64_t)A.W);
     const int Wb = Wp + R - 1;
@@ -161,27 +258,27 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
 
     key_t* AB = (key_t*)(sm + G.off_AB);
     key_t* CB = (key_t*)(sm + G.off_CB);
-    real* PRE = (real*)(sm + G.off_PRE);
-    real* CM = (real*)(sm + G.off_CM);
-    real* XCH = (real*)(sm + G.off_XCH);  // [parity][hi/lo][warp]
+    real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * G.LP;  // this group's [parity][V][LP]
+    real* CM = (real*)(sm + G.off_CM) + (size_t)g * 2 * (NTc + 1);   // [parity][NTc + 1]
+    real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][hi/lo][warp]
     real* rdf = (real*)(sm + G.off_row);
     real* rdg = rdf + R;
     real* ra = rdg + R;
     real* rmu = ra + R;   // hi part of mu_i - refs
     real* rmul = rmu + R; // lo part
     real* lseed = (real*)(sm + G.off_left);
-    real* top = (real*)(sm + G.off_top);
+    real* top = (real*)(sm + G.off_top);  // [group][NTc * V] seeds, later the groups' column maxima
     real* Tc = (real*)(sm + G.off_Tc);    // T - refc as hi + lo pairs: exact to about
     real* Tcl = (real*)(sm + G.off_Tcl);  // twice the working precision
     real* Ts = (real*)(sm + G.off_Ts);
     real* Tsl = (real*)(sm + G.off_Tsl);
-    real* q = (real*)(sm + G.off_q);
+    real* q = (real*)(sm + G.off_q);      // [group][ell + 1] centred head of the group's first row
 
     // ---------------------------------------------------------------- stage
     const double refc = A.mu[p0];
     const double refs = A.mu[i0];
     const int nTc = Wb + ell - 1;
-    for (int y = tid; y < NT * V + ell + 64; y += NT) {
+    for (int y = tid; y < NTc * V + ell + 64; y += NT) {
         const double d = y < nTc ? A.T[p0 + y] - refc : 0.0;
         const real h = (real)d;
         Tc[y] = h;
@@ -201,14 +298,19 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         rmu[r] = (real)d;
         rmul[r] = (real)(d - (double)rmu[r]);
     }
-    for (int t = tid; t < ell; t += NT) q[t] = (real)(A.T[i0 + t] - A.mu[i0]);
+    for (int e = tid; e < G.NG * ell; e += NT) {
+        const int gg = e / ell, u = e - gg * ell;
+        const int64_t ig = i0 + (int64_t)gg * Rg;
+        q[gg * (ell + 1) + u] = (real)(A.T[ig + u] - A.mu[ig]);
+    }
     __syncthreads();
-    if (warp == 0) {  // sum of the rounded q, accumulated in FP64
+    if ((tid >> 5) < G.NG) {  // warp gg: sum of group gg's rounded q, in FP64
+        const int gg = tid >> 5;
         double acc = 0;
-        for (int t = lane; t < ell; t += 32) acc += (double)q[t];
+        for (int u = lane; u < ell; u += 32) acc += (double)q[gg * (ell + 1) + u];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (lane == 0) q[ell] = (real)acc;
+        if (lane == 0) q[gg * (ell + 1) + ell] = (real)acc;
     }
 
     // ---------------------------------------------------------------- seeds
@@ -218,23 +320,24 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     for (int r = 1 + tid; r < R; r += NT) {
         const real mh = rmu[r], ml = rmul[r];
         real acc = 0;
-        for (int t = 0; t < ell; ++t) acc += ((Ts[r + t] - mh) + (Tsl[r + t] - ml)) * (Tc[t] + Tcl[t]);
+        for (int u = 0; u < ell; ++u) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
         lseed[r] = acc;
     }
     __syncthreads();
-    // top row: cov(0, x) = sum_t q[t] * (T[x+t] - c) - (mu_x - c) * sum_t q[t] for any
-    // constant c (the centred q sums to 0 up to rounding, and its rounded sum is
-    // taken exactly).  c is the mean of each block's first column: the series
-    // values of a block are centred once, from their hi + lo parts, as they enter
-    // a sliding register window, so the products never carry the level of the
-    // series, only its local deviations.  Lane-contiguous blocks of 9 columns
-    // (odd stride: conflict-free sliding loads).
+    // first row of every group: cov(r0, x) = sum_t q[t] * (T[x+t] - c) - (mu_x - c) * sum_t q[t]
+    // for any constant c (the centred q sums to 0 up to rounding, and its rounded
+    // sum is taken exactly).  c is the mean of each block's first column: the
+    // series values of a block are centred once, from their hi + lo parts, as
+    // they enter a sliding register window, so the products never carry the
+    // level of the series, only its local deviations.  Lane-contiguous blocks of
+    // 9 columns (odd stride: conflict-free sliding loads).
     {
         constexpr int J = 9;
-        const int nblk = (NT * V + J - 1) / J;
-        const real sq = q[ell];
-        for (int b = tid; b < nblk; b += NT) {
-            const int x0 = b * J;
+        const int nblk = (NTc * V + J - 1) / J;
+        for (int b = tid; b < G.NG * nblk; b += NT) {
+            const int gg = b / nblk;
+            const int x0 = (b - gg * nblk) * J;
+            const real* qg = q + gg * (ell + 1);
             const double cb = x0 < Wb ? A.mu[p0 + x0] - refc : 0.0;
             const real cbh = (real)cb, cbl = (real)(cb - (double)cbh);
             real acc[J], win[J];
@@ -243,33 +346,35 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 acc[j] = 0;
                 win[j] = (Tc[x0 + j] - cbh) + (Tcl[x0 + j] - cbl);
             }
-            int t = 0;
-            for (; t + J <= ell; t += J) {
+            int u0 = 0;
+            for (; u0 + J <= ell; u0 += J) {
 #pragma unroll
                 for (int u = 0; u < J; ++u) {
-                    const real qt = q[t + u];
+                    const real qt = qg[u0 + u];
 #pragma unroll
                     for (int j = 0; j < J; ++j) acc[j] += qt * win[(j + u) % J];
-                    const int e = x0 + t + u + J;
+                    const int e = x0 + u0 + u + J;
                     win[u] = (Tc[e] - cbh) + (Tcl[e] - cbl);
                 }
             }
-            for (; t < ell; ++t) {
-                const real qt = q[t];
+            for (; u0 < ell; ++u0) {
+                const real qt = qg[u0];
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    const int e = x0 + t + j;
+                    const int e = x0 + u0 + j;
                     acc[j] += qt * ((Tc[e] - cbh) + (Tcl[e] - cbl));
                 }
             }
+            const real sq = qg[ell];
+            real* topg = top + (size_t)gg * NTc * V;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const int x = x0 + j;
                 if (x < Wb) {
                     const real dm = (real)(A.mu[p0 + x] - refc - cb);
-                    top[x] = acc[j] - dm * sq;
-                } else if (x < NT * V) {
-                    top[x] = 0;
+                    topg[x] = acc[j] - dm * sq;
+                } else if (x < NTc * V) {
+                    topg[x] = 0;
                 }
             }
         }
@@ -277,151 +382,187 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     __syncthreads();
 
     // ---------------------------------------------------------------- rows
-    const int xb = tid * V;
+    const int xb = t * V;
+    const real NEG = RealLimits<real>::lowest();
     real hi[V], lo[V], cmx[V], cdf[V], cdg[V], ca[V];
-    unsigned act = 0;
+    const bool partial_cols = xb + V > Wb;  // only the last column thread of a tile
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int x = xb + v;
-        if (x < Wb) {
-            cdf[v] = A.df[p0 + x];
-            cdg[v] = A.dg[p0 + x];
-            ca[v] = A.a[p0 + x];
-            act |= 1u << v;
-        } else {
-            cdf[v] = 0;
-            cdg[v] = 0;
-            ca[v] = 0;
-        }
-        hi[v] = top[x];
+        const bool in = x < Wb;
+        cdf[v] = in ? A.df[p0 + x] : (real)0;
+        cdg[v] = in ? A.dg[p0 + x] : (real)0;
+        ca[v] = in ? A.a[p0 + x] : (real)0;
+        hi[v] = top[(size_t)g * NTc * V + x];
         lo[v] = 0;
-        cmx[v] = RealLimits<real>::lowest();
+        cmx[v] = NEG;
     }
-    const real NEG = RealLimits<real>::lowest();
-    const int q0 = (R - 1) / V;  // chunk offset of the window end for i = 0
-    // column of this thread's first cell on the main diagonal i == j at row r
-    const int64_t xdiag0 = i0 - p0 - xb;
+    const int q0 = (R - 1) / V;       // chunk offset of the window end for i = 0
+    const bool small_R = R - 1 < V;   // some windows end inside their own chunk
+    const int xdiag0 = (int)(i0 - p0) - xb;  // column (relative to xb) where i == j at row 0
+    const bool owns_positions = xb < Wp;
+    const bool full_positions = xb + V <= Wp;
+    const int nrows = (r0 + Rg <= R ? Rg : R - r0);
 
-    for (int r = 0; r < R; ++r) {
-        const int par = r & 1;
-        real* PREp = PRE + par * V * G.LP;
-        real* CMp = CM + par * (NT + 1);
-        if (r > 0) {
-            // cov(r-1, x-1) of this thread's first column: the neighbour lane's last
-            // column, the previous warp's last column (lane 0), or, for tile column 0,
-            // no predecessor at all: there cov(r, 0) is the exact left-edge seed
-            real lhi = __shfl_up_sync(FULL, hi[V - 1], 1);
-            real llo = __shfl_up_sync(FULL, lo[V - 1], 1);
-            if (lane == 0 && warp > 0) {
-                lhi = XCH[((par ^ 1) * 2 + 0) * NW + warp - 1];
-                llo = XCH[((par ^ 1) * 2 + 1) * NW + warp - 1];
-            }
-            const real fr = rdf[r], gr = rdg[r];
+    for (int c0 = 0; c0 < Rg; c0 += V) {
 #pragma unroll
-            for (int v = V - 1; v >= 1; --v) {
-                hi[v] = hi[v - 1];
-                lo[v] = fr * cdg[v] + (cdf[v] * gr + lo[v - 1]);
-            }
-            if (tid == 0) {
-                hi[0] = lseed[r];
-                lo[0] = 0;
-            } else {
-                hi[0] = lhi;
-                lo[0] = fr * cdg[0] + (cdf[0] * gr + llo);
-            }
-            if (r % FOLD == 0) {
+        for (int jj = 0; jj < V; ++jj) {
+            const int sidx = c0 + jj;          // row step within the group
+            const int r = r0 + sidx;
+            const bool active = sidx < nrows;  // uniform within the group
+            const int par = sidx & 1;
+            real* PREp = PRE + par * V * G.LP;
+            real* CMp = CM + par * (NTc + 1);
+            // logical column v of this thread lives in register (v - jj) mod V
+            real rho[V];
+            if (active) {
+                if (sidx > 0) {
+                    const int Pout = (V - jj) % V;  // register of the previous row's last column
+                    real lhi = __shfl_up_sync(FULL, hi[Pout], 1);
+                    real llo = __shfl_up_sync(FULL, lo[Pout], 1);
+                    if (lane == 0 && wc > 0) {
+                        lhi = XCH[((par ^ 1) * 2 + 0) * NWc + wc - 1];
+                        llo = XCH[((par ^ 1) * 2 + 1) * NWc + wc - 1];
+                    }
+                    const real fr = rdf[r], gr = rdg[r];
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    hi[v] += lo[v];
-                    lo[v] = 0;
+                    for (int v = 1; v < V; ++v) {
+                        const int P = (v - jj + V) % V;
+                        lo[P] = fr * cdg[v] + (cdf[v] * gr + lo[P]);
+                    }
+                    if (t == 0) {
+                        hi[Pout] = lseed[r];
+                        lo[Pout] = 0;
+                    } else {
+                        hi[Pout] = lhi;
+                        lo[Pout] = fr * cdg[0] + (cdf[0] * gr + llo);
+                    }
+                }
+                if (lane == 31) {
+                    const int Plast = (V - 1 - jj + V) % V;
+                    XCH[(par * 2 + 0) * NWc + wc] = hi[Plast];
+                    XCH[(par * 2 + 1) * NWc + wc] = lo[Plast];
+                }
+                const real ar = ra[r];
+                if (ar != (real)0) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int P = (v - jj + V) % V;
+                        rho[v] = ((hi[P] + lo[P]) * ar) * ca[v];
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) rho[v] = ca[v] == (real)0 ? (real)1 : (real)0;
+                }
+                const unsigned xd = (unsigned)(xdiag0 + r);  // i == j: correlation 1 by definition
+                if (xd < (unsigned)V) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (v == (int)xd) rho[v] = (real)1;
+                }
+                if (partial_cols) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (xb + v >= Wb) rho[v] = NEG;
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) cmx[v] = rmax(cmx[v], rho[v]);
+                real pre = rho[0];
+                PREp[t] = pre;
+#pragma unroll
+                for (int v = 1; v < V; ++v) {
+                    pre = rmax(pre, rho[v]);
+                    PREp[v * G.LP + t] = pre;
+                }
+                CMp[t] = pre;
+                if (t == 0) CMp[NTc] = NEG;
+            }
+            __syncthreads();
+            if (active && owns_positions) {
+                real suf[V];
+                suf[V - 1] = rho[V - 1];
+#pragma unroll
+                for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
+                key_t* ABr = AB + (size_t)r * G.RS + t;
+                if (!small_R) {
+                    // whole chunks strictly inside the window: t+1 .. t+q0-1 for small i,
+                    // one more (t+q0) once the window end moves into chunk t+q0+1
+                    real mid = NEG;
+                    int c = t + 1;
+                    const int cend = t + q0;
+                    for (; c + 4 <= cend; c += 4) {
+                        const real a0 = CMp[c], a1 = CMp[c + 1], a2 = CMp[c + 2], a3 = CMp[c + 3];
+                        mid = rmax(mid, rmax(rmax(a0, a1), rmax(a2, a3)));
+                    }
+                    for (; c < cend; ++c) mid = rmax(mid, CMp[c]);
+                    const real mid1 = rmax(mid, CMp[t + q0]);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        const int e = i + R - 1;        // window end, relative to xb
+                        const int oi = e / V, si = e - oi * V;
+                        const real ab = rmax(rmax(suf[i], oi > q0 ? mid1 : mid), PREp[si * G.LP + t + oi]);
+                        if (full_positions || xb + i < Wp) ABr[i * G.LA] = K::enc(ab);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        real ab;
+                        if (i + R - 1 < V) {  // window inside this chunk
+                            ab = NEG;
+#pragma unroll
+                            for (int j = 0; j < V; ++j)
+                                if (j >= i && j < i + R) ab = rmax(ab, rho[j]);
+                        } else {
+                            const int e = i + R - 1;
+                            const int oi = e / V, si = e - oi * V;
+                            ab = rmax(suf[i], PREp[si * G.LP + t + oi]);
+                        }
+                        if (full_positions || xb + i < Wp) ABr[i * G.LA] = K::enc(ab);
+                    }
                 }
             }
         }
-        if (lane == 31) {
-            XCH[(par * 2 + 0) * NW + warp] = hi[V - 1];
-            XCH[(par * 2 + 1) * NW + warp] = lo[V - 1];
-        }
-        real rho[V];
-        const real ar = ra[r];
-        if (ar != (real)0) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) rho[v] = ((hi[v] + lo[v]) * ar) * ca[v];
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) rho[v] = ca[v] == (real)0 ? (real)1 : (real)0;
-        }
-        const int64_t xd = xdiag0 + r;  // i == j exactly: correlation 1 by definition
-        if (xd >= 0 && xd < V) {
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (v == (int)xd) rho[v] = (real)1;
-        }
+        // fold the small covariance term into the large one every V rows
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            if (!((act >> v) & 1u)) rho[v] = NEG;
-            cmx[v] = rmax(cmx[v], rho[v]);
-        }
-        real pre[V], suf[V];
-        pre[0] = rho[0];
-#pragma unroll
-        for (int v = 1; v < V; ++v) pre[v] = rmax(pre[v - 1], rho[v]);
-        suf[V - 1] = rho[V - 1];
-#pragma unroll
-        for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
-#pragma unroll
-        for (int v = 0; v < V; ++v) PREp[v * G.LP + tid] = pre[v];
-        CMp[tid] = pre[V - 1];
-        if (tid == 0) CMp[NT] = NEG;
-        __syncthreads();
-        // window maxima for the positions p = xb + i owned here
-        if (xb < Wp) {
-            // whole chunks strictly inside the window: tid+1 .. tid+q0-1 for small i,
-            // one more (tid+q0) once the window end moves into chunk tid+q0+1
-            real mid = NEG;
-            for (int c = tid + 1; c < tid + q0; ++c) mid = rmax(mid, CMp[c]);
-            const real mid1 = q0 >= 1 && tid + q0 <= NT ? rmax(mid, CMp[tid + q0]) : mid;
-#pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const int p = xb + i;
-                if (p < Wp) {
-                    real ab;
-                    if (i + R - 1 < V) {  // window inside this chunk (R < V only)
-                        ab = NEG;
-#pragma unroll
-                        for (int j = 0; j < V; ++j)
-                            if (j >= i && j < i + R) ab = rmax(ab, rho[j]);
-                    } else {
-                        const int e = p + R - 1;
-                        const int te = e / V;
-                        ab = rmax(suf[i], te > tid + q0 ? mid1 : mid);
-                        ab = rmax(ab, PREp[(e - te * V) * G.LP + te]);
-                    }
-                    AB[r * G.RS + i * G.LA + tid] = K::enc(ab);
-                }
-            }
+            hi[v] += lo[v];
+            lo[v] = 0;
         }
     }
+    // column maxima over all row groups
+    {
+        real* cmg = top + (size_t)g * NTc * V;
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const int x = xb + v;
-        if (x < Wb) CB[x] = K::enc(cmx[v]);
+        for (int v = 0; v < V; ++v) cmg[xb + v] = cmx[v];
+    }
+    __syncthreads();
+    for (int x = tid; x < Wb; x += NT) {
+        real mx = top[x];
+        for (int gg = 1; gg < G.NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
+        CB[x] = K::enc(mx);
     }
     __syncthreads();
 
     // ---------------------------------------------------------------- select
     const int kk = 2 * R > A.k ? A.k : 2 * R;
     const real two_ell = (real)(2 * ell);
+    // lanes per position stream: enough that each lane holds several of the 2R keys
+    const int GS = 2 * R >= 192 ? 32 : (2 * R >= 96 ? 16 : 8);
+    const int ngroups = NT / GS;
+    const int grp = tid / GS, gl = tid % GS;
+    const unsigned gmask = (GS == 32) ? FULL : (((1u << GS) - 1u) << ((lane / GS) * GS));
+    const int PW = (Wp + ngroups - 1) / ngroups;
+    const int pb = grp * PW, pe = pb + PW < Wp ? pb + PW : Wp;
     double tmax = 0.0;
-    for (int p = tid; p < Wp; p += NT) {
-        const int swp = (p % V) * G.LA + p / V;
-        const key_t kb = select_kth_bisect<key_t>(AB, G.RS, swp, CB, p, R, kk);
+    real* Drow = A.D + (int64_t)s * A.P + p0;
+    select_track<key_t>(AB, G.RS, G.LA, V, CB, R, kk, pb, pe, GS, gmask, gl, [&](int p, key_t kb) {
         const real rs = K::dec(kb);
         real u = (real)1 - rs;
         u = u > (real)0 ? u : (real)0;
         const real d = sqrt(two_ell * u);
-        A.D[(int64_t)s * A.P + p0 + p] = d;
+        Drow[p] = d;
         tmax = (double)d > tmax ? (double)d : tmax;
-    }
+    });
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double other = __shfl_xor_sync(FULL, tmax, o);
