@@ -121,122 +121,140 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
 template <typename real>
 __device__ __forceinline__ real rmax(real a, real b) { return a > b ? a : b; }
 
-// Group-wide reductions over G consecutive lanes (G = 8, 16 or 32; `mask`
-// holds exactly those lanes).
-__device__ __forceinline__ uint32_t grp_add(unsigned mask, int, uint32_t v) { return __reduce_add_sync(mask, v); }
-__device__ __forceinline__ uint32_t grp_min(unsigned mask, int, uint32_t v) { return __reduce_min_sync(mask, v); }
-__device__ __forceinline__ uint32_t grp_max(unsigned mask, int, uint32_t v) { return __reduce_max_sync(mask, v); }
-__device__ __forceinline__ unsigned long long grp_min(unsigned mask, int G, unsigned long long v) {
+// Reductions over the G lanes of a group (G = 8, 16 or 32 consecutive lanes;
+// every lane of the warp takes part, each group reduces its own values).
+template <typename T>
+__device__ __forceinline__ T grp_sum(T v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T grp_min(T v, int G) {
     for (int o = G >> 1; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(mask, v, o, G);
+        const T w = __shfl_xor_sync(0xffffffffu, v, o, G);
         v = w < v ? w : v;
     }
     return v;
 }
-__device__ __forceinline__ unsigned long long grp_max(unsigned mask, int G, unsigned long long v) {
+template <typename T>
+__device__ __forceinline__ T grp_max(T v, int G) {
     for (int o = G >> 1; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(mask, v, o, G);
+        const T w = __shfl_xor_sync(0xffffffffu, v, o, G);
         v = w > v ? w : v;
     }
     return v;
 }
 
-// k-th largest key (kk-th, 1-based) of P_ABBA for the positions p_begin .. p_end-1
-// of a tile, walked in order by one group of G lanes: lane gl of the group holds
-// rows gl, gl+G, ... of AB column p and the window entries CB[p+gl], CB[p+gl+G], ...
-// The first position is found by bisection over the key range; every later one
-// starts from the previous answer tau (consecutive positions share all but a
-// few of their 2R values, so the rank of tau moves little): one pass counts the
-// keys >= tau and > tau and finds the nearest keys below and above tau, which
-// settles the answer whenever its rank moved by at most one; otherwise tau steps
-// to that neighbour and the pass repeats, and after a few steps the search
-// falls back to bisection inside the bracket already known.
+constexpr int SEL_CACHE = 9;  // keys of one position held per lane, per half (rows, window)
+
+// k-th largest key (kk-th, 1-based) of P_ABBA for a run of consecutive tile
+// positions, one run per group of G lanes; all groups of a warp step through
+// their runs together (npos_warp steps; a group past its own run idles).  Lane
+// gl of a group holds rows gl, gl+G, ... of AB column p and the window entries
+// CB[p+gl], CB[p+gl+G], ... in registers.  The first position of a run is found
+// by bisection over the key range; every later one starts from the previous
+// answer tau (consecutive positions share all but a few of their 2R values, so
+// the rank of tau moves little): a pass counts the keys >= tau and > tau and
+// finds the nearest keys below and above tau, which settles the answer when its
+// rank moved by at most one; otherwise tau steps to that neighbour and the pass
+// repeats, and after three steps a bisection inside the bracket already known
+// finishes.  Control flow is uniform across the warp: decisions are per-group
+// selects, loops run while any group of the warp still works.
 template <typename key_t, typename Out>
 __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int RS, int LA, int V,
                                              const key_t* __restrict__ CB, int R, int kk, int p_begin,
-                                             int p_end, int G, unsigned mask, int gl, Out out) {
+                                             int npos, int npos_warp, int G, int gl, Out out) {
+    const unsigned FULL = 0xffffffffu;
     const key_t KMAX = ~(key_t)0;
+    const int nr = (R - gl + G - 1) / G;  // values per half held by this lane
     key_t tau = 0;
-    bool have = false;
-    for (int p = p_begin; p < p_end; ++p) {
-        const key_t* col = AB + (p % V) * LA + p / V;
-        const key_t* win = CB + p;
-        key_t lo = 0, hi = KMAX;  // answer in [lo, hi]
+    for (int it = 0; it < npos_warp; ++it) {
+        const bool valid = it < npos;
+        const int p = valid ? p_begin + it : 0;  // an idle group reads position 0
+        key_t va[SEL_CACHE], vb[SEL_CACHE];
+        {
+            const key_t* col = AB + (p % V) * LA + p / V + (size_t)gl * RS;
+            const key_t* win = CB + p + gl;
+#pragma unroll
+            for (int j = 0; j < SEL_CACHE; ++j) {
+                const bool in = j < nr;
+                va[j] = in ? col[(size_t)j * G * RS] : (key_t)0;
+                vb[j] = in ? win[j * G] : (key_t)0;
+            }
+        }
+        key_t lo = 0, hi = KMAX;
         bool done = false;
-        int steps = 0;
-        if (have) {
-            while (!done) {
-                uint32_t cge = 0, cgt = 0;
-                key_t xb = KMAX, ya = KMAX;  // tau-1-key (keys below), key-tau-1 (keys above)
-                for (int r = gl; r < R; r += G) {
-                    const key_t v = col[r * RS];
-                    cge += v >= tau;
-                    cgt += v > tau;
-                    const key_t x = tau - (key_t)1 - v, y = v - tau - (key_t)1;
-                    xb = x < xb ? x : xb;
-                    ya = y < ya ? y : ya;
-                }
-                for (int j = gl; j < R; j += G) {
-                    const key_t v = win[j];
-                    cge += v >= tau;
-                    cgt += v > tau;
-                    const key_t x = tau - (key_t)1 - v, y = v - tau - (key_t)1;
-                    xb = x < xb ? x : xb;
-                    ya = y < ya ? y : ya;
-                }
-                cge = grp_add(mask, G, cge);
-                cgt = grp_add(mask, G, cgt);
-                xb = grp_min(mask, G, xb);
-                ya = grp_min(mask, G, ya);
-                if ((int)cgt < kk && kk <= (int)cge) {
-                    done = true;  // tau is the answer
-                } else if ((int)cge < kk) {  // answer below tau: nearest key below exists
-                    const key_t below = tau - (key_t)1 - xb;
-                    hi = below;
-                    if ((int)cge == kk - 1) {
-                        tau = below;
-                        done = true;
-                    } else {
-                        tau = below;
-                    }
-                } else {  // cgt >= kk: answer above tau: nearest key above exists
-                    const key_t above = tau + (key_t)1 + ya;
-                    lo = above;
-                    if ((int)cgt == kk) {
-                        tau = above;
-                        done = true;
-                    } else {
-                        tau = above;
-                    }
-                }
-                if (!done && ++steps >= 3) break;
-            }
-        }
-        if (!done) {
-            // bisection in [lo, hi], tightened to the keys present
-            key_t mn = KMAX, mx = 0;
-            for (int r = gl; r < R; r += G) {
-                const key_t v = col[r * RS];
-                if (v >= lo && v <= hi) { mn = v < mn ? v : mn; mx = v > mx ? v : mx; }
-            }
-            for (int j = gl; j < R; j += G) {
-                const key_t v = win[j];
-                if (v >= lo && v <= hi) { mn = v < mn ? v : mn; mx = v > mx ? v : mx; }
-            }
-            lo = grp_min(mask, G, mn);
-            hi = grp_max(mask, G, mx);
-            while (lo < hi) {
-                const key_t mid = lo + (key_t)((hi - lo) >> 1) + 1;
+        if (it > 0) {
+            for (int step = 0; step < 3; ++step) {
                 uint32_t c = 0;
-                for (int r = gl; r < R; r += G) c += col[r * RS] >= mid;
-                for (int j = gl; j < R; j += G) c += win[j] >= mid;
-                c = grp_add(mask, G, c);
-                if ((int)c >= kk) lo = mid; else hi = mid - 1;
+                key_t xb = KMAX, ya = KMAX;
+#pragma unroll
+                for (int j = 0; j < SEL_CACHE; ++j) {
+                    if (j < nr) {
+                        const key_t a = va[j], b = vb[j];
+                        c += (a >= tau ? 1u : 0u) + (a > tau ? 65536u : 0u);
+                        c += (b >= tau ? 1u : 0u) + (b > tau ? 65536u : 0u);
+                        const key_t xa = tau - (key_t)1 - a, xb2 = tau - (key_t)1 - b;
+                        const key_t ya1 = a - tau - (key_t)1, yb = b - tau - (key_t)1;
+                        xb = xa < xb ? xa : xb;
+                        xb = xb2 < xb ? xb2 : xb;
+                        ya = ya1 < ya ? ya1 : ya;
+                        ya = yb < ya ? yb : ya;
+                    }
+                }
+                c = grp_sum(c, G);
+                xb = grp_min(xb, G);
+                ya = grp_min(ya, G);
+                const int cge = (int)(c & 0xffffu), cgt = (int)(c >> 16);
+                const bool res = cgt < kk && kk <= cge;
+                const bool down = cge < kk;
+                const key_t below = tau - (key_t)1 - xb, above = tau + (key_t)1 + ya;
+                if (!done) {
+                    if (res) {
+                        done = true;
+                    } else if (down) {
+                        hi = below;
+                        tau = below;
+                        done = cge == kk - 1;
+                    } else {
+                        lo = above;
+                        tau = above;
+                        done = cgt == kk;
+                    }
+                }
+                if (__all_sync(FULL, done)) break;
             }
-            tau = lo;
         }
-        have = true;
-        if (gl == 0) out(p, tau);
+        // bisection in [lo, hi] (the whole key range at a run's first position),
+        // tightened to the keys present
+        const bool need = !done;
+        if (__any_sync(FULL, need)) {
+            key_t mn = KMAX, mx = 0;
+#pragma unroll
+            for (int j = 0; j < SEL_CACHE; ++j) {
+                if (j < nr) {
+                    const key_t a = va[j], b = vb[j];
+                    if (a >= lo && a <= hi) { mn = a < mn ? a : mn; mx = a > mx ? a : mx; }
+                    if (b >= lo && b <= hi) { mn = b < mn ? b : mn; mx = b > mx ? b : mx; }
+                }
+            }
+            mn = grp_min(mn, G);
+            mx = grp_max(mx, G);
+            key_t blo = need ? mn : tau, bhi = need ? mx : tau;
+            while (__any_sync(FULL, blo < bhi)) {
+                const key_t mid = blo + (key_t)((bhi - blo) >> 1) + 1;
+                uint32_t c = 0;
+#pragma unroll
+                for (int j = 0; j < SEL_CACHE; ++j)
+                    if (j < nr) c += (va[j] >= mid ? 1u : 0u) + (vb[j] >= mid ? 1u : 0u);
+                c = grp_sum(c, G);
+                if (blo < bhi) {
+                    if ((int)c >= kk) blo = mid; else bhi = mid - 1;
+                }
+            }
+            tau = blo;
+        }
+        if (valid && gl == 0) out(p, tau);
     }
 }
 
@@ -546,16 +564,16 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // ---------------------------------------------------------------- select
     const int kk = 2 * R > A.k ? A.k : 2 * R;
     const real two_ell = (real)(2 * ell);
-    // lanes per position stream: enough that each lane holds several of the 2R keys
-    const int GS = 2 * R >= 192 ? 32 : (2 * R >= 96 ? 16 : 8);
+    // lanes per position run: each lane caches at most SEL_CACHE keys of each half
+    const int GS = R <= 8 * SEL_CACHE ? 8 : (R <= 16 * SEL_CACHE ? 16 : 32);
     const int ngroups = NT / GS;
     const int grp = tid / GS, gl = tid % GS;
-    const unsigned gmask = (GS == 32) ? FULL : (((1u << GS) - 1u) << ((lane / GS) * GS));
     const int PW = (Wp + ngroups - 1) / ngroups;
-    const int pb = grp * PW, pe = pb + PW < Wp ? pb + PW : Wp;
+    const int pb = grp * PW;
+    const int npos = pb >= Wp ? 0 : (pb + PW <= Wp ? PW : Wp - pb);
     double tmax = 0.0;
     real* Drow = A.D + (int64_t)s * A.P + p0;
-    select_track<key_t>(AB, G.RS, G.LA, V, CB, R, kk, pb, pe, GS, gmask, gl, [&](int p, key_t kb) {
+    select_track<key_t>(AB, G.RS, G.LA, V, CB, R, kk, pb, npos, PW, GS, gl, [&](int p, key_t kb) {
         const real rs = K::dec(kb);
         real u = (real)1 - rs;
         u = u > (real)0 ? u : (real)0;
