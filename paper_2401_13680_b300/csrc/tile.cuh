@@ -121,11 +121,33 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
 template <typename real>
 __device__ __forceinline__ real rmax(real a, real b) { return a > b ? a : b; }
 
-// Reductions over the G lanes of a group (G = 8, 16 or 32 consecutive lanes;
+// Reductions over the G lanes of a group (G = 4, 8, 16 or 32 consecutive lanes;
 // every lane of the warp takes part, each group reduces its own values).
 template <typename T>
 __device__ __forceinline__ T grp_sum(T v, int G) {
     for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+    return v;
+}
+// whole-warp groups: one redux.sync instead of a shuffle tree (32-bit values)
+__device__ __forceinline__ uint32_t grp_sum(uint32_t v, int G) {
+    if (G == 32) return __reduce_add_sync(0xffffffffu, v);
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+    return v;
+}
+__device__ __forceinline__ uint32_t grp_min(uint32_t v, int G) {
+    if (G == 32) return __reduce_min_sync(0xffffffffu, v);
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const uint32_t w = __shfl_xor_sync(0xffffffffu, v, o, G);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ uint32_t grp_max(uint32_t v, int G) {
+    if (G == 32) return __reduce_max_sync(0xffffffffu, v);
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const uint32_t w = __shfl_xor_sync(0xffffffffu, v, o, G);
+        v = w > v ? w : v;
+    }
     return v;
 }
 template <typename T>
@@ -565,7 +587,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int kk = 2 * R > A.k ? A.k : 2 * R;
     const real two_ell = (real)(2 * ell);
     // lanes per position run: each lane caches at most SEL_CACHE keys of each half
-    const int GS = R <= 8 * SEL_CACHE ? 8 : (R <= 16 * SEL_CACHE ? 16 : 32);
+    const int GS = R <= 4 * SEL_CACHE ? 4 : (R <= 8 * SEL_CACHE ? 8 : (R <= 16 * SEL_CACHE ? 16 : 32));
     const int ngroups = NT / GS;
     const int grp = tid / GS, gl = tid % GS;
     const int PW = (Wp + ngroups - 1) / ngroups;
