@@ -249,18 +249,20 @@ def run_ours(args):
     e2e = {"value": world * prof_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
 
-    # ---- roofline of the dominant kernel (profile tiles), from its own events
-    ed_alg_per_launch = ed_cells / len(ms)
-    tile_avg_s = (tile_ms / 1e3) / max(tile_launches, 1)
-    achieved = FLOP_PER_ED_CELL * ed_alg_per_launch / tile_avg_s / 1e12
+    # ---- roofline of the dominant kernel (profile tiles), from its own events:
+    # the algorithmic ED cells (S x R x C per length) of all timed launches over
+    # their summed device time
+    tile_s = tile_ms / 1e3
+    achieved = FLOP_PER_ED_CELL * ed_cells * args.steps / tile_s / 1e12
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "profile_tiles_kernel<float,8>",
+                "kernel": "batched_tiles_kernel<float,8> (one launch per step: every length of the sweep)",
                 "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (max SM clock), derived",
-                "ed_cells_per_s": ed_alg_per_launch / tile_avg_s,
-                "tile_share_of_step": (tile_ms / 1e3) / tot_s if world == 1 else None,
-                "halo_factor": tile_cells_halo / (ed_alg_per_launch * max(tile_launches, 1))}
+                "launches": tile_launches, "avg_launch_ms": tile_ms / max(tile_launches, 1),
+                "ed_cells_per_s": ed_cells * args.steps / tile_s,
+                "tile_share_of_step": tile_s / tot_s if world == 1 else None,
+                "halo_factor": tile_cells_halo / (ed_cells * args.steps)}
 
     # ---- the plain FP64 one-job GPU path on the same workload (one step)
     fp64 = None

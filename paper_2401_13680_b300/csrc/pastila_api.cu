@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/pastila.h"
+#include "batch.cuh"
 #include "keys.cuh"
 #include "snippets.cuh"
 #include "stats.cuh"
@@ -86,6 +87,18 @@ struct pastila_series {
     double tile_cells = 0.0;
     std::map<int, Stats> stats;
     std::map<std::string, Buf> bufs;
+    uint64_t alloc_gen = 0;  // bumped whenever a device buffer is (re)allocated
+    // captured select_length sequence, replayed while the configuration and the
+    // buffers it references stay the same
+    struct {
+        std::vector<int32_t> ms;
+        pastila_mparams rule{0, 0};
+        int K = 0;
+        uint64_t gen = ~0ull;
+        cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // statistics, tiles, snippets
+        int calls = 0;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the tile graph, while timing is on
+    } graph;
 };
 
 namespace {
@@ -103,6 +116,7 @@ pastila_status dev_alloc(pastila_series* h, void** p, size_t bytes) {
     }
     if (e != cudaSuccess) return fail(PASTILA_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
     h->held += bytes;
+    h->alloc_gen++;
     return PASTILA_OK;
 }
 
@@ -388,6 +402,259 @@ pastila_status read_snippets(pastila_series* h, int K, pastila_snippet* out) {
     return PASTILA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The whole length sweep of select_length in batched launches (FP32 handles):
+// statistics for every distinct ell, one tile launch for all lengths, the greedy
+// steps, the eq. 18 criterion and m_best, and the eq. 8 records of m_best, with
+// no host synchronisation in between (so the sequence can be captured in a CUDA
+// graph and replayed).
+// ---------------------------------------------------------------------------
+struct SweepBufs {
+    void* items = nullptr;
+    void* best = nullptr;
+    void* counts = nullptr;
+    void* rec_index = nullptr;
+    void* rec_rank = nullptr;
+    void* rec_frac = nullptr;
+    void* rec_area = nullptr;
+    void* crit = nullptr;
+};
+
+inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename real, int V>
+pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs, int K, SweepBufs* sb,
+                               std::vector<BatchItem<real>>* items_out, int* block_out, size_t* smem_out,
+                               long long* ctas_out, int64_t* maxS_out, int64_t* maxP_out) {
+    const int n = (int)qs.size();
+    std::vector<TileGeom> geo(n);
+    int block = 0;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        TRY(choose_tile<real, V>(h, qs[i], &geo[i]));
+        block = geo[i].NT > block ? geo[i].NT : block;
+        smem = geo[i].bytes > smem ? geo[i].bytes : smem;
+    }
+    // one region for every item's D, curve and small arrays
+    size_t dbytes = 0, sbytes = 0;
+    for (int i = 0; i < n; ++i) {
+        dbytes += up256(sizeof(real) * (size_t)qs[i].S * (size_t)qs[i].P);
+        sbytes += up256(sizeof(real) * (size_t)qs[i].P) + up256(8 * (size_t)qs[i].S) + up256(4 * 64) +
+                  up256(8 * 64) + up256(8 * CRIT_BLOCKS) + up256(8) + up256(8);
+    }
+    void *dreg, *sreg;
+    TRY(scratch(h, "sweep_D", dbytes, &dreg));
+    TRY(scratch(h, "sweep_small", sbytes, &sreg));
+    TRY(scratch(h, "sweep_items", sizeof(BatchItem<real>) * (size_t)n, &sb->items));
+    TRY(scratch(h, "sweep_best", 16, &sb->best));
+    TRY(scratch(h, "sweep_counts", 8 * 64, &sb->counts));
+    TRY(scratch(h, "sweep_rec_index", 4 * 64, &sb->rec_index));
+    TRY(scratch(h, "sweep_rec_rank", 4 * 64, &sb->rec_rank));
+    TRY(scratch(h, "sweep_rec_frac", 8 * 64, &sb->rec_frac));
+    TRY(scratch(h, "sweep_rec_area", 8 * 64, &sb->rec_area));
+    std::vector<Stats*> st(n);
+    for (int i = 0; i < n; ++i) TRY(ensure_stats(h, qs[i].ell, &st[i]));
+    std::vector<BatchItem<real>>& items = *items_out;
+    items.assign(n, BatchItem<real>{});
+    char* dp = (char*)dreg;
+    char* sp = (char*)sreg;
+    long long cta = 0;
+    int64_t maxS = 0, maxP = 0;
+    for (int i = 0; i < n; ++i) {
+        const MParams& q = qs[i];
+        BatchItem<real>& it = items[i];
+        ProfileArgs<real>& A = it.A;
+        A.T = h->T;
+        A.mu = st[i]->mu;
+        A.a = (const real*)st[i]->a;
+        A.df = (const real*)st[i]->df;
+        A.dg = (const real*)st[i]->dg;
+        A.n = h->n;
+        A.C = q.C;
+        A.P = q.P;
+        A.m = q.m;
+        A.ell = q.ell;
+        A.k = q.k;
+        A.R = q.R;
+        A.S = q.S;
+        A.W = geo[i].W;
+        A.ntiles = (int)((q.P + geo[i].W - 1) / geo[i].W);
+        A.D = (real*)dp;
+        dp += up256(sizeof(real) * (size_t)q.S * (size_t)q.P);
+        it.G = geo[i];
+        it.cta_begin = cta;
+        cta += (long long)q.S * A.ntiles;
+        it.M = (real*)sp;
+        sp += up256(sizeof(real) * (size_t)q.P);
+        it.area = (double*)sp;
+        sp += up256(8 * (size_t)q.S);
+        it.chosen = (int32_t*)sp;
+        sp += up256(4 * 64);
+        it.area_after = (double*)sp;
+        sp += up256(8 * 64);
+        it.crit_part = (double*)sp;
+        sp += up256(8 * CRIT_BLOCKS);
+        it.crit = (double*)sp;
+        sp += up256(8);
+        A.dmax_key = (unsigned long long*)sp;
+        sp += up256(8);
+        it.K = K;
+        maxS = q.S > maxS ? q.S : maxS;
+        maxP = q.P > maxP ? q.P : maxP;
+    }
+    *block_out = block;
+    *smem_out = smem;
+    *ctas_out = cta;
+    *maxS_out = maxS;
+    *maxP_out = maxP;
+    return PASTILA_OK;
+}
+
+// The launches of one sweep on the handle's stream.  Statistics are recomputed
+// for every distinct ell (the series may have been reloaded).
+// phase 0: statistics and D-max reset; phase 1: the tile launch; phase 2: the
+// greedy steps, the criterion, m_best and its eq. 8 records
+template <typename real, int V>
+pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs, int K, const SweepBufs& sb,
+                               int block, size_t smem, long long ctas, int64_t maxS, int64_t maxP, int phase) {
+    const int n = (int)qs.size();
+    const BatchItem<real>* items = (const BatchItem<real>*)sb.items;
+    if (phase == 1) {
+        CK(cudaFuncSetAttribute(batched_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+        batched_tiles_kernel<real, V><<<(unsigned)ctas, block, smem, h->stream>>>(items, n);
+        CK(cudaGetLastError());
+        h->launches += 1;
+        return PASTILA_OK;
+    }
+    if (phase == 2) {
+        const unsigned pb = (unsigned)((maxP + 255) / 256);
+        for (int t = 0; t < K; ++t) {
+            batched_area_kernel<real><<<dim3((unsigned)maxS, n), AREA_THREADS, 0, h->stream>>>(items, t);
+            batched_argmin_kernel<real><<<n, 1024, 0, h->stream>>>(items, t);
+            if (t + 1 < K) batched_update_kernel<real><<<dim3(pb, n), 256, 0, h->stream>>>(items, t);
+        }
+        batched_criterion_kernel<real><<<dim3(CRIT_BLOCKS, n), AREA_THREADS, 0, h->stream>>>(items);
+        batched_finish_kernel<real><<<1, 256, 0, h->stream>>>(items, n, (int32_t*)sb.best);
+        CK(cudaMemsetAsync(sb.counts, 0, 8 * 64, h->stream));
+        batched_neighbors_kernel<real><<<pb, 256, 0, h->stream>>>(items, (const int32_t*)sb.best, nullptr,
+                                                                  (unsigned long long*)sb.counts);
+        batched_records_kernel<real><<<1, 1, 0, h->stream>>>(items, (const int32_t*)sb.best,
+                                                             (const unsigned long long*)sb.counts,
+                                                             (int32_t*)sb.rec_index, (int32_t*)sb.rec_rank,
+                                                             (double*)sb.rec_frac, (double*)sb.rec_area);
+        CK(cudaGetLastError());
+        h->launches += 3 * K - 1 + 4;
+        return PASTILA_OK;
+    }
+    std::vector<int> done_ell;
+    for (int i = 0; i < n; ++i) {
+        bool seen = false;
+        for (int e : done_ell) seen |= e == qs[i].ell;
+        if (seen) continue;
+        done_ell.push_back(qs[i].ell);
+        h->stats[qs[i].ell].stale = true;
+        Stats* st;
+        TRY(ensure_stats(h, qs[i].ell, &st));
+    }
+    batched_init_dmax_kernel<real><<<1, 64, 0, h->stream>>>(items, n);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    return PASTILA_OK;
+}
+
+// select_length on FP32 handles: batched, captured into a CUDA graph on the
+// second call with the same configuration and replayed from then on.
+template <typename real, int V>
+pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list, int n_m, pastila_mparams rule,
+                                       const std::vector<MParams>& qs, int K, int32_t* m_best, double* crit_out,
+                                       pastila_snippet* best_out) {
+    SweepBufs sb;
+    std::vector<BatchItem<real>> items;
+    int block;
+    size_t smem;
+    long long ctas;
+    int64_t maxS, maxP;
+    TRY(sweep_prepare_t<real, V>(h, qs, K, &sb, &items, &block, &smem, &ctas, &maxS, &maxP));
+    CK(cudaMemcpyAsync(sb.items, items.data(), sizeof(BatchItem<real>) * items.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    auto& gr = h->graph;
+    double cells = 0.0;  // ED cells of the tile launch, halo columns included
+    for (int i = 0; i < n_m; ++i) {
+        const TileGeom& g = items[i].G;
+        cells += (double)qs[i].S * (double)items[i].A.ntiles * (double)qs[i].R * (double)g.Wb;
+    }
+    const bool same = gr.ms == std::vector<int32_t>(m_list, m_list + n_m) && gr.rule.ell == rule.ell &&
+                      gr.rule.k == rule.k && gr.K == K && gr.gen == h->alloc_gen;
+    if (!same) {
+        for (auto& e : gr.exec)
+            if (e) cudaGraphExecDestroy(e);
+        gr.exec[0] = gr.exec[1] = gr.exec[2] = nullptr;
+        gr.ms.assign(m_list, m_list + n_m);
+        gr.rule = rule;
+        gr.K = K;
+        gr.gen = h->alloc_gen;
+        gr.calls = 0;
+    }
+    gr.calls++;
+    if (!gr.ev0) {
+        CK(cudaEventCreate(&gr.ev0));
+        CK(cudaEventCreate(&gr.ev1));
+    }
+    if (!gr.exec[0] && gr.calls >= 2) {  // capture the three phases
+        const uint64_t l0 = h->launches;
+        for (int ph = 0; ph < 3; ++ph) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            pastila_status st = sweep_enqueue_t<real, V>(h, qs, K, sb, block, smem, ctas, maxS, maxP, ph);
+            cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+            if (st != PASTILA_OK) return st;
+            if (ec != cudaSuccess) return fail(PASTILA_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+            cudaError_t ei = cudaGraphInstantiate(&gr.exec[ph], graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) return fail(PASTILA_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+        }
+        h->launches = l0;
+        gr.gen = h->alloc_gen;
+    }
+    const uint64_t l_before = h->launches;
+    for (int ph = 0; ph < 3; ++ph) {
+        if (ph == 1 && h->timing) CK(cudaEventRecord(gr.ev0, h->stream));
+        if (gr.exec[ph]) {
+            CK(cudaGraphLaunch(gr.exec[ph], h->stream));
+        } else {
+            TRY(sweep_enqueue_t<real, V>(h, qs, K, sb, block, smem, ctas, maxS, maxP, ph));
+        }
+        if (ph == 1 && h->timing) CK(cudaEventRecord(gr.ev1, h->stream));
+    }
+    if (gr.exec[0]) h->launches = l_before + 2 * (uint64_t)n_m + 1 + 1 + 3 * K - 1 + 4;
+    gr.gen = h->alloc_gen;
+    int32_t b = 0;
+    std::vector<double> cv(n_m);
+    std::vector<int32_t> ri(K), rr(K);
+    std::vector<double> rf(K), ra(K);
+    CK(cudaMemcpyAsync(&b, sb.best, 4, cudaMemcpyDeviceToHost, h->stream));
+    for (int i = 0; i < n_m; ++i)
+        CK(cudaMemcpyAsync(&cv[i], items[i].crit, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(ri.data(), sb.rec_index, 4 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(rr.data(), sb.rec_rank, 4 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(rf.data(), sb.rec_frac, 8 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(ra.data(), sb.rec_area, 8 * K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->timing) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, gr.ev0, gr.ev1));
+        h->tile_ms += ms;
+        h->tile_launches += 1;
+        h->tile_cells += cells;
+    }
+    *m_best = m_list[b];
+    if (crit_out) memcpy(crit_out, cv.data(), 8 * (size_t)n_m);
+    if (best_out)
+        for (int i = 0; i < K; ++i) best_out[i] = pastila_snippet{ri[i], rr[i], rf[i], ra[i]};
+    return PASTILA_OK;
+}
+
 pastila_status create_common(pastila_series** out, int64_t n, int device, size_t budget,
                              pastila_precision prec, cudaStream_t stream, pastila_series** hp) {
     if (!out) return fail(PASTILA_EINVAL, "out is NULL");
@@ -502,6 +769,10 @@ void pastila_destroy(pastila_series* h) {
         cudaEventDestroy(pr.second);
     }
     for (auto e : h->ev_free) cudaEventDestroy(e);
+    for (auto& e : h->graph.exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (h->graph.ev0) cudaEventDestroy(h->graph.ev0);
+    if (h->graph.ev1) cudaEventDestroy(h->graph.ev1);
     for (auto& kv : h->stats) {
         cudaFree(kv.second.mu);
         cudaFree(kv.second.a);
@@ -626,6 +897,9 @@ pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, i
     if (K < 2 || K > min_S || K > 64)
         return fail(PASTILA_EINVAL, "K = %d: must satisfy 2 <= K <= min(n / max m, 64) = %d", K,
                     min_S < 64 ? min_S : 64);
+    if (h->prec == PASTILA_FP32)
+        return select_length_batched_t<float, V_F32>(h, m_list, n_m, rule, qs, K, m_best, crit_out, best_out);
+    // FP64: the plain path, one length after the other
     const size_t rs = real_size(h);
     void *crit, *ms, *bi, *dk;
     TRY(scratch(h, "sel_crit", 8 * (size_t)n_m, &crit));

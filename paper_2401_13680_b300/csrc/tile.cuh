@@ -287,8 +287,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     typedef typename K::type key_t;
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int NT = G.NT, NTc = G.NTc, NWc = G.NWc;
-    const int g = tid / NTc, t = tid % NTc, wc = t >> 5;  // row group, column thread, warp in group
+    // a CTA may have more threads than the tile's layout uses (a batched launch
+    // sized for its largest item): threads past G.NT only stage data and select
+    const int BD = blockDim.x;
+    const bool worker = tid < G.NT;
+    const int NTc = G.NTc, NWc = G.NWc;
+    const int RS = G.RS, LA = G.LA, LP = G.LP, NG = G.NG;  // read once: hot loops use registers
+    const int g = worker ? tid / NTc : 0, t = tid % NTc, wc = t >> 5;  // row group, column thread, warp in group
     const int R = A.R, ell = A.ell, m = A.m, Rg = G.Rg;
     const int r0 = g * Rg;
     const int64_t p0 = (int64_t)tt * A.W;
@@ -298,7 +303,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
 
     key_t* AB = (key_t*)(sm + G.off_AB);
     key_t* CB = (key_t*)(sm + G.off_CB);
-    real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * G.LP;  // this group's [parity][V][LP]
+    real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * LP;  // this group's [parity][V][LP]
     real* CM = (real*)(sm + G.off_CM) + (size_t)g * 2 * (NTc + 1);   // [parity][NTc + 1]
     real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][hi/lo][warp]
     real* rdf = (real*)(sm + G.off_row);
@@ -318,19 +323,19 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const double refc = A.mu[p0];
     const double refs = A.mu[i0];
     const int nTc = Wb + ell - 1;
-    for (int y = tid; y < NTc * V + ell + 64; y += NT) {
+    for (int y = tid; y < NTc * V + ell + 64; y += BD) {
         const double d = y < nTc ? A.T[p0 + y] - refc : 0.0;
         const real h = (real)d;
         Tc[y] = h;
         Tcl[y] = (real)(d - (double)h);
     }
-    for (int u = tid; u < m; u += NT) {
+    for (int u = tid; u < m; u += BD) {
         const double d = A.T[i0 + u] - refs;
         const real h = (real)d;
         Ts[u] = h;
         Tsl[u] = (real)(d - (double)h);
     }
-    for (int r = tid; r < R; r += NT) {
+    for (int r = tid; r < R; r += BD) {
         rdf[r] = A.df[i0 + r];
         rdg[r] = A.dg[i0 + r];
         ra[r] = A.a[i0 + r];
@@ -338,13 +343,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         rmu[r] = (real)d;
         rmul[r] = (real)(d - (double)rmu[r]);
     }
-    for (int e = tid; e < G.NG * ell; e += NT) {
+    for (int e = tid; e < NG * ell; e += BD) {
         const int gg = e / ell, u = e - gg * ell;
         const int64_t ig = i0 + (int64_t)gg * Rg;
         q[gg * (ell + 1) + u] = (real)(A.T[ig + u] - A.mu[ig]);
     }
     __syncthreads();
-    if ((tid >> 5) < G.NG) {  // warp gg: sum of group gg's rounded q, in FP64
+    if ((tid >> 5) < NG) {  // warp gg: sum of group gg's rounded q, in FP64
         const int gg = tid >> 5;
         double acc = 0;
         for (int u = lane; u < ell; u += 32) acc += (double)q[gg * (ell + 1) + u];
@@ -357,7 +362,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0); the row
     // values are centred term by term from their hi + lo parts, and mu of
     // column 0 is the reference of Tc
-    for (int r = 1 + tid; r < R; r += NT) {
+    for (int r = 1 + tid; r < R; r += BD) {
         const real mh = rmu[r], ml = rmul[r];
         real acc = 0;
         for (int u = 0; u < ell; ++u) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
@@ -374,7 +379,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     {
         constexpr int J = 9;
         const int nblk = (NTc * V + J - 1) / J;
-        for (int b = tid; b < G.NG * nblk; b += NT) {
+        for (int b = tid; b < NG * nblk; b += BD) {
             const int gg = b / nblk;
             const int x0 = (b - gg * nblk) * J;
             const real* qg = q + gg * (ell + 1);
@@ -433,16 +438,16 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         cdf[v] = in ? A.df[p0 + x] : (real)0;
         cdg[v] = in ? A.dg[p0 + x] : (real)0;
         ca[v] = in ? A.a[p0 + x] : (real)0;
-        hi[v] = top[(size_t)g * NTc * V + x];
+        hi[v] = worker ? top[(size_t)g * NTc * V + x] : (real)0;
         lo[v] = 0;
         cmx[v] = NEG;
     }
     const int q0 = (R - 1) / V;       // chunk offset of the window end for i = 0
     const bool small_R = R - 1 < V;   // some windows end inside their own chunk
     const int xdiag0 = (int)(i0 - p0) - xb;  // column (relative to xb) where i == j at row 0
-    const bool owns_positions = xb < Wp;
+    const bool owns_positions = worker && xb < Wp;
     const bool full_positions = xb + V <= Wp;
-    const int nrows = (r0 + Rg <= R ? Rg : R - r0);
+    const int nrows = !worker ? 0 : (r0 + Rg <= R ? Rg : R - r0);
 
     for (int c0 = 0; c0 < Rg; c0 += V) {
 #pragma unroll
@@ -451,7 +456,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             const int r = r0 + sidx;
             const bool active = sidx < nrows;  // uniform within the group
             const int par = sidx & 1;
-            real* PREp = PRE + par * V * G.LP;
+            real* PREp = PRE + par * V * LP;
             real* CMp = CM + par * (NTc + 1);
             // logical column v of this thread lives in register (v - jj) mod V
             real rho[V];
@@ -512,7 +517,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
 #pragma unroll
                 for (int v = 1; v < V; ++v) {
                     pre = rmax(pre, rho[v]);
-                    PREp[v * G.LP + t] = pre;
+                    PREp[v * LP + t] = pre;
                 }
                 CMp[t] = pre;
                 if (t == 0) CMp[NTc] = NEG;
@@ -523,7 +528,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 suf[V - 1] = rho[V - 1];
 #pragma unroll
                 for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
-                key_t* ABr = AB + (size_t)r * G.RS + t;
+                key_t* ABr = AB + (size_t)r * RS + t;
                 if (!small_R) {
                     // whole chunks strictly inside the window: t+1 .. t+q0-1 for small i,
                     // one more (t+q0) once the window end moves into chunk t+q0+1
@@ -540,8 +545,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     for (int i = 0; i < V; ++i) {
                         const int e = i + R - 1;        // window end, relative to xb
                         const int oi = e / V, si = e - oi * V;
-                        const real ab = rmax(rmax(suf[i], oi > q0 ? mid1 : mid), PREp[si * G.LP + t + oi]);
-                        if (full_positions || xb + i < Wp) ABr[i * G.LA] = K::enc(ab);
+                        const real ab = rmax(rmax(suf[i], oi > q0 ? mid1 : mid), PREp[si * LP + t + oi]);
+                        if (full_positions || xb + i < Wp) ABr[i * LA] = K::enc(ab);
                     }
                 } else {
 #pragma unroll
@@ -555,9 +560,9 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                         } else {
                             const int e = i + R - 1;
                             const int oi = e / V, si = e - oi * V;
-                            ab = rmax(suf[i], PREp[si * G.LP + t + oi]);
+                            ab = rmax(suf[i], PREp[si * LP + t + oi]);
                         }
-                        if (full_positions || xb + i < Wp) ABr[i * G.LA] = K::enc(ab);
+                        if (full_positions || xb + i < Wp) ABr[i * LA] = K::enc(ab);
                     }
                 }
             }
@@ -572,13 +577,15 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // column maxima over all row groups
     {
         real* cmg = top + (size_t)g * NTc * V;
+        if (worker) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) cmg[xb + v] = cmx[v];
+            for (int v = 0; v < V; ++v) cmg[xb + v] = cmx[v];
+        }
     }
     __syncthreads();
-    for (int x = tid; x < Wb; x += NT) {
+    for (int x = tid; x < Wb; x += BD) {
         real mx = top[x];
-        for (int gg = 1; gg < G.NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
+        for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
         CB[x] = K::enc(mx);
     }
     __syncthreads();
@@ -588,14 +595,14 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const real two_ell = (real)(2 * ell);
     // lanes per position run: each lane caches at most SEL_CACHE keys of each half
     const int GS = R <= 4 * SEL_CACHE ? 4 : (R <= 8 * SEL_CACHE ? 8 : (R <= 16 * SEL_CACHE ? 16 : 32));
-    const int ngroups = NT / GS;
+    const int ngroups = BD / GS;
     const int grp = tid / GS, gl = tid % GS;
     const int PW = (Wp + ngroups - 1) / ngroups;
     const int pb = grp * PW;
     const int npos = pb >= Wp ? 0 : (pb + PW <= Wp ? PW : Wp - pb);
     double tmax = 0.0;
     real* Drow = A.D + (int64_t)s * A.P + p0;
-    select_track<key_t>(AB, G.RS, G.LA, V, CB, R, kk, pb, npos, PW, GS, gl, [&](int p, key_t kb) {
+    select_track<key_t>(AB, RS, LA, V, CB, R, kk, pb, npos, PW, GS, gl, [&](int p, key_t kb) {
         const real rs = K::dec(kb);
         real u = (real)1 - rs;
         u = u > (real)0 ? u : (real)0;

@@ -227,3 +227,30 @@ def test_sweep_full_size_sampled_cells(lib):
             assert_profiles_close(D[segs, pos], ref, ell, TOL[0])
             assert np.all(D >= 0) and np.all(D <= 2 * np.sqrt(ell) * (1 + 1e-6))
             assert dmax == pytest.approx(float(D.max()), rel=1e-7)
+
+
+def test_select_length_batched_graph_replay(lib):
+    """FP32 select_length runs every length in batched launches, is captured in a
+    CUDA graph on its second call and replayed after: three calls agree bit for
+    bit; each criterion equals eq. 18 evaluated (oracle) on the GPU's own
+    profiles and greedy choice; a reload with other values replays correctly."""
+    s = synth.four_regimes(per_regime=768)
+    ms = [48, 64, 96, 128]
+    K = 3
+    from paper_2401_13680_b300 import pastila
+    with _series(s.T, 0) as h:
+        runs = [h.select_length(ms, K) for _ in range(3)]
+        for r in runs[1:]:
+            assert r[0] == runs[0][0] and np.array_equal(r[1], runs[0][1]) and r[2] == runs[0][2]
+        for i, m in enumerate(ms):
+            D, _ = h.profiles(m)
+            Dd = D.astype(np.float64)
+            c, _ = oracle.greedy(Dd, K)
+            assert runs[0][1][i] == pytest.approx(oracle.criterion(Dd, c), rel=1e-12)
+        T2 = synth.six_regime_sweep(seed=5, n=s.T.shape[0], min_len=300).T
+        h.reload(T2)
+        got = [h.select_length(ms, K) for _ in range(3)]
+    with _series(T2, 0) as h2:
+        fresh = h2.select_length(ms, K)
+    for g in got:
+        assert g[0] == fresh[0] and np.array_equal(g[1], fresh[1]) and g[2] == fresh[2]
