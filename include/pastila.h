@@ -180,6 +180,115 @@ pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, i
 pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, int64_t P, int32_t K,
                                       int32_t* chosen_dev, double* area_after_dev, void* stream);
 
+/* -------------------------------------------------------------- engine ---- */
+
+/* Serving engine (no counterpart in the paper: the paper runs one series at a
+ * time).  Jobs are whole select_length problems -- a series, its sweep of
+ * lengths m_list, the ell/k rule and K -- submitted from any host thread and
+ * run by one scheduler thread with continuous batching on one GPU:
+ *   - admission: queued jobs are admitted in submission order while fewer than
+ *     max_active_jobs are resident and the job's resident memory (series,
+ *     window statistics, K chosen profiles per length, small state) plus its
+ *     largest S x P profile set fit in the memory budget; a job that can never
+ *     fit is refused by pastila_engine_submit with ENOMEM;
+ *   - waves: each wave is one tile launch over segment ranges of every active
+ *     job's lengths (the wave's eq. 9 cells are shared equally among the active
+ *     jobs), then one batched greedy search (eqs. 16-17) and criterion (eq. 18)
+ *     for every length whose profiles are complete, then m_best and the eq. 8
+ *     records of every job whose lengths are all done; a profile set lives only
+ *     from its first wave to its greedy search;
+ *   - overlap: up to max_waves_in_flight waves are queued on the device at
+ *     once, and jobs that arrive while waves run join the next wave.
+ * A job's results are bit-identical to pastila_select_length on a handle of the
+ * engine's precision and device for FP32 (FP64: equal up to the criterion's
+ * summation order), whatever other jobs share its waves.  All entry points
+ * are thread-safe. */
+typedef struct pastila_engine pastila_engine;
+
+typedef struct {
+    int32_t device;
+    pastila_precision prec;
+    size_t mem_budget_bytes;     /* device memory the engine may hold; 0: 90 % of the memory free at creation */
+    int32_t max_active_jobs;     /* jobs resident at once, 1..256; 0: 32 */
+    double wave_ed_cells;        /* eq. 9 cells (halo columns included) per wave; 0: 4e9 */
+    int32_t max_waves_in_flight; /* 1..8; 0: 2 */
+    int32_t fail_alloc_at;       /* fault injection for tests: the n-th device allocation (1-based) of the
+                                    engine reports ENOMEM and fails the job it was for; 0: off */
+} pastila_engine_config;
+
+typedef enum {
+    PASTILA_JOB_QUEUED = 0,
+    PASTILA_JOB_ACTIVE = 1,
+    PASTILA_JOB_DONE = 2,
+    PASTILA_JOB_FAILED = 3,
+    PASTILA_JOB_CANCELLED = 4
+} pastila_job_state;
+
+typedef struct {
+    int32_t state;            /* pastila_job_state */
+    int32_t status;           /* OK, or the pastila_status that ended the job */
+    double t_submit;          /* engine clock, seconds since pastila_engine_create (steady clock) */
+    double t_admit;           /* -1 until admitted */
+    double t_done;            /* -1 until final; t_done - t_submit is the job's latency */
+    int64_t first_wave;       /* first and last wave that carried the job's work; -1 until set */
+    int64_t last_wave;
+    double ed_cells;          /* eq. 9 cells of the job's tiles, halo columns included */
+    double profile_cells;     /* sum over the sweep of S * P */
+    size_t mem_bytes;         /* device memory admission asks for: resident + largest profile set */
+    size_t resident_bytes;    /* the part held from admission to the job's last wave */
+} pastila_job_info;
+
+typedef struct {
+    uint64_t submitted, done, failed, cancelled;
+    uint64_t waves, launches;  /* waves enqueued; kernel launches they issued */
+    double ed_cells;           /* eq. 9 cells of all tile launches */
+    double profile_cells;      /* S * P summed over the lengths of the finished jobs */
+    double busy_ms;            /* device time of the finished waves (events around each wave) */
+    size_t mem_budget, mem_held, mem_peak;
+    double now;                /* engine clock */
+} pastila_engine_counters;
+
+/* Creates an engine (its streams, memory pool and scheduler thread) on
+ * cfg->device; cfg NULL selects every default.  Errors: EINVAL, ENOMEM, ECUDA. */
+pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_config* cfg);
+
+/* Queues one job; the n host values of T are copied before the call returns.
+ * m_list: n_m lengths (1 <= n_m <= 64), each 4 <= m <= n, with the ell/k rule
+ * of pastila_mparams; 2 <= K <= min(n / max m, 64).  *job_out receives the
+ * job's id.  Errors: EINVAL (arguments, tile does not fit shared memory, engine
+ * shutting down), ENOMEM (the job can never fit the budget), ECUDA (the engine
+ * stopped after a device error). */
+pastila_status pastila_engine_submit(pastila_engine* e, const double* T, int64_t n, const int32_t* m_list,
+                                     int32_t n_m, pastila_mparams rule, int32_t K, int64_t* job_out);
+
+/* Waits up to timeout_ms (0: no wait, < 0: no limit) for the job to reach
+ * DONE, FAILED or CANCELLED and fills *info (may be NULL) either way.
+ * Returns OK when the job is final, ETIMEOUT when it is not; EINVAL for an
+ * unknown or released job. */
+pastila_status pastila_engine_poll(pastila_engine* e, int64_t job, int32_t timeout_ms, pastila_job_info* info);
+
+/* Results of a DONE job, as pastila_select_length gives them: m_best, the n_m
+ * criterion values (crit_out, may be NULL) and the K records of m_best
+ * (best_out, may be NULL).  Errors: EBUSY (not final), ECANCELLED, the job's
+ * own error for a FAILED job, EINVAL. */
+pastila_status pastila_engine_result(pastila_engine* e, int64_t job, int32_t* m_best, double* crit_out,
+                                     pastila_snippet* best_out);
+
+/* Cancels a queued or running job; its memory is returned at the next wave
+ * boundary (work already on the device finishes first).  Errors: EINVAL
+ * (unknown job, or a job that has finished or is in its final wave). */
+pastila_status pastila_engine_cancel(pastila_engine* e, int64_t job);
+
+/* Forgets a final job and its results.  Errors: EBUSY (not final), EINVAL. */
+pastila_status pastila_engine_release(pastila_engine* e, int64_t job);
+
+/* Engine counters.  Errors: EINVAL. */
+pastila_status pastila_engine_stats(pastila_engine* e, pastila_engine_counters* out);
+
+/* Lets the waves on the device finish, cancels every other job, stops the
+ * scheduler and frees everything.  NULL is a no-op. */
+void pastila_engine_destroy(pastila_engine* e);
+
 /* ------------------------------------------------------------- tracing ---- */
 
 /* Kernel launches the handle has issued since it was created. */

@@ -23,6 +23,8 @@ struct BatchItem {
     ProfileArgs<real> A;   // profile arguments (series, statistics, D, D max key)
     TileGeom G;            // tile layout of this item
     long long cta_begin;   // first CTA of this item in the flattened tile grid
+    int s_begin;           // first segment of this launch's share of the item (the
+                           // engine splits an item's segments over several waves)
     real* M;               // representativeness curve, P values
     double* area;          // S areas of the current greedy step
     int32_t* chosen;       // K chosen segments, greedy order
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(512) batched_tiles_kernel(const BatchItem<real
     }
     __syncthreads();
     const long long local = b - items[lo].cta_begin;
-    const int s = (int)(local / sA.ntiles), tt = (int)(local % sA.ntiles);
+    const int s = items[lo].s_begin + (int)(local / sA.ntiles), tt = (int)(local % sA.ntiles);
     profile_tile<real, V>(sA, sG, s, tt, smem);
 }
 

@@ -201,9 +201,9 @@ struct MParams {
     int64_t P, C;
 };
 
-pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, MParams* o) {
+pastila_status resolve_n(int64_t n, int32_t m, pastila_mparams mp, MParams* o) {
     if (m < 4) return fail(PASTILA_EINVAL, "m = %d: must be at least 4", m);
-    if ((int64_t)m > h->n) return fail(PASTILA_EINVAL, "m = %d exceeds the series length %lld", m, (long long)h->n);
+    if ((int64_t)m > n) return fail(PASTILA_EINVAL, "m = %d exceeds the series length %lld", m, (long long)n);
     const int ell = mp.ell ? mp.ell : m / 2;
     const int k = mp.k ? mp.k : (m + 9) / 10;
     if (ell < 2 || ell > m) return fail(PASTILA_EINVAL, "ell = %d: must satisfy 2 <= ell <= m = %d", ell, m);
@@ -212,10 +212,14 @@ pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, M
     o->ell = ell;
     o->k = k;
     o->R = m - ell + 1;
-    o->S = (int)(h->n / m);
-    o->P = h->n - m + 1;
-    o->C = h->n - ell + 1;
+    o->S = (int)(n / m);
+    o->P = n - m + 1;
+    o->C = n - ell + 1;
     return PASTILA_OK;
+}
+
+pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, MParams* o) {
+    return resolve_n(h->n, m, mp, o);
 }
 
 // Tile width W and row groups NG: the smallest modelled cost per ED cell of the
@@ -225,8 +229,7 @@ pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, M
 // positions; NG row groups add NG seed rows of ell products per column, and
 // fewer than 12 resident warps leave latency exposed.
 template <typename real, int V>
-pastila_status choose_tile(const pastila_series* h, const MParams& q, TileGeom* g) {
-    const size_t limit = (size_t)h->smem_optin;
+pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
     const int64_t Pmax = ((q.P + 31) / 32) * 32;
     double best_cost = 1e300;
     TileGeom best{};
@@ -253,6 +256,11 @@ pastila_status choose_tile(const pastila_series* h, const MParams& q, TileGeom* 
         return fail(PASTILA_EINVAL, "m = %d, ell = %d: the tile does not fit in shared memory", q.m, q.ell);
     *g = best;
     return PASTILA_OK;
+}
+
+template <typename real, int V>
+pastila_status choose_tile(const pastila_series* h, const MParams& q, TileGeom* g) {
+    return choose_tile_s<real, V>((size_t)h->smem_optin, q, g);
 }
 
 pastila_status get_event(pastila_series* h, cudaEvent_t* e) {
@@ -305,7 +313,7 @@ pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st,
     A.D = D;
     A.dmax_key = dmax;
     CK(cudaFuncSetAttribute(profile_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)g.bytes));
+                            h->smem_optin));
     init_dmax_kernel<<<1, 1, 0, h->stream>>>(dmax);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->timing) {
@@ -520,8 +528,10 @@ pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs
     const int n = (int)qs.size();
     const BatchItem<real>* items = (const BatchItem<real>*)sb.items;
     if (phase == 1) {
+        // the attribute is process-wide: every caller sets the same device maximum, so
+        // concurrent callers (handles, the engine) never lower it under one another
         CK(cudaFuncSetAttribute(batched_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+                                h->smem_optin));
         batched_tiles_kernel<real, V><<<(unsigned)ctas, block, smem, h->stream>>>(items, n);
         CK(cudaGetLastError());
         h->launches += 1;
@@ -700,6 +710,8 @@ pastila_status check_finite(const double* T, int64_t n) {
 }
 
 }  // namespace
+
+#include "engine.cuh"
 
 extern "C" {
 

@@ -29,6 +29,30 @@ class MParams(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int32), ("k", ctypes.c_int32)]
 
 
+class EngineConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("prec", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
+                ("max_active_jobs", ctypes.c_int32), ("wave_ed_cells", ctypes.c_double),
+                ("max_waves_in_flight", ctypes.c_int32), ("fail_alloc_at", ctypes.c_int32)]
+
+
+class JobInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("first_wave", ctypes.c_int64),
+                ("last_wave", ctypes.c_int64), ("ed_cells", ctypes.c_double), ("profile_cells", ctypes.c_double),
+                ("mem_bytes", ctypes.c_size_t), ("resident_bytes", ctypes.c_size_t)]
+
+
+class EngineCounters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("done", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("waves", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("ed_cells", ctypes.c_double), ("profile_cells", ctypes.c_double), ("busy_ms", ctypes.c_double),
+                ("mem_budget", ctypes.c_size_t), ("mem_held", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t),
+                ("now", ctypes.c_double)]
+
+
+JOB_QUEUED, JOB_ACTIVE, JOB_DONE, JOB_FAILED, JOB_CANCELLED = range(5)
+
+
 class Snippet(ctypes.Structure):
     _fields_ = [("index", ctypes.c_int32), ("rank", ctypes.c_int32), ("frac", ctypes.c_double),
                 ("area_after", ctypes.c_double)]
@@ -77,6 +101,24 @@ def load(path: str | None = None):
         lib.pastila_tile_time.restype = S
         lib.pastila_greedy_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp]
         lib.pastila_greedy_noalloc.restype = S
+        lib.pastila_engine_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(EngineConfig)]
+        lib.pastila_engine_create.restype = S
+        lib.pastila_engine_submit.argtypes = [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32, MParams,
+                                              ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+        lib.pastila_engine_submit.restype = S
+        lib.pastila_engine_poll.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(JobInfo)]
+        lib.pastila_engine_poll.restype = S
+        lib.pastila_engine_result.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), _vp,
+                                              ctypes.POINTER(Snippet)]
+        lib.pastila_engine_result.restype = S
+        lib.pastila_engine_cancel.argtypes = [_vp, ctypes.c_int64]
+        lib.pastila_engine_cancel.restype = S
+        lib.pastila_engine_release.argtypes = [_vp, ctypes.c_int64]
+        lib.pastila_engine_release.restype = S
+        lib.pastila_engine_stats.argtypes = [_vp, ctypes.POINTER(EngineCounters)]
+        lib.pastila_engine_stats.restype = S
+        lib.pastila_engine_destroy.argtypes = [_vp]
+        lib.pastila_engine_destroy.restype = None
         _lib = lib
     return _lib
 
@@ -195,6 +237,80 @@ class Series:
         _check(load().pastila_select_length(self._h, _ptr(ms), ms.shape[0], MParams(ell, k), K,
                                             ctypes.byref(best), _ptr(crit), out))
         return best.value, crit, _recs(out)
+
+
+class Engine:
+    """Serving engine (``pastila_engine_*``): continuous batching of
+    select_length jobs on one GPU."""
+
+    def __init__(self, device: int = 0, precision: int = FP32, mem_budget: int = 0, max_active: int = 0,
+                 wave_ed_cells: float = 0.0, max_waves_in_flight: int = 0, fail_alloc_at: int = 0):
+        lib = load()
+        cfg = EngineConfig(device, precision, mem_budget, max_active, wave_ed_cells, max_waves_in_flight,
+                           fail_alloc_at)
+        h = _vp()
+        _check(lib.pastila_engine_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self._h = h
+        self._sizes = {}
+
+    def close(self):
+        if self._h:
+            load().pastila_engine_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, T, ms, K: int, ell: int = 0, k: int = 0) -> int:
+        """Queues a job; returns its id."""
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        ms = np.ascontiguousarray(ms, dtype=np.int32)
+        job = ctypes.c_int64()
+        _check(load().pastila_engine_submit(self._h, _ptr(T), T.shape[0], _ptr(ms), ms.shape[0], MParams(ell, k),
+                                            K, ctypes.byref(job)))
+        self._sizes[job.value] = (ms.shape[0], K)
+        return job.value
+
+    def poll(self, job: int, timeout_ms: int = 0):
+        """(final?, JobInfo as a dict)."""
+        info = JobInfo()
+        st = load().pastila_engine_poll(self._h, job, timeout_ms, ctypes.byref(info))
+        if st not in (OK, ETIMEOUT):
+            _check(st)
+        return st == OK, {f: getattr(info, f) for f, _ in JobInfo._fields_}
+
+    def wait(self, job: int):
+        return self.poll(job, -1)[1]
+
+    def result(self, job: int):
+        """(m_best, crit per m, K records of m_best) of a finished job."""
+        n_m, K = self._sizes.get(job, (64, 64))  # an unknown job is the library's error to report
+        crit = np.empty(n_m, dtype=np.float64)
+        out = (Snippet * K)()
+        best = ctypes.c_int32()
+        _check(load().pastila_engine_result(self._h, job, ctypes.byref(best), _ptr(crit), out))
+        return best.value, crit, _recs(out)
+
+    def cancel(self, job: int):
+        _check(load().pastila_engine_cancel(self._h, job))
+
+    def release(self, job: int):
+        _check(load().pastila_engine_release(self._h, job))
+        self._sizes.pop(job, None)
+
+    def stats(self) -> dict:
+        c = EngineCounters()
+        _check(load().pastila_engine_stats(self._h, ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in EngineCounters._fields_}
 
 
 def greedy_noalloc(D_ptr: int, S: int, P: int, K: int, chosen_ptr: int, area_ptr: int,

@@ -190,3 +190,45 @@ def default_k(m: int) -> int:
 
 def white_noise(seed: int, n: int, sd: float = 1.0) -> np.ndarray:
     return np.random.default_rng(seed).normal(0.0, sd, size=n)
+
+
+# ----------------------------------------------------------------------------
+# serving workload: a stream of independent labelling jobs
+# ----------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Job:
+    """One serving job: a planted-regime series and its own length sweep."""
+
+    arrival: float      # seconds after the first arrival
+    n: int
+    ms: list            # distinct snippet lengths, ascending
+    K: int
+    n_regimes: int
+    seed: int           # seed of the series' generator
+
+    def series(self) -> np.ndarray:
+        rng = np.random.default_rng(self.seed)
+        return random_planted(rng, self.n, self.n_regimes, 0.05, name=f"job_n{self.n}").T
+
+
+def serving_jobs(n_jobs: int = 1000, rate: float = 20.0, seed: int = 3, n_lo: int = 10_000,
+                 n_hi: int = 500_000) -> list:
+    """Poisson arrivals at `rate` jobs/s (exponential gaps, first job at t = 0);
+    n log-uniform in [n_lo, n_hi]; 3-8 planted regimes from the six-regime set
+    plus N(0, 0.05^2) noise; a sweep of 3-10 distinct lengths from the multiples
+    of 32 in [64, 768]; ell = m / 2; K uniform in [3, 6]."""
+    rng = np.random.default_rng(seed)
+    grid = np.arange(64, 769, 32)
+    jobs, t = [], 0.0
+    for q in range(n_jobs):
+        if q:
+            t += float(rng.exponential(1.0 / rate))
+        n = int(round(float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))))
+        n_m = int(rng.integers(3, 11))
+        ms = sorted(int(x) for x in rng.choice(grid, size=n_m, replace=False))
+        K = int(rng.integers(3, 7))
+        n_reg = int(rng.integers(3, 9))
+        jobs.append(Job(t, n, ms, K, n_reg, int(rng.integers(0, 2**31 - 1))))
+    return jobs

@@ -43,3 +43,26 @@ def test_host_side_argument_validation():
     assert lib.pastila_set_timing(None, 1) == pastila.EINVAL
     assert lib.pastila_kernel_launches(None) == 0
     lib.pastila_destroy(None)  # no-op
+
+
+def test_engine_host_side_validation():
+    lib = pastila.load()
+    e = ctypes.c_void_p()
+    assert lib.pastila_engine_create(None, None) == pastila.EINVAL
+    bad = pastila.EngineConfig(0, 7, 0, 0, 0.0, 0, 0)
+    assert lib.pastila_engine_create(ctypes.byref(e), ctypes.byref(bad)) == pastila.EINVAL
+    assert "precision" in pastila.last_error()
+    bad = pastila.EngineConfig(0, pastila.FP32, 0, 1000, 0.0, 0, 0)
+    assert lib.pastila_engine_create(ctypes.byref(e), ctypes.byref(bad)) == pastila.EINVAL
+    job = ctypes.c_int64()
+    T = np.zeros(100)
+    ms = np.array([16], dtype=np.int32)
+    assert lib.pastila_engine_submit(None, T.ctypes.data_as(ctypes.c_void_p), 100,
+                                     ms.ctypes.data_as(ctypes.c_void_p), 1, pastila.MParams(0, 0), 2,
+                                     ctypes.byref(job)) == pastila.EINVAL
+    assert lib.pastila_engine_poll(None, 1, 0, None) == pastila.EINVAL
+    assert lib.pastila_engine_result(None, 1, None, None, None) == pastila.EINVAL
+    assert lib.pastila_engine_cancel(None, 1) == pastila.EINVAL
+    assert lib.pastila_engine_release(None, 1) == pastila.EINVAL
+    assert lib.pastila_engine_stats(None, None) == pastila.EINVAL
+    lib.pastila_engine_destroy(None)  # no-op

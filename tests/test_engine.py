@@ -1,0 +1,210 @@
+"""The serving engine (pastila_engine_*): results against select_length on a
+handle, the same result alone and in a mix, admission by memory and by slots,
+cancellation, an injected allocation failure and shutdown with work pending.
+Failures are made on the host (an injected allocation error, a cancel); no
+test faults or stalls the GPU."""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    rng = np.random.default_rng(11)
+    out = []
+    for n, ms, K in ((20_000, [64, 128, 256], 3), (31_000, [96, 160, 512, 640], 4),
+                     (12_345, [64, 96, 352], 6), (47_000, [128, 192], 5)):
+        T = synth.random_planted(rng, n, int(rng.integers(3, 9))).T
+        out.append((T, ms, K))
+    return out
+
+
+def _run_alone(pastila, T, ms, K, precision):
+    with pastila.Engine(precision=precision) as e:
+        j = e.submit(T, ms, K)
+        info = e.wait(j)
+        assert info["state"] == pastila.JOB_DONE
+        return e.result(j)
+
+
+def _same(a, b):
+    assert a[0] == b[0]
+    np.testing.assert_array_equal(a[1], b[1])
+    assert a[2] == b[2]
+
+
+def test_engine_matches_select_length_fp32(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()
+    with pastila.Engine() as e:
+        ids = [e.submit(T, ms, K) for T, ms, K in jobs]
+        for j in ids:
+            assert e.wait(j)["state"] == pastila.JOB_DONE
+        got = [e.result(j) for j in ids]
+        st = e.stats()
+    for (T, ms, K), r in zip(jobs, got):
+        with pastila.Series(T, precision=pastila.FP32) as h:
+            ref = h.select_length(ms, K)
+        _same(r, ref)  # bit-identical: same kernels, same tile geometry
+    assert st["done"] == len(jobs) and st["failed"] == 0
+    assert st["mem_held"] == 0 and st["mem_peak"] <= st["mem_budget"]
+
+
+def test_engine_matches_select_length_fp64(lib):
+    from paper_2401_13680_b300 import pastila
+    T, ms, K = _jobs()[2]
+    got = _run_alone(pastila, T, ms, K, pastila.FP64)
+    with pastila.Series(T, precision=pastila.FP64) as h:
+        ref = h.select_length(ms, K)
+    assert got[0] == ref[0]
+    # the criterion's partial sums are split differently: equal up to rounding
+    np.testing.assert_allclose(got[1], ref[1], rtol=1e-12)
+    assert [r[0] for r in got[2]] == [r[0] for r in ref[2]]
+    assert [r[2] for r in got[2]] == [r[2] for r in ref[2]]
+    np.testing.assert_allclose([r[3] for r in got[2]], [r[3] for r in ref[2]], rtol=1e-12)
+
+
+def test_result_alone_equals_result_in_mix(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()
+    alone = [_run_alone(pastila, T, ms, K, pastila.FP32) for T, ms, K in jobs]
+    # small waves: every length is split over several waves and shares them with
+    # the other jobs; half the jobs arrive while the first ones run
+    with pastila.Engine(wave_ed_cells=3e7, max_waves_in_flight=3) as e:
+        ids = [e.submit(T, ms, K) for T, ms, K in jobs[:2]]
+        time.sleep(0.05)
+        ids += [e.submit(T, ms, K) for T, ms, K in jobs[2:]]
+        infos = [e.wait(j) for j in ids]
+        mixed = [e.result(j) for j in ids]
+        st = e.stats()
+    for a, b in zip(alone, mixed):
+        _same(a, b)
+    # the jobs really shared waves and really were split
+    assert st["waves"] > len(jobs)
+    spans = [(i["first_wave"], i["last_wave"]) for i in infos]
+    assert any(s[1] > s[0] for s in spans)
+    assert any(spans[x][0] <= spans[y][1] and spans[y][0] <= spans[x][1]
+               for x in range(len(spans)) for y in range(x + 1, len(spans)))
+    for i in infos:
+        assert 0 <= i["t_submit"] <= i["t_admit"] <= i["t_done"]
+
+
+def test_admission_refuses_a_job_that_can_never_fit(lib):
+    from paper_2401_13680_b300 import pastila
+    T, ms, K = _jobs()[0]
+    with pastila.Engine(mem_budget=1 << 20) as e:
+        with pytest.raises(pastila.PastilaError, match="ENOMEM"):
+            e.submit(T, ms, K)
+
+
+def test_admission_defers_on_memory(lib):
+    from paper_2401_13680_b300 import pastila
+    T, ms, K = _jobs()[0]
+    with pastila.Engine() as e:
+        j = e.submit(T, ms, K)
+        info = e.wait(j)
+    need, res = info["mem_bytes"], info["resident_bytes"]
+    budget = need + res // 2  # one job fits; a second is admitted only once the first is gone
+    with pastila.Engine(mem_budget=budget) as e:
+        a, b = e.submit(T, ms, K), e.submit(T, ms, K)
+        ia, ib = e.wait(a), e.wait(b)
+        st = e.stats()
+        ra, rb = e.result(a), e.result(b)
+    assert ia["state"] == ib["state"] == pastila.JOB_DONE
+    assert ib["first_wave"] > ia["last_wave"]  # b waited for a's memory
+    assert st["mem_peak"] <= budget
+    _same(ra, rb)
+
+
+def test_admission_by_slots(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()[:3]
+    with pastila.Engine(max_active=1) as e:
+        ids = [e.submit(T, ms, K) for T, ms, K in jobs]
+        infos = [e.wait(j) for j in ids]
+    for x, y in zip(infos, infos[1:]):
+        assert y["t_admit"] >= x["t_done"] - 1e-6 or y["first_wave"] > x["last_wave"]
+
+
+def test_cancel_queued_and_running_jobs(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()
+    T, ms, K = jobs[3]
+    with pastila.Engine(max_active=1, wave_ed_cells=2e7) as e:
+        run = e.submit(T, ms, K)
+        queued = e.submit(*jobs[0])
+        e.cancel(queued)
+        # wait until the long job is on the device, then cancel it between waves
+        for _ in range(2000):
+            if e.poll(run)[1]["state"] == pastila.JOB_ACTIVE:
+                break
+            time.sleep(0.001)
+        try:
+            e.cancel(run)
+            cancelled_running = True
+        except pastila.PastilaError:
+            cancelled_running = False  # finished before the cancel arrived
+        iq = e.wait(queued)
+        ir = e.wait(run)
+        assert iq["state"] == pastila.JOB_CANCELLED
+        with pytest.raises(pastila.PastilaError, match="ECANCELLED"):
+            e.result(queued)
+        if cancelled_running:
+            assert ir["state"] == pastila.JOB_CANCELLED
+        # the engine keeps serving, and every byte comes back
+        j = e.submit(*jobs[2])
+        assert e.wait(j)["state"] == pastila.JOB_DONE
+        ref = _run_alone(pastila, *jobs[2], pastila.FP32)
+        _same(e.result(j), ref)
+        st = e.stats()
+        assert st["mem_held"] == 0
+        assert st["cancelled"] >= 1
+
+
+def test_injected_allocation_failure_fails_one_job(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()
+    with pastila.Engine(fail_alloc_at=1) as e:
+        bad = e.submit(*jobs[0])
+        ib = e.wait(bad)
+        assert ib["state"] == pastila.JOB_FAILED and ib["status"] == pastila.ENOMEM
+        with pytest.raises(pastila.PastilaError, match="injected"):
+            e.result(bad)
+        good = e.submit(*jobs[0])
+        assert e.wait(good)["state"] == pastila.JOB_DONE
+        _same(e.result(good), _run_alone(pastila, *jobs[0], pastila.FP32))
+        assert e.stats()["failed"] == 1
+
+
+def test_destroy_with_pending_work_returns(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()
+    e = pastila.Engine(max_active=1, wave_ed_cells=2e7)
+    for T, ms, K in jobs:
+        e.submit(T, ms, K)
+    t0 = time.time()
+    e.close()
+    assert time.time() - t0 < 60
+
+
+def test_submit_argument_errors(lib):
+    from paper_2401_13680_b300 import pastila
+    T = synth.white_noise(5, 5000)
+    with pastila.Engine() as e:
+        with pytest.raises(pastila.PastilaError, match="K = 40"):
+            e.submit(T, [128], 40)
+        with pytest.raises(pastila.PastilaError, match="exceeds"):
+            e.submit(T, [6000], 2)
+        with pytest.raises(pastila.PastilaError, match="n_m"):
+            e.submit(T, [], 2)
+        with pytest.raises(pastila.PastilaError, match="unknown"):
+            e.poll(12345)
+        j = e.submit(T, [64, 96], 2)
+        e.wait(j)
+        e.release(j)
+        with pytest.raises(pastila.PastilaError, match="unknown"):
+            e.result(j)
