@@ -12,6 +12,15 @@ sweep of floor(n/m) * (n - m + 1) per step).  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+A serving leg follows (``--serve-jobs``, 0 to skip): the first jobs of the
+seeded serving stream (n log-uniform in [10^4, 5*10^5], 3-10 lengths in
+[64, 768], K in [3, 6], Poisson arrivals) submitted in real time to the
+serving engine, with the arrival clock scaled so that the offered load is
+``--serve-load`` of the ED-cell rate the sweep leg measured; it reports p50/p99
+job latency (arrival to results on the host) beside the engine's throughput,
+and the p50/p99 that the plain FP64 one-job path would give on the same
+arrivals (first come, first served, service times from its measured rate).
+
 ``--impl reference`` times the FP64 CPU oracle (the paper's definitions, PSF
 steps) on a bounded sample of the same workload on this host's cores.
 """
@@ -44,8 +53,8 @@ SM_MAX_MHZ = 2032.0
 FLOP_PER_ED_CELL = 8.0
 
 
-def workload():
-    return synth.six_regime_sweep(), synth.sweep_lengths()
+def workload(m_list=None):
+    return synth.six_regime_sweep(), (m_list or synth.sweep_lengths())
 
 
 def cells(n, ms):
@@ -55,7 +64,10 @@ def cells(n, ms):
 
 
 def config_dict(n, ms):
-    return {"workload": "six-regime sweep, n=100000, m=64..512 step 32, ell=m/2, k=ceil(0.1m), K=4",
+    name = ("six-regime sweep, n=100000, m=64..512 step 32, ell=m/2, k=ceil(0.1m), K=4"
+            if ms == synth.sweep_lengths() else
+            f"six-regime series, n=100000, m in {ms} (a reduced sweep, not the benchmark), ell=m/2, K=4")
+    return {"workload": name,
             "n": n, "m_list": ms, "K": K_SNIPPETS, "l2": "flushed (256 MiB write) between timed steps",
             "parallelism": "replicas"}
 
@@ -141,7 +153,7 @@ def oracle_sample(T, ms, block: int, seed: int, cores: int):
 def run_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    s, ms = workload()
+    s, ms = workload(args.m_list)
     cores = os.cpu_count() or 1
     block = 512
     for w in range(args.warmup):
@@ -163,6 +175,66 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- serving
+
+def job_ed_cells(job):
+    """Algorithmic eq. 9 cells of a serving job: sum over its sweep of S x R x C."""
+    return sum((job.n // m) * (m - m // 2 + 1) * (job.n - m // 2 + 1) for m in job.ms)
+
+
+def job_profile_cells(job):
+    return sum((job.n // m) * (job.n - m + 1) for m in job.ms)
+
+
+def fifo_latencies(arrivals, service):
+    """Latencies of one server taking jobs first come, first served."""
+    free, out = 0.0, []
+    for a, s in zip(arrivals, service):
+        start = max(a, free)
+        free = start + s
+        out.append(free - a)
+    return out
+
+
+def run_serving(args, pastila, device, ed_rate, fp64_ed_rate):
+    jobs = synth.serving_jobs(n_jobs=args.serve_jobs, rate=20.0, seed=3)
+    series = [j.series() for j in jobs]  # drawn before the clock starts
+    ed = np.array([job_ed_cells(j) for j in jobs], dtype=np.float64)
+    prof = np.array([job_profile_cells(j) for j in jobs], dtype=np.float64)
+    rate = args.serve_load * ed_rate / ed.mean()  # jobs/s
+    arrivals = [j.arrival * 20.0 / rate for j in jobs]
+    with pastila.Engine(device=device) as e, ClockSampler(device) as clk:
+        t0 = time.perf_counter()
+        ids = []
+        for T, j, at in zip(series, jobs, arrivals):
+            wait = t0 + at - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(e.submit(T, j.ms, j.K))
+        infos = [e.wait(i) for i in ids]
+        st = e.stats()
+    assert all(i["state"] == pastila.JOB_DONE for i in infos), "a serving job did not finish"
+    lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    out = {"jobs": len(jobs), "arrival_rate_jobs_per_s": rate, "offered_load": args.serve_load,
+           "workload": "serving stream seed 3: n log-uniform [1e4, 5e5], 3-8 planted regimes + N(0, 0.05^2), "
+                       "3-10 lengths from {64, 96, ..., 768}, ell = m/2, K in [3, 6]; Poisson arrivals, "
+                       "time-scaled from 20 jobs/s to the offered load",
+           "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+           "latency_mean_s": float(lat.mean()), "latency_max_s": float(lat.max()),
+           "makespan_s": span, "profile_cells_per_s": float(prof.sum() / span),
+           "ed_cells_per_s": float(ed.sum() / span), "waves": st["waves"], "launches": st["launches"],
+           "device_busy_frac": st["busy_ms"] / 1e3 / span, "mem_peak_gb": st["mem_peak"] / 1e9,
+           "clocks": clk.summary()}
+    if fp64_ed_rate:
+        lat64 = np.array(fifo_latencies(arrivals, ed / fp64_ed_rate))
+        out["fp64_plain_fifo_model"] = {
+            "latency_p50_s": float(np.percentile(lat64, 50)), "latency_p99_s": float(np.percentile(lat64, 99)),
+            "basis": "same arrivals, one job at a time, service time = job ED cells / the FP64 path's "
+                     "measured ED-cell rate on the sweep"}
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args):
@@ -179,7 +251,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    s, ms = workload()
+    s, ms = workload(args.m_list)
     T = s.T
     n = T.shape[0]
     prof_cells, ed_cells = cells(n, ms)
@@ -281,8 +353,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
         fp64 = {"value": prof_cells / t64, "unit": UNIT, "ms_per_step": 1e3 * t64, "m_best": r64[0],
+                "ed_cells_per_s": ed_cells / t64,
                 "speedup_fp32_over_fp64": (prof_cells / (tot_s / args.steps)) / (prof_cells / t64)}
         h64.close()
+
+    serving = None
+    if args.serve_jobs > 0 and world == 1:
+        serving = run_serving(args, pastila, local, ed_cells * args.steps / tot_s,
+                              fp64["ed_cells_per_s"] if fp64 else None)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
@@ -291,7 +369,7 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps, "roofline": roofline,
             "ed_cells_per_s": world * ed_cells * args.steps / tot_s,
             "m_best": result[0], "criterion": [float(x) for x in result[1]],
-            "step_ms": step_ms, "fp64_path": fp64}
+            "step_ms": step_ms, "fp64_path": fp64, "serving": serving}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     h.close()
@@ -310,6 +388,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--m-list", type=lambda x: [int(v) for v in x.split(",")], default=None,
+                    help="comma-separated lengths replacing the sweep (profiling runs on a small case)")
+    ap.add_argument("--serve-jobs", type=int, default=32, help="serving-leg jobs (0: no serving leg)")
+    ap.add_argument("--serve-load", type=float, default=0.7,
+                    help="offered load of the serving leg, as a fraction of the measured ED-cell rate")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -186,6 +186,7 @@ template <typename key_t, typename Out>
 __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int RS, int LA, int V,
                                              const key_t* __restrict__ CB, int R, int kk, int p_begin,
                                              int npos, int npos_warp, int G, int gl, Out out) {
+    // requires R <= G * SEL_CACHE: every value of a position sits in the registers of its group
     const unsigned FULL = 0xffffffffu;
     const key_t KMAX = ~(key_t)0;
     const int nr = (R - gl + G - 1) / G;  // values per half held by this lane
@@ -280,6 +281,204 @@ __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int R
     }
 }
 
+// The bits of a value in a key-typed shared-memory slot (the warp selector reads
+// the slots back as values).
+template <typename real>
+__device__ __forceinline__ typename KeyOf<real>::type as_key(real v);
+template <>
+__device__ __forceinline__ uint32_t as_key<float>(float v) { return __float_as_uint(v); }
+template <>
+__device__ __forceinline__ unsigned long long as_key<double>(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+// Whole-warp reductions of working-precision values.
+__device__ __forceinline__ float warp_max(float v) {
+    return KeyOf<float>::dec(__reduce_max_sync(0xffffffffu, KeyOf<float>::enc(v)));
+}
+__device__ __forceinline__ float warp_min(float v) {
+    return KeyOf<float>::dec(__reduce_min_sync(0xffffffffu, KeyOf<float>::enc(v)));
+}
+__device__ __forceinline__ double warp_max(double v) { return grp_max(v, 32); }
+__device__ __forceinline__ double warp_min(double v) { return grp_min(v, 32); }
+
+constexpr int SEL_CAP = 12;  // AB values of a column held per lane in registers (R <= 384)
+
+// kk-th largest (1-based) of the 2R values of P_ABBA (eqs. 12-13) for a run of
+// consecutive tile positions p_begin .. p_begin + npos - 1, one run per warp.
+// Position p's values are AB column p (the R row-window maxima, eq. 11) and the
+// window CB[p .. p+R-1] (column maxima, eq. 10); lane l holds rows l, l+32, ...
+//
+// The answer tau is tracked along the run together with the counts
+// cge = #{x >= tau} and cgt = #{x > tau}.  From one position to the next only a
+// few row-window maxima change (a window maximum changes only when it leaves the
+// window or a larger value enters) and the column window slides by one, so the
+// counts are updated from the changed values alone; tau stays the answer while
+// cgt < kk <= cge.  Otherwise a pass over all 2R values finds the counts and the
+// nearest values below and above tau and moves tau to the neighbour, up to three
+// times, then a bisection inside the bracket found so far finishes; the first
+// position of a run is found by bisection over the range of its values.  The
+// bisections run over the order-preserving integer keys of the values (their
+// midpoints are keys) but compare values, so equal values (+0 and -0 included)
+// always count together.  Control flow is uniform across the warp.
+// out(p, tau) is called by one lane per position, for 32 positions at a time.
+template <typename real, typename Out>
+__device__ __forceinline__ void select_runs(const real* __restrict__ AB, int RS, int LA, int V,
+                                            const real* __restrict__ CB, int R, int kk, int p_begin,
+                                            int npos, Out out) {
+    typedef KeyOf<real> K;
+    typedef typename K::type key_t;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nrw = (R + 31) >> 5;  // entries per lane and half (the last may be partly empty)
+    const real NEG = RealLimits<real>::lowest();
+    const real POS = -NEG;
+    real cur[SEL_CAP];              // AB column of the current position, rows lane + 32 j
+    real tau = 0, mine = 0;
+    int cge = 0, cgt = 0;
+    int p = 0, cp = 0, cprev = 0;   // position; AB offsets of its column and of the previous one
+
+    // f(x) for every value of position p held by this lane: rows, then window
+    auto each = [&](auto&& f) {
+#pragma unroll
+        for (int j = 0; j < SEL_CAP; ++j) {
+            const int r = lane + 32 * j;
+            if (j < nrw && r < R) {
+                f(cur[j]);
+                f(CB[p + r]);
+            }
+        }
+        for (int j = SEL_CAP; j < nrw; ++j) {
+            const int r = lane + 32 * j;
+            if (r < R) {
+                f(AB[(size_t)r * RS + cp]);
+                f(CB[p + r]);
+            }
+        }
+    };
+    auto count = [&]() {
+        uint32_t c = 0;
+        each([&](real x) { c += (x >= tau ? 1u : 0u) + (x > tau ? 65536u : 0u); });
+        c = __reduce_add_sync(FULL, c);
+        cge = (int)(c & 0xffffu);
+        cgt = (int)(c >> 16);
+    };
+    // largest key v in [lo, hi] with #{x >= value(v)} >= kk
+    auto bisect = [&](key_t lo, key_t hi) {
+        while (lo < hi) {
+            const key_t mid = lo + (key_t)((hi - lo) >> 1) + (key_t)1;
+            const real mv = K::dec(mid);
+            uint32_t c = 0;
+            each([&](real x) { c += x >= mv ? 1u : 0u; });
+            c = __reduce_add_sync(FULL, c);
+            if ((int)c >= kk) lo = mid; else hi = mid - (key_t)1;
+        }
+        return K::dec(lo);
+    };
+    auto range = [&](key_t* lo, key_t* hi) {
+        real mn = POS, mx = NEG;
+        each([&](real x) {
+            mn = x < mn ? x : mn;
+            mx = x > mx ? x : mx;
+        });
+        *lo = K::enc(warp_min(mn));
+        *hi = K::enc(warp_max(mx));
+    };
+    // tau from its previous value (the rank test has failed); leaves exact counts
+    auto retrack = [&]() {
+        key_t lo, hi;
+        bool lo_set = false, hi_set = false;
+        for (int step = 0; step < 3; ++step) {
+            uint32_t c = 0;
+            real below = NEG, above = POS;
+            each([&](real x) {
+                c += (x >= tau ? 1u : 0u) + (x > tau ? 65536u : 0u);
+                below = (x < tau && x > below) ? x : below;
+                above = (x > tau && x < above) ? x : above;
+            });
+            c = __reduce_add_sync(FULL, c);
+            cge = (int)(c & 0xffffu);
+            cgt = (int)(c >> 16);
+            if (cgt < kk && kk <= cge) return;
+            if (cge < kk) {  // the answer lies below tau
+                tau = warp_max(below);
+                hi = K::enc(tau);
+                hi_set = true;
+                if (cge == kk - 1) {
+                    count();
+                    return;
+                }
+            } else {         // above tau
+                tau = warp_min(above);
+                lo = K::enc(tau);
+                lo_set = true;
+                if (cgt == kk) {
+                    count();
+                    return;
+                }
+            }
+        }
+        key_t rlo, rhi;
+        range(&rlo, &rhi);
+        tau = bisect(lo_set ? lo : rlo, hi_set ? hi : rhi);
+        count();
+    };
+
+    for (int it = 0; it < npos; ++it) {
+        p = p_begin + it;
+        cprev = cp;
+        cp = (p % V) * LA + p / V;
+        if (it == 0) {
+#pragma unroll
+            for (int j = 0; j < SEL_CAP; ++j) {
+                const int r = lane + 32 * j;
+                cur[j] = (j < nrw && r < R) ? AB[(size_t)r * RS + cp] : NEG;
+            }
+            key_t lo, hi;
+            range(&lo, &hi);
+            tau = bisect(lo, hi);
+            count();
+        } else {
+            // count changes of the values that changed: rows, then the window slide
+            int d = 0;
+#pragma unroll
+            for (int j = 0; j < SEL_CAP; ++j) {
+                const int r = lane + 32 * j;
+                if (j < nrw && r < R) {
+                    const real nv = AB[(size_t)r * RS + cp], ov = cur[j];
+                    d += ((nv >= tau) - (ov >= tau)) + 65536 * ((nv > tau) - (ov > tau));
+                    cur[j] = nv;
+                }
+            }
+            for (int j = SEL_CAP; j < nrw; ++j) {
+                const int r = lane + 32 * j;
+                if (r < R) {
+                    const real nv = AB[(size_t)r * RS + cp], ov = AB[(size_t)r * RS + cprev];
+                    d += ((nv >= tau) - (ov >= tau)) + 65536 * ((nv > tau) - (ov > tau));
+                }
+            }
+            if (lane == 0) {
+                const real ov = CB[p - 1];
+                d -= (ov >= tau) + 65536 * (ov > tau);
+            } else if (lane == 1) {
+                const real nv = CB[p + R - 1];
+                d += (nv >= tau) + 65536 * (nv > tau);
+            }
+            d = __reduce_add_sync(FULL, d);
+            const int dge = (int)(int16_t)(d & 0xffff);
+            cge += dge;
+            cgt += (d - dge) >> 16;
+            if (!(cgt < kk && kk <= cge)) retrack();
+        }
+        // lane (it mod 32) keeps this position's answer; 32 positions are written at once
+        if (lane == (it & 31)) mine = tau;
+        if ((it & 31) == 31 || it == npos - 1) {
+            const int base = it & ~31;
+            if (base + lane <= it) out(p_begin + base + lane, mine);
+        }
+    }
+}
+
 template <typename real, int V>
 __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const TileGeom& G, int s,
                                              int tt, unsigned char* __restrict__ sm) {
@@ -301,6 +500,10 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int Wb = Wp + R - 1;
     const int64_t i0 = (int64_t)s * m;
 
+    // row-window maxima (eq. 11), [row][position], and column maxima (eq. 10): as
+    // order-preserving keys for the grouped selector (R <= 288), as values for the
+    // warp selector
+    const bool keyed = R <= 32 * SEL_CACHE;
     key_t* AB = (key_t*)(sm + G.off_AB);
     key_t* CB = (key_t*)(sm + G.off_CB);
     real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * LP;  // this group's [parity][V][LP]
@@ -546,7 +749,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                         const int e = i + R - 1;        // window end, relative to xb
                         const int oi = e / V, si = e - oi * V;
                         const real ab = rmax(rmax(suf[i], oi > q0 ? mid1 : mid), PREp[si * LP + t + oi]);
-                        if (full_positions || xb + i < Wp) ABr[i * LA] = K::enc(ab);
+                        if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
                     }
                 } else {
 #pragma unroll
@@ -562,7 +765,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                             const int oi = e / V, si = e - oi * V;
                             ab = rmax(suf[i], PREp[si * LP + t + oi]);
                         }
-                        if (full_positions || xb + i < Wp) ABr[i * LA] = K::enc(ab);
+                        if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
                     }
                 }
             }
@@ -586,36 +789,43 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     for (int x = tid; x < Wb; x += BD) {
         real mx = top[x];
         for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
-        CB[x] = K::enc(mx);
+        CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
     }
     __syncthreads();
 
     // ---------------------------------------------------------------- select
     const int kk = 2 * R > A.k ? A.k : 2 * R;
     const real two_ell = (real)(2 * ell);
-    // lanes per position run: each lane caches at most SEL_CACHE keys of each half
-    const int GS = R <= 4 * SEL_CACHE ? 4 : (R <= 8 * SEL_CACHE ? 8 : (R <= 16 * SEL_CACHE ? 16 : 32));
-    const int ngroups = BD / GS;
-    const int grp = tid / GS, gl = tid % GS;
-    const int PW = (Wp + ngroups - 1) / ngroups;
-    const int pb = grp * PW;
-    const int npos = pb >= Wp ? 0 : (pb + PW <= Wp ? PW : Wp - pb);
-    double tmax = 0.0;
+    real tmax = 0;
     real* Drow = A.D + (int64_t)s * A.P + p0;
-    select_track<key_t>(AB, RS, LA, V, CB, R, kk, pb, npos, PW, GS, gl, [&](int p, key_t kb) {
-        const real rs = K::dec(kb);
+    auto emit = [&](int p, real rs) {
         real u = (real)1 - rs;
         u = u > (real)0 ? u : (real)0;
         const real d = sqrt(two_ell * u);
         Drow[p] = d;
-        tmax = (double)d > tmax ? (double)d : tmax;
-    });
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double other = __shfl_xor_sync(FULL, tmax, o);
-        tmax = other > tmax ? other : tmax;
+        tmax = d > tmax ? d : tmax;
+    };
+    if (keyed) {
+        // groups of GS lanes, each with a run of positions; a lane caches at most
+        // SEL_CACHE values of each half
+        const int GS = R <= 4 * SEL_CACHE ? 4 : (R <= 8 * SEL_CACHE ? 8 : (R <= 16 * SEL_CACHE ? 16 : 32));
+        const int ngroups = BD / GS;
+        const int grp = tid / GS, gl = tid % GS;
+        const int PW = (Wp + ngroups - 1) / ngroups;
+        const int pb = grp * PW;
+        const int npos = pb >= Wp ? 0 : (pb + PW <= Wp ? PW : Wp - pb);
+        select_track<key_t>(AB, RS, LA, V, CB, R, kk, pb, npos, PW, GS, gl,
+                            [&](int p, key_t kb) { emit(p, K::dec(kb)); });
+    } else {
+        // one run per warp; values beyond the register cache are read from shared memory
+        const int nwarps = BD >> 5;
+        const int PW = (Wp + nwarps - 1) / nwarps;
+        const int pb = (tid >> 5) * PW;
+        const int npos = pb >= Wp ? 0 : (pb + PW <= Wp ? PW : Wp - pb);
+        select_runs<real>((const real*)AB, RS, LA, V, (const real*)CB, R, kk, pb, npos, emit);
     }
-    if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(tmax));
+    const double wmax = warp_max(tmax);
+    if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(wmax));
 }
 
 // One CTA per (tile, segment): grid (ntiles, S).

@@ -32,8 +32,12 @@ def test_four_regime_profiles(lib, prec):
 
 # (n, m, ell, k): several tiles with a ragged last tile and a tail segment
 # (n % m != 0); R < V (ell close to m); R = 1 (ell = m); k >= 2R (max branch);
-# k = 1 (min branch); odd sizes
+# k = 1 (min branch); odd sizes; R > 288 and R > 384 (the selection keeps 12
+# values of a column per lane in registers and reads the rest from shared memory)
 CASES = [
+    (4000, 640, 320, 64),
+    (4500, 600, 150, 60),
+    (3000, 400, 200, 40),
     (3000, 64, 32, 7),
     (2501, 50, 25, 5),
     (1800, 40, 37, 3),
