@@ -33,9 +33,11 @@
 //      R-column window (allP_AB, eq. 11) come from van Herk / Gil-Werman style
 //      prefix/suffix maxima over V-column chunks plus the maxima of the whole
 //      chunks in between.
-//   3  per position, the k-th largest of the 2R values of P_ABBA (eqs. 12-13) on
-//      order-preserving integer keys, tracked from position to position by
-//      groups of lanes (select_track); D = sqrt(2 ell max(0, 1-rho*))
+//   3  per position, the k-th largest of the 2R values of P_ABBA (eqs. 12-13),
+//      tracked from position to position: by groups of lanes on order-preserving
+//      integer keys for R <= 288 (select_track), by one warp per run of positions
+//      on values with incrementally updated counts beyond that (select_runs);
+//      D = sqrt(2 ell max(0, 1-rho*))
 #pragma once
 #include <cstdint>
 #include <cfloat>
