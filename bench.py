@@ -271,6 +271,16 @@ def run_ours(args):
     h = pastila.Series(None, device=local, precision=pastila.FP32, device_ptr=T_dev.data_ptr(), n=n,
                        stream=stream.cuda_stream)
 
+    # autotuner: time candidate tile layouts per length (outside the timed region);
+    # the fastest is used by every later call, the serving engine's included
+    tune = None
+    if not args.no_tune:
+        res = h.tune(ms, max_candidates=8)
+        tune = {"per_m": [{"m": r["m"], "W": r["W"], "NG": r["NG"], "NT": r["NT"], "candidates": r["candidates"],
+                           "ms_model": r["ms_model"], "ms_best": r["ms_best"]} for r in res],
+                "sample_speedup_over_model": sum(r["ms_model"] for r in res) / sum(r["ms_best"] for r in res),
+                "sample": "first min(S, 64) segments of each length, all positions; best of 2 timed launches"}
+
     def step():
         h.reload_device(T_dev.data_ptr())
         return h.select_length(ms, K_SNIPPETS)
@@ -369,7 +379,7 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps, "roofline": roofline,
             "ed_cells_per_s": world * ed_cells * args.steps / tot_s,
             "m_best": result[0], "criterion": [float(x) for x in result[1]],
-            "step_ms": step_ms, "fp64_path": fp64, "serving": serving}
+            "step_ms": step_ms, "fp64_path": fp64, "serving": serving, "autotune": tune}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     h.close()
@@ -388,6 +398,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the cost model's tile layouts")
     ap.add_argument("--m-list", type=lambda x: [int(v) for v in x.split(",")], default=None,
                     help="comma-separated lengths replacing the sweep (profiling runs on a small case)")
     ap.add_argument("--serve-jobs", type=int, default=32, help="serving-leg jobs (0: no serving leg)")

@@ -289,6 +289,34 @@ pastila_status pastila_engine_stats(pastila_engine* e, pastila_engine_counters* 
  * scheduler and frees everything.  NULL is a no-op. */
 void pastila_engine_destroy(pastila_engine* e);
 
+/* ----------------------------------------------------------- autotuner ---- */
+
+/* The tile layout of a length (positions per CTA W, row groups NG, threads NT)
+ * comes from a cost model unless the autotuner has chosen one.  pastila_tune
+ * times, for every m of m_list with the ell/k rule, the model's layout and up
+ * to max_candidates - 1 rivals (the cheapest of every thread count first, then
+ * by modelled cost, all within 1.5x of the model's best) on the first
+ * min(S, 64) segments of h's series, and keeps the fastest in a process-wide
+ * table keyed by (precision, m, ell, k) that every later call uses (handles and
+ * engines alike; a captured select_length graph is rebuilt).  Results depend
+ * on the layout only through FP32 rounding (the seeds sit at the tile and
+ * row-group edges); a given layout always gives the same results.  out, when
+ * not NULL, receives n_m records.  No counterpart in the paper, whose kernel
+ * has one fixed layout.  Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct {
+    int32_t m;
+    int32_t W, NG, NT;     /* the chosen layout */
+    int32_t candidates;    /* layouts timed */
+    double ms_model;       /* device time of the cost model's layout on the sample */
+    double ms_best;        /* device time of the chosen layout */
+} pastila_tune_result;
+
+pastila_status pastila_tune(pastila_series* h, const int32_t* m_list, int32_t n_m, pastila_mparams rule,
+                            int32_t max_candidates, pastila_tune_result* out);
+
+/* Forgets every tuned layout (the cost model decides again). */
+void pastila_tune_clear(void);
+
 /* ------------------------------------------------------------- tracing ---- */
 
 /* Kernel launches the handle has issued since it was created. */

@@ -5,9 +5,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -95,6 +97,7 @@ struct pastila_series {
         pastila_mparams rule{0, 0};
         int K = 0;
         uint64_t gen = ~0ull;
+        uint64_t tune_gen = ~0ull;  // the autotuner's table when the graphs were made
         cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // statistics, tiles, snippets
         int calls = 0;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the tile graph, while timing is on
@@ -228,11 +231,16 @@ pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, M
 // halo columns are recomputed by the next tile), the selection on its W
 // positions; NG row groups add NG seed rows of ell products per column, and
 // fewer than 12 resident warps leave latency exposed.
+struct TileCand {
+    double cost;  // modelled cost per ED cell
+    int W, ngw;   // tile width and the row groups asked of tile_geom
+    TileGeom g;
+};
+
 template <typename real, int V>
-pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
+void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out) {
+    out->clear();
     const int64_t Pmax = ((q.P + 31) / 32) * 32;
-    double best_cost = 1e300;
-    TileGeom best{};
     for (int W = 32; W <= MAX_NT * V && W <= Pmax; W += 32) {
         const int Wb = W + q.R - 1;
         const int NTc = ((Wb + V - 1) / V + 31) / 32 * 32;
@@ -245,16 +253,47 @@ pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
             const double rows = 17.0 + 2.0 * t.NG * (double)q.ell / q.R;
             const double sel = 23.0;
             const double eff = t.NT >= 384 ? 1.0 : t.NT / 384.0;
-            const double cost = ((double)Wb / W * rows + sel) / eff;
-            if (cost < best_cost) {
-                best_cost = cost;
-                best = t;
+            out->push_back(TileCand{((double)Wb / W * rows + sel) / eff, W, ngw, t});
+        }
+    }
+}
+
+// Layouts chosen by the autotuner (pastila_tune), process-wide, keyed by
+// (precision, m, ell, k): tile width and row groups asked.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;
+uint64_t g_tune_gen = 0;  // bumped by every change of the table (captured graphs depend on it)
+
+uint64_t tune_generation() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune_gen;
+}
+
+template <typename real>
+std::tuple<int, int, int, int> tune_key(const MParams& q) {
+    return std::make_tuple((int)sizeof(real), q.m, q.ell, q.k);
+}
+
+template <typename real, int V>
+pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(tune_key<real>(q));
+        if (it != g_tuned.end()) {
+            const TileGeom t = tile_geom<real>(q.m, q.ell, it->second.first, V, it->second.second);
+            if (t.NT <= MAX_NT && t.bytes <= limit) {
+                *g = t;
+                return PASTILA_OK;
             }
         }
     }
-    if (best_cost >= 1e300)
-        return fail(PASTILA_EINVAL, "m = %d, ell = %d: the tile does not fit in shared memory", q.m, q.ell);
-    *g = best;
+    std::vector<TileCand> c;
+    tile_candidates<real, V>(limit, q, &c);
+    if (c.empty()) return fail(PASTILA_EINVAL, "m = %d, ell = %d: the tile does not fit in shared memory", q.m, q.ell);
+    size_t b = 0;
+    for (size_t i = 1; i < c.size(); ++i)
+        if (c[i].cost < c[b].cost) b = i;
+    *g = c[b].g;
     return PASTILA_OK;
 }
 
@@ -288,6 +327,30 @@ pastila_status drain_events(pastila_series* h) {
 
 __global__ void init_dmax_kernel(unsigned long long* k) { *k = KeyOf<double>::enc(0.0); }
 __global__ void dec_dmax_kernel(const unsigned long long* k, double* o) { *o = KeyOf<double>::dec(*k); }
+
+template <typename real, int V>
+ProfileArgs<real> profile_args(const pastila_series* h, const MParams& q, const Stats* st, const TileGeom& g,
+                               real* D, unsigned long long* dmax) {
+    ProfileArgs<real> A;
+    A.T = h->T;
+    A.mu = st->mu;
+    A.a = (const real*)st->a;
+    A.df = (const real*)st->df;
+    A.dg = (const real*)st->dg;
+    A.n = h->n;
+    A.C = q.C;
+    A.P = q.P;
+    A.m = q.m;
+    A.ell = q.ell;
+    A.k = q.k;
+    A.R = q.R;
+    A.S = q.S;
+    A.W = g.W;
+    A.ntiles = (int)((q.P + g.W - 1) / g.W);
+    A.D = D;
+    A.dmax_key = dmax;
+    return A;
+}
 
 template <typename real, int V>
 pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st, real* D,
@@ -338,6 +401,86 @@ pastila_status launch_profiles(pastila_series* h, const MParams& q, void* D, uns
     TRY(ensure_stats(h, q.ell, &st));
     if (h->prec == PASTILA_FP64) return launch_profiles_t<double, V_F64>(h, q, st, (double*)D, dmax);
     return launch_profiles_t<float, V_F32>(h, q, st, (float*)D, dmax);
+}
+
+// Autotuner: times the cost model's layout and its closest rivals (the cheapest
+// of every thread count first, then by modelled cost, within 1.5x of the
+// model's best) on the first min(S, 64) segments of this series, and keeps the
+// fastest for (precision, m, ell, k).
+template <typename real, int V>
+pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila_tune_result* res) {
+    std::vector<TileCand> c;
+    tile_candidates<real, V>((size_t)h->smem_optin, q, &c);
+    if (c.empty()) return fail(PASTILA_EINVAL, "m = %d, ell = %d: the tile does not fit in shared memory", q.m, q.ell);
+    std::stable_sort(c.begin(), c.end(), [](const TileCand& x, const TileCand& y) { return x.cost < y.cost; });
+    std::vector<TileCand> pick;
+    std::vector<int> nts;
+    for (const TileCand& t : c) {  // cheapest layout of every thread count
+        if ((int)pick.size() >= max_cand || t.cost > 1.5 * c[0].cost) break;
+        if (std::find(nts.begin(), nts.end(), t.g.NT) == nts.end()) {
+            nts.push_back(t.g.NT);
+            pick.push_back(t);
+        }
+    }
+    for (const TileCand& t : c) {  // then by modelled cost
+        if ((int)pick.size() >= max_cand || t.cost > 1.5 * c[0].cost) break;
+        bool have = false;
+        for (const TileCand& u : pick) have |= u.W == t.W && u.g.NG == t.g.NG;
+        if (!have) pick.push_back(t);
+    }
+    Stats* st;
+    TRY(ensure_stats(h, q.ell, &st));
+    const int S_sub = q.S < 64 ? q.S : 64;
+    void *D, *dk;
+    TRY(scratch(h, "tune_D", sizeof(real) * (size_t)S_sub * (size_t)q.P, &D));
+    TRY(scratch(h, "tune_dmax", 8, &dk));
+    CK(cudaFuncSetAttribute(profile_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            h->smem_optin));
+    cudaEvent_t e0, e1;
+    TRY(get_event(h, &e0));
+    TRY(get_event(h, &e1));
+    double best_ms = 1e300, model_ms = 0.0;
+    size_t bi = 0;
+    for (size_t i = 0; i < pick.size(); ++i) {
+        const TileGeom& g = pick[i].g;
+        const ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, (real*)D, (unsigned long long*)dk);
+        const dim3 grid((unsigned)A.ntiles, (unsigned)S_sub);
+        profile_tiles_kernel<real, V><<<grid, g.NT, g.bytes, h->stream>>>(A, g);  // warm-up
+        float best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaEventRecord(e0, h->stream));
+            profile_tiles_kernel<real, V><<<grid, g.NT, g.bytes, h->stream>>>(A, g);
+            CK(cudaEventRecord(e1, h->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            best = ms < best ? ms : best;
+        }
+        CK(cudaGetLastError());
+        h->launches += 3;
+        if (i == 0) model_ms = best;
+        if (best < best_ms) {
+            best_ms = best;
+            bi = i;
+        }
+    }
+    h->ev_free.push_back(e0);
+    h->ev_free.push_back(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key<real>(q)] = {pick[bi].W, pick[bi].ngw};
+        g_tune_gen++;
+    }
+    if (res) {
+        res->m = q.m;
+        res->W = pick[bi].g.W;
+        res->NG = pick[bi].g.NG;
+        res->NT = pick[bi].g.NT;
+        res->candidates = (int32_t)pick.size();
+        res->ms_model = model_ms;
+        res->ms_best = best_ms;
+    }
+    return PASTILA_OK;
 }
 
 // Greedy (eqs. 16-17) + neighbours (eqs. 6-8) on a resident D.  Results stay on
@@ -594,8 +737,9 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
         const TileGeom& g = items[i].G;
         cells += (double)qs[i].S * (double)items[i].A.ntiles * (double)qs[i].R * (double)g.Wb;
     }
+    const uint64_t tgen = tune_generation();
     const bool same = gr.ms == std::vector<int32_t>(m_list, m_list + n_m) && gr.rule.ell == rule.ell &&
-                      gr.rule.k == rule.k && gr.K == K && gr.gen == h->alloc_gen;
+                      gr.rule.k == rule.k && gr.K == K && gr.gen == h->alloc_gen && gr.tune_gen == tgen;
     if (!same) {
         for (auto& e : gr.exec)
             if (e) cudaGraphExecDestroy(e);
@@ -604,6 +748,7 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
         gr.rule = rule;
         gr.K = K;
         gr.gen = h->alloc_gen;
+        gr.tune_gen = tgen;
         gr.calls = 0;
     }
     gr.calls++;
@@ -716,6 +861,31 @@ pastila_status check_finite(const double* T, int64_t n) {
 extern "C" {
 
 const char* pastila_last_error(void) { return g_err.c_str(); }
+
+pastila_status pastila_tune(pastila_series* h, const int32_t* m_list, int32_t n_m, pastila_mparams rule,
+                            int32_t max_candidates, pastila_tune_result* out) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!m_list || n_m < 1) return fail(PASTILA_EINVAL, "m_list is empty");
+    if (max_candidates < 1 || max_candidates > 64)
+        return fail(PASTILA_EINVAL, "max_candidates = %d: must be in [1, 64]", max_candidates);
+    TRY(set_device(h));
+    for (int i = 0; i < n_m; ++i) {
+        MParams q;
+        TRY(resolve(h, m_list[i], rule, &q));
+        if (h->prec == PASTILA_FP64)
+            TRY(tune_t<double, V_F64>(h, q, max_candidates, out ? out + i : nullptr));
+        else
+            TRY(tune_t<float, V_F32>(h, q, max_candidates, out ? out + i : nullptr));
+    }
+    return PASTILA_OK;
+}
+
+void pastila_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
+    g_tune_gen++;
+}
 
 pastila_status pastila_create(pastila_series** out, const double* T, int64_t n, int device,
                               size_t mem_budget_bytes, pastila_precision prec) {

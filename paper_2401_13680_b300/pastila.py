@@ -50,6 +50,11 @@ class EngineCounters(ctypes.Structure):
                 ("now", ctypes.c_double)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("W", ctypes.c_int32), ("NG", ctypes.c_int32), ("NT", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("ms_model", ctypes.c_double), ("ms_best", ctypes.c_double)]
+
+
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE, JOB_FAILED, JOB_CANCELLED = range(5)
 
 
@@ -101,6 +106,10 @@ def load(path: str | None = None):
         lib.pastila_tile_time.restype = S
         lib.pastila_greedy_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp]
         lib.pastila_greedy_noalloc.restype = S
+        lib.pastila_tune.argtypes = [_vp, _vp, ctypes.c_int32, MParams, ctypes.c_int32, ctypes.POINTER(TuneResult)]
+        lib.pastila_tune.restype = S
+        lib.pastila_tune_clear.argtypes = []
+        lib.pastila_tune_clear.restype = None
         lib.pastila_engine_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(EngineConfig)]
         lib.pastila_engine_create.restype = S
         lib.pastila_engine_submit.argtypes = [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32, MParams,
@@ -228,6 +237,14 @@ class Series:
                                        _ptr(prof) if want_profiles else None))
         return _recs(out), labels, prof
 
+    def tune(self, ms, max_candidates: int = 8, ell: int = 0, k: int = 0):
+        """``pastila_tune``: time candidate tile layouts per m and keep the fastest
+        (process-wide); returns one dict per m."""
+        ms = np.ascontiguousarray(ms, dtype=np.int32)
+        out = (TuneResult * ms.shape[0])()
+        _check(load().pastila_tune(self._h, _ptr(ms), ms.shape[0], MParams(ell, k), max_candidates, out))
+        return [{f: getattr(r, f) for f, _ in TuneResult._fields_} for r in out]
+
     def select_length(self, ms, K: int, ell: int = 0, k: int = 0):
         """(m_best, crit per m, K records of m_best) -- ``pastila_select_length``."""
         ms = np.ascontiguousarray(ms, dtype=np.int32)
@@ -311,6 +328,11 @@ class Engine:
         c = EngineCounters()
         _check(load().pastila_engine_stats(self._h, ctypes.byref(c)))
         return {f: getattr(c, f) for f, _ in EngineCounters._fields_}
+
+
+def tune_clear():
+    """``pastila_tune_clear``: back to the cost model's layouts."""
+    load().pastila_tune_clear()
 
 
 def greedy_noalloc(D_ptr: int, S: int, P: int, K: int, chosen_ptr: int, area_ptr: int,
