@@ -258,3 +258,41 @@ def test_select_length_batched_graph_replay(lib):
         fresh = h2.select_length(ms, K)
     for g in got:
         assert g[0] == fresh[0] and np.array_equal(g[1], fresh[1]) and g[2] == fresh[2]
+
+
+def test_large_drift_series_full_size_sampled(lib):
+    """n = 1,000,000 (eight regimes on a random-walk drift), m = 256, ell = 128,
+    FP32, the whole S x P = 3,906 x 999,745 profile set (15.6 GB) resident on the
+    device: 32 seeded segments x 4 seeded blocks of 256 positions checked cell by
+    cell against the oracle's PSF steps, every value in [0, 2 sqrt(ell)], each
+    sampled segment zero at its own offset, and D_max equal to the maximum of D;
+    then the greedy snippets (K = 6) of the same profile set."""
+    import torch
+    from paper_2401_13680_b300 import pastila
+    s = synth.large_drift()
+    m, ell, k, K = 256, 128, 26, 6
+    n = s.T.shape[0]
+    S, P = n // m, n - m + 1
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(2024)
+    segs = np.sort(rng.choice(S, 32, replace=False))
+    blocks = rng.integers(0, P - 256, 4)
+    with _series(s.T, 0) as h:
+        D = torch.empty((S, P), dtype=torch.float32, device=dev)
+        dmax = torch.zeros(1, dtype=torch.float64, device=dev)
+        h.profiles_device(m, D.data_ptr(), dmax.data_ptr())
+        torch.cuda.synchronize()
+        assert float(D.min()) >= 0.0 and float(D.max()) <= 2 * np.sqrt(ell) * (1 + 1e-6)
+        assert float(dmax.item()) == pytest.approx(float(D.max()), rel=1e-7)
+        Ds = D[torch.from_numpy(segs).to(dev)]
+        for b in blocks:
+            ref = oracle.profiles_range(s.T, m, ell, k, segs, int(b), int(b) + 256)
+            got = Ds[:, int(b):int(b) + 256].cpu().numpy()
+            assert_profiles_close(got, ref, ell, TOL[0])
+        own = Ds.cpu().numpy()[np.arange(32), segs * m]
+        assert np.all(own == 0.0)
+        del D, Ds
+        torch.cuda.empty_cache()
+        recs, _, _ = h.snippets(m, K)
+    assert len({r[0] for r in recs}) == K
+    assert sum(r[2] for r in recs) == pytest.approx(1.0)
