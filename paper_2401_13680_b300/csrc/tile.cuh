@@ -169,26 +169,37 @@ __device__ __forceinline__ T grp_max(T v, int G) {
     return v;
 }
 
+// The working-precision type whose order-preserving key type is key_t.
+template <typename key_t> struct KeyReal;
+template <> struct KeyReal<uint32_t> { typedef float type; };
+template <> struct KeyReal<unsigned long long> { typedef double type; };
+
 constexpr int SEL_CACHE = 9;  // keys of one position held per lane, per half (rows, window)
 
 // k-th largest key (kk-th, 1-based) of P_ABBA for a run of consecutive tile
 // positions, one run per group of G lanes; all groups of a warp step through
 // their runs together (npos_warp steps; a group past its own run idles).  Lane
 // gl of a group holds rows gl, gl+G, ... of AB column p and the window entries
-// CB[p+gl], CB[p+gl+G], ... in registers.  The first position of a run is found
-// by bisection over the key range; every later one starts from the previous
-// answer tau (consecutive positions share all but a few of their 2R values, so
-// the rank of tau moves little): a pass counts the keys >= tau and > tau and
-// finds the nearest keys below and above tau, which settles the answer when its
-// rank moved by at most one; otherwise tau steps to that neighbour and the pass
-// repeats, and after three steps a bisection inside the bracket already known
-// finishes.  Control flow is uniform across the warp: decisions are per-group
-// selects, loops run while any group of the warp still works.
+// CB[p+gl], CB[p+gl+G], ... in registers.  Every position after the first of
+// a run starts from the previous answer tau (consecutive positions share all
+// but a few of their 2R values, so the rank of tau moves little): a pass counts
+// the keys >= tau and > tau and finds the nearest keys below and above tau,
+// which settles the answer when its rank moved by at most one; otherwise tau
+// steps to that neighbour and the pass repeats.  The first position of a run,
+// and a position still open after three steps, is searched inside its bracket
+// of keys: the pivot interpolates between the values of two bounds with known
+// counts (#{>= L} >= kk > #{>= H}) at the rank kk, and once a bound's count is
+// exactly kk (or kk - 1 at H) one min (max) pass gives the answer; a bisection
+// over the keys finishes anything still open after six pivots.  Control flow
+// is uniform across the warp: decisions are per-group selects, loops run while
+// any group of the warp still works.
 template <typename key_t, typename Out>
 __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int RS, int LA, int V,
                                              const key_t* __restrict__ CB, int R, int kk, int p_begin,
                                              int npos, int npos_warp, int G, int gl, Out out) {
     // requires R <= G * SEL_CACHE: every value of a position sits in the registers of its group
+    typedef KeyOf<typename KeyReal<key_t>::type> K;
+    typedef typename KeyReal<key_t>::type real;
     const unsigned FULL = 0xffffffffu;
     const key_t KMAX = ~(key_t)0;
     const int nr = (R - gl + G - 1) / G;  // values per half held by this lane
@@ -250,22 +261,66 @@ __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int R
                 if (__all_sync(FULL, done)) break;
             }
         }
-        // bisection in [lo, hi] (the whole key range at a run's first position),
-        // tightened to the keys present
+        // search inside [lo, hi] (the whole key range at a run's first position):
+        // interpolation on the values between two counted bounds, then the exact
+        // answer by one min/max pass once a bound's count is exactly kk (or kk - 1
+        // just above it); a bisection over the keys finishes whatever is left
         const bool need = !done;
         if (__any_sync(FULL, need)) {
             key_t mn = KMAX, mx = 0;
+            uint32_t cb = 0;  // #{>= lo} + 65536 * #{> hi}
 #pragma unroll
             for (int j = 0; j < SEL_CACHE; ++j) {
                 if (j < nr) {
                     const key_t a = va[j], b = vb[j];
                     if (a >= lo && a <= hi) { mn = a < mn ? a : mn; mx = a > mx ? a : mx; }
                     if (b >= lo && b <= hi) { mn = b < mn ? b : mn; mx = b > mx ? b : mx; }
+                    cb += (a >= lo ? 1u : 0u) + (a > hi ? 65536u : 0u) + (b >= lo ? 1u : 0u) + (b > hi ? 65536u : 0u);
                 }
             }
             mn = grp_min(mn, G);
             mx = grp_max(mx, G);
-            key_t blo = need ? mn : tau, bhi = need ? mx : tau;
+            cb = grp_sum(cb, G);
+            // bracket [L, H): #{>= L} = cL >= kk > cH = #{>= H}
+            key_t L = mn, H = mx + (key_t)1;
+            int cL = (int)(cb & 0xffffu), cH = (int)(cb >> 16);
+            auto open = [&]() { return need && cL != kk && cH != kk - 1 && H - L > (key_t)1; };
+            for (int itr = 0; itr < 6 && __any_sync(FULL, open()); ++itr) {
+                const bool act = open();
+                const real fL = K::dec(L), fH = K::dec(H);
+                const real f = ((real)(cL - kk) + (real)0.5) / (real)(cL - cH);
+                key_t pv = K::enc(fL + (fH - fL) * f);
+                if (!(pv > L && pv < H)) pv = L + (key_t)((H - L) >> 1);
+                uint32_t c = 0;
+#pragma unroll
+                for (int j = 0; j < SEL_CACHE; ++j)
+                    if (j < nr) c += (va[j] >= pv ? 1u : 0u) + (vb[j] >= pv ? 1u : 0u);
+                c = grp_sum(c, G);
+                if (act) {
+                    if ((int)c >= kk) { L = pv; cL = (int)c; } else { H = pv; cH = (int)c; }
+                }
+            }
+            // exactly kk keys >= L: the answer is the smallest of them; exactly
+            // kk - 1 keys >= H: the largest key below H
+            const bool by_min = need && cL == kk, by_max = need && !by_min && cH == kk - 1;
+            if (__any_sync(FULL, by_min || by_max)) {
+                key_t lo_ge = KMAX, hi_lt = 0;
+#pragma unroll
+                for (int j = 0; j < SEL_CACHE; ++j) {
+                    if (j < nr) {
+                        const key_t a = va[j], b = vb[j];
+                        if (a >= L) lo_ge = a < lo_ge ? a : lo_ge;
+                        if (b >= L) lo_ge = b < lo_ge ? b : lo_ge;
+                        if (a < H) hi_lt = a > hi_lt ? a : hi_lt;
+                        if (b < H) hi_lt = b > hi_lt ? b : hi_lt;
+                    }
+                }
+                lo_ge = grp_min(lo_ge, G);
+                hi_lt = grp_max(hi_lt, G);
+                if (by_min) { L = lo_ge; H = lo_ge + (key_t)1; }
+                if (by_max) { L = hi_lt; H = hi_lt + (key_t)1; }
+            }
+            key_t blo = need ? L : tau, bhi = need ? H - (key_t)1 : tau;
             while (__any_sync(FULL, blo < bhi)) {
                 const key_t mid = blo + (key_t)((bhi - blo) >> 1) + 1;
                 uint32_t c = 0;
