@@ -72,7 +72,7 @@ struct ProfileArgs {
 // Shared-memory layout and thread layout of one tile; identical on host and device.
 struct TileGeom {
     int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, LP, ell, m;
-    size_t off_AB, off_CB, off_PRE, off_CM, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
+    size_t off_AB, off_CB, off_PRE, off_CM, off_PSW, off_SSW, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
         off_Ts, off_Tsl, off_q, bytes;
 };
 
@@ -107,6 +107,8 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.off_CB = o;   o = align16(o + sizeof(key_t) * (size_t)(g.Wb + 32));
     g.off_PRE = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)V * g.LP);
     g.off_CM = o;   o = align16(o + sizeof(real) * NG * 2 * (size_t)(g.NTc + 1));
+    g.off_PSW = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)g.NTc);
+    g.off_SSW = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)g.NTc);
     g.off_XCH = o;  o = align16(o + sizeof(real) * NG * 4 * (size_t)g.NWc);
     g.off_row = o;  o = align16(o + sizeof(real) * 5 * (size_t)g.R);
     g.off_left = o; o = align16(o + sizeof(real) * (size_t)g.R);
@@ -565,6 +567,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     key_t* CB = (key_t*)(sm + G.off_CB);
     real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * LP;  // this group's [parity][V][LP]
     real* CM = (real*)(sm + G.off_CM) + (size_t)g * 2 * (NTc + 1);   // [parity][NTc + 1]
+    real* PSW = (real*)(sm + G.off_PSW) + (size_t)g * 2 * NTc;       // [parity][NTc]: CM prefix maxima
+    real* SSW = (real*)(sm + G.off_SSW) + (size_t)g * 2 * NTc;       // and suffix maxima within each warp
     real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][hi/lo][warp]
     real* rdf = (real*)(sm + G.off_row);
     real* rdg = rdf + R;
@@ -718,8 +722,11 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             const int par = sidx & 1;
             real* PREp = PRE + par * V * LP;
             real* CMp = CM + par * (NTc + 1);
+            real* PSWp = PSW + par * NTc;
+            real* SSWp = SSW + par * NTc;
             // logical column v of this thread lives in register (v - jj) mod V
             real rho[V];
+            real pre = NEG;  // this thread's chunk maximum
             if (active) {
                 if (sidx > 0) {
                     const int Pout = (V - jj) % V;  // register of the previous row's last column
@@ -772,7 +779,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 }
 #pragma unroll
                 for (int v = 0; v < V; ++v) cmx[v] = rmax(cmx[v], rho[v]);
-                real pre = rho[0];
+                pre = rho[0];
                 PREp[t] = pre;
 #pragma unroll
                 for (int v = 1; v < V; ++v) {
@@ -781,8 +788,45 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 }
                 CMp[t] = pre;
                 if (t == 0) CMp[NTc] = NEG;
+                if (!small_R && q0 >= 2) {  // prefix and suffix maxima of the chunk maxima within each warp
+                    real ps = pre, ss = pre;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const real u = __shfl_up_sync(FULL, ps, o);
+                        const real d = __shfl_down_sync(FULL, ss, o);
+                        if (lane >= o) ps = rmax(ps, u);
+                        if (lane + o < 32) ss = rmax(ss, d);
+                    }
+                    PSWp[t] = ps;
+                    SSWp[t] = ss;
+                }
             }
             __syncthreads();
+            // maximum of the whole chunks t+1 .. t+q0-1 strictly inside the windows of
+            // this thread's positions: a window inside this warp from a sparse table
+            // of shuffles (max over 2^k chunks from a lane, twice); a window reaching
+            // into later warps from the suffix maximum of its first warp, the warp
+            // maxima in between and the prefix maximum of its last warp
+            real mid = NEG;
+            if (active && !small_R && q0 >= 2) {
+                const int L = q0 - 1, z = t + L;
+                const bool inwarp = (z >> 5) == (t >> 5);
+                if (L <= 31) {  // uniform: some windows of the warp stay inside it (two spans of 2^k <= 16)
+                    const int k = 31 - __clz(L);
+                    real lv = pre;
+                    for (int s2 = 0; s2 < k; ++s2) lv = rmax(lv, __shfl_down_sync(FULL, lv, 1 << s2));
+                    const real m1 = __shfl_sync(FULL, lv, (lane + 1) & 31);
+                    const real m2 = __shfl_sync(FULL, lv, (lane + L - (1 << k) + 1) & 31);
+                    if (inwarp) mid = rmax(m1, m2);
+                }
+                if (!inwarp && owns_positions) {
+                    const int wa = (t + 1) >> 5, wz = z >> 5;
+                    // t + 1 opens the next warp (lane 31) and the window ends in it: a prefix
+                    real x = wa == wz ? PSWp[z] : rmax(SSWp[t + 1], PSWp[z]);
+                    for (int w = wa + 1; w < wz; ++w) x = rmax(x, PSWp[w * 32 + 31]);
+                    mid = x;
+                }
+            }
             if (active && owns_positions) {
                 real suf[V];
                 suf[V - 1] = rho[V - 1];
@@ -790,16 +834,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
                 key_t* ABr = AB + (size_t)r * RS + t;
                 if (!small_R) {
-                    // whole chunks strictly inside the window: t+1 .. t+q0-1 for small i,
-                    // one more (t+q0) once the window end moves into chunk t+q0+1
-                    real mid = NEG;
-                    int c = t + 1;
-                    const int cend = t + q0;
-                    for (; c + 4 <= cend; c += 4) {
-                        const real a0 = CMp[c], a1 = CMp[c + 1], a2 = CMp[c + 2], a3 = CMp[c + 3];
-                        mid = rmax(mid, rmax(rmax(a0, a1), rmax(a2, a3)));
-                    }
-                    for (; c < cend; ++c) mid = rmax(mid, CMp[c]);
+                    // whole chunks strictly inside the window: t+1 .. t+q0-1 (mid) for small
+                    // i, one more (t+q0) once the window end moves into chunk t+q0+1
                     const real mid1 = rmax(mid, CMp[t + q0]);
 #pragma unroll
                     for (int i = 0; i < V; ++i) {
