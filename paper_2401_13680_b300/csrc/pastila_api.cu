@@ -261,7 +261,7 @@ void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out)
 // Layouts chosen by the autotuner (pastila_tune), process-wide, keyed by
 // (precision, m, ell, k): tile width and row groups asked.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;
+std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> g_tuned;  // W, row groups asked, GS
 uint64_t g_tune_gen = 0;  // bumped by every change of the table (captured graphs depend on it)
 
 uint64_t tune_generation() {
@@ -280,7 +280,8 @@ pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key<real>(q));
         if (it != g_tuned.end()) {
-            const TileGeom t = tile_geom<real>(q.m, q.ell, it->second.first, V, it->second.second);
+            TileGeom t = tile_geom<real>(q.m, q.ell, std::get<0>(it->second), V, std::get<1>(it->second));
+            t.GS = std::get<2>(it->second);
             if (t.NT <= MAX_NT && t.bytes <= limit) {
                 *g = t;
                 return PASTILA_OK;
@@ -439,6 +440,17 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     cudaEvent_t e0, e1;
     TRY(get_event(h, &e0));
     TRY(get_event(h, &e1));
+    // every picked layout with the default selection group width, and with twice
+    // that width where the grouped selector runs (longer runs per group)
+    {
+        const size_t np = pick.size();
+        for (size_t i = 0; i < np; ++i)
+            if (pick[i].g.R <= 32 * SEL_CACHE && pick[i].g.GS < 32) {
+                TileCand t = pick[i];
+                t.g.GS *= 2;
+                pick.push_back(t);
+            }
+    }
     double best_ms = 1e300, model_ms = 0.0;
     size_t bi = 0;
     for (size_t i = 0; i < pick.size(); ++i) {
@@ -468,7 +480,7 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     h->ev_free.push_back(e1);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key<real>(q)] = {pick[bi].W, pick[bi].ngw};
+        g_tuned[tune_key<real>(q)] = std::make_tuple(pick[bi].W, pick[bi].ngw, pick[bi].g.GS);
         g_tune_gen++;
     }
     if (res) {
@@ -476,6 +488,7 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
         res->W = pick[bi].g.W;
         res->NG = pick[bi].g.NG;
         res->NT = pick[bi].g.NT;
+        res->GS = pick[bi].g.GS;
         res->candidates = (int32_t)pick.size();
         res->ms_model = model_ms;
         res->ms_best = best_ms;

@@ -72,6 +72,7 @@ struct ProfileArgs {
 // Shared-memory layout and thread layout of one tile; identical on host and device.
 struct TileGeom {
     int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, LP, ell, m;
+    int GS;  // lanes per selection group (R <= 288: 4, 8, 16 or 32 with R <= 9 GS)
     size_t off_AB, off_CB, off_PRE, off_CM, off_PSW, off_SSW, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
         off_Ts, off_Tsl, off_q, bytes;
 };
@@ -101,6 +102,7 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.LA = (W + V - 1) / V;
     g.RS = (V * g.LA) | 1;
     g.LP = g.NTc + 1;  // chunk prefix maxima: [V][LP], thread t at t (+ chunk offset)
+    g.GS = g.R <= 36 ? 4 : (g.R <= 72 ? 8 : (g.R <= 144 ? 16 : 32));  // the narrowest that fits 9 values per half
     const size_t NG = (size_t)g.NG;
     size_t o = 0;
     g.off_AB = o;   o = align16(o + sizeof(key_t) * (size_t)g.R * g.RS);
@@ -901,7 +903,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     if (keyed) {
         // groups of GS lanes, each with a run of positions; a lane caches at most
         // SEL_CACHE values of each half
-        const int GS = R <= 4 * SEL_CACHE ? 4 : (R <= 8 * SEL_CACHE ? 8 : (R <= 16 * SEL_CACHE ? 16 : 32));
+        const int GS = G.GS;
         const int ngroups = BD / GS;
         const int grp = tid / GS, gl = tid % GS;
         const int PW = (Wp + ngroups - 1) / ngroups;

@@ -52,7 +52,7 @@ class EngineCounters(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("W", ctypes.c_int32), ("NG", ctypes.c_int32), ("NT", ctypes.c_int32),
-                ("candidates", ctypes.c_int32), ("ms_model", ctypes.c_double), ("ms_best", ctypes.c_double)]
+                ("GS", ctypes.c_int32), ("candidates", ctypes.c_int32), ("ms_model", ctypes.c_double), ("ms_best", ctypes.c_double)]
 
 
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE, JOB_FAILED, JOB_CANCELLED = range(5)
