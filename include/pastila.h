@@ -289,6 +289,24 @@ pastila_status pastila_engine_stats(pastila_engine* e, pastila_engine_counters* 
  * scheduler and frees everything.  NULL is a no-op. */
 void pastila_engine_destroy(pastila_engine* e);
 
+/* The greedy snippet search of pastila_snippets without materialising the S x P
+ * profile set, for lengths whose D does not fit the budget or the device
+ * (pastila_snippets switches to it by itself when allocating D fails with
+ * ENOMEM).  Rows of D are recomputed by the profile kernel: one pass over all
+ * segments for each of the first two greedy steps, then only the rows whose
+ * area bound can still beat the best (the gain sum_p max(0, M_p - D_s(p)) of a
+ * segment never grows as M shrinks, so its last known gain bounds its next
+ * area).  Memory: K + 9 rows of P values, the FP64 partial sums of at most
+ * 256 MiB, and S doubles.  Results (records, labels, chosen profiles) are
+ * identical to pastila_snippets on the materialised D: every area it compares
+ * is computed exactly as there.  work_out (may be NULL) receives two values:
+ * full passes over the segments and rows recomputed.  No counterpart in the
+ * paper (Section 4.2 materialises D over a cluster).  Errors as
+ * pastila_snippets. */
+pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_mparams mp, int32_t K,
+                                         pastila_snippet* out, int32_t* labels_out, void* snippet_profiles_out,
+                                         int64_t* work_out);
+
 /* ----------------------------------------------------------- autotuner ---- */
 
 /* The tile layout of a length (positions per CTA W, row groups NG, threads NT,

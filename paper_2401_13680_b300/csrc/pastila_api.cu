@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <string>
@@ -332,7 +333,7 @@ __global__ void dec_dmax_kernel(const unsigned long long* k, double* o) { *o = K
 template <typename real, int V>
 ProfileArgs<real> profile_args(const pastila_series* h, const MParams& q, const Stats* st, const TileGeom& g,
                                real* D, unsigned long long* dmax) {
-    ProfileArgs<real> A;
+    ProfileArgs<real> A{};  // every field zero (M, part: the plain, non-streaming form)
     A.T = h->T;
     A.mu = st->mu;
     A.a = (const real*)st->a;
@@ -358,7 +359,7 @@ pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st,
                                  unsigned long long* dmax) {
     TileGeom g;
     TRY(choose_tile<real, V>(h, q, &g));
-    ProfileArgs<real> A;
+    ProfileArgs<real> A{};  // every field zero (M, part: the plain, non-streaming form)
     A.T = h->T;
     A.mu = st->mu;
     A.a = (const real*)st->a;
@@ -547,6 +548,183 @@ pastila_status snippets_on_device(pastila_series* h, const MParams& q, const voi
     if (h->prec == PASTILA_FP64)
         return snippets_on_device_t<double>(h, q, (const double*)D, K, labels_dev, dmax, crit_dev);
     return snippets_on_device_t<float>(h, q, (const float*)D, K, labels_dev, dmax, crit_dev);
+}
+
+// ---------------------------------------------------------------------------
+// Greedy snippet search without the S x P profile set (eqs. 16-17 by lazy
+// evaluation), for lengths whose D does not fit.  Rows of D are recomputed by
+// the tile kernel; the profiles of the K chosen segments are kept.
+//
+// Steps 0 and 1 run one streaming pass over all segments, which gives every
+// segment's area sum_p min(M_p, D_s(p)) up to FP64 rounding (relative error far
+// below 1e-9); the segments whose area lies within that margin of the best are
+// recomputed exactly (their rows, then the same per-row sum as the
+// materialized path), and the exact minimum wins (lowest index on ties).  From
+// step 2 the gain of a segment, sum_p M_p - area, can only shrink as M shrinks,
+// so the last gain known for it bounds its area from below; segments are
+// recomputed in order of that bound until the bound passes the best exact area.
+// Every choice and area is therefore the one the materialized search makes.
+// ---------------------------------------------------------------------------
+template <typename real, int V>
+pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, int32_t* labels_out,
+                                   void* prof_out, int64_t* work) {
+    const int S = q.S;
+    const int64_t P = q.P;
+    const size_t rs = sizeof(real);
+    constexpr int BATCH = 8;
+    TileGeom g;
+    TRY(choose_tile<real, V>(h, q, &g));
+    Stats* st;
+    TRY(ensure_stats(h, q.ell, &st));
+    const int ntiles = (int)((P + g.W - 1) / g.W);
+    const int chunk = std::max(1, std::min(S, (int)((size_t)(32u << 20) / (size_t)ntiles)));  // <= 256 MiB of partials
+    void *part, *apx, *keep, *M, *rows, *segs, *rarea, *dk, *msum;
+    void *chosen_d, *aafter_d, *counts, *oi, *orank, *ofrac, *oarea, *lab = nullptr;
+    TRY(scratch(h, "st_part", 8 * (size_t)chunk * ntiles, &part));
+    TRY(scratch(h, "st_apx", 8 * (size_t)S, &apx));
+    TRY(scratch(h, "st_keep", rs * (size_t)K * P, &keep));
+    TRY(scratch(h, "st_M", rs * (size_t)P, &M));
+    TRY(scratch(h, "st_rows", rs * (size_t)BATCH * P, &rows));
+    TRY(scratch(h, "st_segs", 4 * BATCH, &segs));
+    TRY(scratch(h, "st_rarea", 8 * BATCH, &rarea));
+    TRY(scratch(h, "dmax", 8, &dk));
+    TRY(scratch(h, "st_msum", 8, &msum));
+    TRY(scratch(h, "sn_chosen", 4 * 64, &chosen_d));
+    TRY(scratch(h, "sn_aafter", 8 * 64, &aafter_d));
+    TRY(scratch(h, "sn_counts", 8 * 64, &counts));
+    TRY(scratch(h, "sn_oi", 4 * 64, &oi));
+    TRY(scratch(h, "sn_orank", 4 * 64, &orank));
+    TRY(scratch(h, "sn_ofrac", 8 * 64, &ofrac));
+    TRY(scratch(h, "sn_oarea", 8 * 64, &oarea));
+    if (labels_out) TRY(scratch(h, "labels", 4 * (size_t)P, &lab));
+    CK(cudaFuncSetAttribute(stream_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            h->smem_optin));
+    CK(cudaFuncSetAttribute(rows_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            h->smem_optin));
+    init_dmax_kernel<<<1, 1, 0, h->stream>>>((unsigned long long*)dk);
+    h->launches += 1;
+    ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, nullptr, (unsigned long long*)dk);
+    A.M = nullptr;
+    A.part = nullptr;
+    int64_t passes = 0, nrows = 0;
+    std::vector<double> hapx(S), ex(BATCH);
+    auto stream_pass = [&](const real* Mc) -> pastila_status {
+        ProfileArgs<real> B = A;
+        B.M = Mc;
+        B.part = (double*)part;
+        for (int s0 = 0; s0 < S; s0 += chunk) {
+            const int ns = std::min(chunk, S - s0);
+            stream_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)ns), g.NT, g.bytes, h->stream>>>(B, g, s0);
+            segment_sum_kernel<<<(ns + 255) / 256, 256, 0, h->stream>>>((const double*)part, ns, ntiles,
+                                                                        (double*)apx + s0);
+            h->launches += 2;
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(hapx.data(), apx, 8 * (size_t)S, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        passes++;
+        return PASTILA_OK;
+    };
+    auto exact = [&](const std::vector<int32_t>& ss, const real* Mc) -> pastila_status {
+        const int nb = (int)ss.size();
+        CK(cudaMemcpyAsync(segs, ss.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, h->stream));
+        ProfileArgs<real> B = A;
+        B.D = (real*)rows;
+        rows_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)nb), g.NT, g.bytes, h->stream>>>(
+            B, g, (const int32_t*)segs);
+        row_area_kernel<real><<<nb, AREA_THREADS, 0, h->stream>>>((const real*)rows, P, Mc, (double*)rarea);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(ex.data(), rarea, 8 * (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->launches += 2;
+        nrows += nb;
+        return PASTILA_OK;
+    };
+    auto curve_sum = [&](double* out) -> pastila_status {
+        curve_sum_kernel<real><<<1, AREA_THREADS, 0, h->stream>>>((const real*)M, P, (double*)msum);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(out, msum, 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        h->launches += 1;
+        return PASTILA_OK;
+    };
+    const double REL = 1e-9;  // far above the FP64 rounding of sums of at most 2^31 terms in these orders
+    std::vector<int32_t> chosen;
+    std::vector<double> aafter;
+    std::vector<char> taken(S, 0);
+    std::vector<double> U(S, 0.0), lb(S);  // gain bounds (from step 1 on), area bounds
+    std::vector<int32_t> order;
+    order.reserve(S);
+    for (int t = 0; t < K; ++t) {
+        const real* Mc = t ? (const real*)M : nullptr;
+        double msum_t = 0.0;
+        if (t >= 1) TRY(curve_sum(&msum_t));
+        if (t <= 1) {
+            TRY(stream_pass(Mc));
+            for (int s = 0; s < S; ++s) {
+                lb[s] = hapx[s] - REL * std::fabs(hapx[s]);
+                if (t == 1) U[s] = msum_t - hapx[s] + REL * (msum_t + std::fabs(hapx[s]));
+            }
+        } else {
+            for (int s = 0; s < S; ++s) lb[s] = msum_t - U[s] - REL * msum_t;
+        }
+        order.clear();
+        for (int s = 0; s < S; ++s)
+            if (!taken[s]) order.push_back(s);
+        std::sort(order.begin(), order.end(),
+                  [&](int32_t x, int32_t y) { return lb[x] < lb[y] || (lb[x] == lb[y] && x < y); });
+        double best = std::numeric_limits<double>::infinity();
+        int32_t bs = -1;
+        size_t i = 0;
+        std::vector<int32_t> batch;
+        while (i < order.size() && lb[order[i]] <= best) {
+            batch.clear();
+            while (i < order.size() && (int)batch.size() < BATCH && lb[order[i]] <= best) batch.push_back(order[i++]);
+            TRY(exact(batch, Mc));
+            for (int j = 0; j < (int)batch.size(); ++j) {
+                const int32_t s = batch[j];
+                const double ar = ex[j];
+                if (t >= 1) U[s] = msum_t - ar + REL * msum_t;
+                if (ar < best || (ar == best && s < bs)) {
+                    best = ar;
+                    bs = s;
+                    CK(cudaMemcpyAsync((char*)keep + rs * (size_t)t * P, (const char*)rows + rs * (size_t)j * P,
+                                       rs * (size_t)P, cudaMemcpyDeviceToDevice, h->stream));
+                }
+            }
+        }
+        chosen.push_back(bs);
+        aafter.push_back(best);
+        taken[bs] = 1;
+        min_curve_kernel<real><<<(unsigned)((P + 255) / 256), 256, 0, h->stream>>>(
+            (const real*)keep + (size_t)t * P, P, t == 0 ? 1 : 0, (real*)M);
+        CK(cudaGetLastError());
+        h->launches += 1;
+    }
+    CK(cudaMemcpyAsync(chosen_d, chosen.data(), 4 * (size_t)K, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(aafter_d, aafter.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(counts, 0, 8 * 64, h->stream));
+    neighbors_rows_kernel<real><<<(unsigned)((P + 255) / 256), 256, 0, h->stream>>>(
+        (const real*)keep, P, (const int32_t*)chosen_d, K, (int32_t*)lab, (unsigned long long*)counts);
+    finalize_snippets_kernel<<<1, 1, 0, h->stream>>>((const int32_t*)chosen_d, (const double*)aafter_d,
+                                                     (const unsigned long long*)counts, K, P, (int32_t*)oi,
+                                                     (int32_t*)orank, (double*)ofrac, (double*)oarea);
+    CK(cudaGetLastError());
+    h->launches += 2;
+    if (labels_out) CK(cudaMemcpyAsync(labels_out, lab, 4 * (size_t)P, cudaMemcpyDeviceToHost, h->stream));
+    if (prof_out) CK(cudaMemcpyAsync(prof_out, keep, rs * (size_t)K * P, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (work) {
+        work[0] = passes;
+        work[1] = nrows;
+    }
+    return PASTILA_OK;
+}
+
+pastila_status streamed(pastila_series* h, const MParams& q, int K, int32_t* labels_out, void* prof_out,
+                        int64_t* work) {
+    if (h->prec == PASTILA_FP64) return snippets_streamed_t<double, V_F64>(h, q, K, labels_out, prof_out, work);
+    return snippets_streamed_t<float, V_F32>(h, q, K, labels_out, prof_out, work);
 }
 
 pastila_status read_snippets(pastila_series* h, int K, pastila_snippet* out) {
@@ -1057,7 +1235,15 @@ pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp
     const size_t rs = real_size(h);
     const size_t bytes = rs * (size_t)q.S * (size_t)q.P;
     void *D, *dk, *lab = nullptr;
-    TRY(scratch(h, "D", bytes, &D));
+    {
+        const pastila_status sd = scratch(h, "D", bytes, &D);
+        if (sd == PASTILA_ENOMEM) {  // D does not fit: search without it, same results
+            g_err.clear();
+            TRY(streamed(h, q, K, labels_out, snippet_profiles_out, nullptr));
+            return read_snippets(h, K, out);
+        }
+        TRY(sd);
+    }
     TRY(scratch(h, "dmax", 8, &dk));
     if (labels_out) TRY(scratch(h, "labels", 4 * (size_t)q.P, &lab));
     TRY(launch_profiles(h, q, D, (unsigned long long*)dk));
@@ -1074,6 +1260,21 @@ pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp
     }
     TRY(read_snippets(h, K, out));
     return PASTILA_OK;
+}
+
+pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_mparams mp, int32_t K,
+                                         pastila_snippet* out, int32_t* labels_out, void* snippet_profiles_out,
+                                         int64_t* work_out) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!out) return fail(PASTILA_EINVAL, "out is NULL");
+    TRY(set_device(h));
+    MParams q;
+    TRY(resolve(h, m, mp, &q));
+    if (K < 1 || K > q.S || K > 64)
+        return fail(PASTILA_EINVAL, "K = %d: must satisfy 1 <= K <= min(n / m, 64) = %d", K, q.S < 64 ? q.S : 64);
+    TRY(streamed(h, q, K, labels_out, snippet_profiles_out, work_out));
+    return read_snippets(h, K, out);
 }
 
 pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, int32_t n_m, pastila_mparams rule,

@@ -55,6 +55,84 @@ area_kernel(const real* __restrict__ D, int S, int64_t P, const real* __restrict
     if (threadIdx.x == 0) area[s] = tot;
 }
 
+// The same per-row sum as area_kernel (same loop and reduction order, hence the
+// same value to the last bit) for nrows contiguous rows: out[y] = sum_p
+// min(M_p, rows[y][p]) (M = nullptr: the row sum).  Grid: (nrows).
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS)
+row_area_kernel(const real* __restrict__ rows, int64_t P, const real* __restrict__ M, double* __restrict__ out) {
+    __shared__ double red[AREA_THREADS / 32];
+    const real* row = rows + (int64_t)blockIdx.x * P;
+    double acc = 0.0;
+    if (M == nullptr) {
+        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += (double)row[p];
+    } else {
+        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) {
+            const real d = row[p], mm = M[p];
+            acc += (double)(d < mm ? d : mm);
+        }
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = tot;
+}
+
+// out[s] = sum over its tiles of part[s][tile], in tile order.  One thread per segment.
+__global__ void segment_sum_kernel(const double* __restrict__ part, int S, int ntiles, double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double t = 0.0;
+    for (int i = 0; i < ntiles; ++i) t += part[(int64_t)s * ntiles + i];
+    out[s] = t;
+}
+
+// sum of the P values of M, FP64 (one CTA)
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS) curve_sum_kernel(const real* __restrict__ M, int64_t P,
+                                                                  double* __restrict__ out) {
+    __shared__ double red[AREA_THREADS / 32];
+    double acc = 0.0;
+    for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += (double)M[p];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) *out = tot;
+}
+
+// M <- row (first step) or min(M, row)
+template <typename real>
+__global__ void min_curve_kernel(const real* __restrict__ row, int64_t P, int first, real* __restrict__ M) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const real d = row[p];
+    M[p] = first ? d : (d < M[p] ? d : M[p]);
+}
+
+// Nearest snippet per position (eq. 6) from the K chosen profiles stored as
+// rows[t][p] (t in greedy order), lowest segment index on ties; counts[] must
+// start at 0.
+template <typename real>
+__global__ void neighbors_rows_kernel(const real* __restrict__ rows, int64_t P, const int32_t* __restrict__ chosen,
+                                      int K, int32_t* __restrict__ labels, unsigned long long* __restrict__ counts) {
+    __shared__ unsigned int local[64];
+    if (threadIdx.x < 64) local[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) {
+        int bt = 0;
+        real bv = rows[p];
+        for (int t = 1; t < K; ++t) {
+            const real v = rows[(int64_t)t * P + p];
+            if (v < bv || (v == bv && chosen[t] < chosen[bt])) {
+                bv = v;
+                bt = t;
+            }
+        }
+        if (labels) labels[p] = chosen[bt];
+        atomicAdd(&local[bt], 1u);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < K && local[threadIdx.x])
+        atomicAdd(&counts[threadIdx.x], (unsigned long long)local[threadIdx.x]);
+}
+
 // Greedy step: the unchosen segment with the smallest area (lowest index on
 // ties) becomes chosen[t]; area_after[t] records its area.  One CTA of 1024.
 __global__ void argmin_area_kernel(const double* __restrict__ area, int S, int32_t* __restrict__ chosen,

@@ -67,6 +67,12 @@ struct ProfileArgs {
     int ntiles;          // tiles per segment
     real* D;             // S x P output, row-major
     unsigned long long* dmax_key;  // KeyOf<double>::enc(max D), combined with atomicMax
+    // streaming form (part != nullptr): D is not written; every CTA writes
+    // part[(s - row_base) * ntiles + tile] = sum over its positions of
+    // min(M_p, D_s(p)) (FP64, fixed order; M = nullptr: of D_s(p)), the greedy
+    // areas without D
+    const real* M;
+    double* part;
 };
 
 // Shared-memory layout and thread layout of one tile; identical on host and device.
@@ -542,7 +548,7 @@ __device__ __forceinline__ void select_runs(const real* __restrict__ AB, int RS,
 
 template <typename real, int V>
 __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const TileGeom& G, int s,
-                                             int tt, unsigned char* __restrict__ sm) {
+                                             int tt, unsigned char* __restrict__ sm, int row_base = 0) {
     typedef KeyOf<real> K;
     typedef typename K::type key_t;
     const unsigned FULL = 0xffffffffu;
@@ -892,12 +898,19 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int kk = 2 * R > A.k ? A.k : 2 * R;
     const real two_ell = (real)(2 * ell);
     real tmax = 0;
-    real* Drow = A.D + (int64_t)s * A.P + p0;
+    real* Drow = A.D + (int64_t)(s - row_base) * A.P + p0;  // row s - row_base of the output
+    const bool streaming = A.part != nullptr;
+    double sacc = 0.0;
     auto emit = [&](int p, real rs) {
         real u = (real)1 - rs;
         u = u > (real)0 ? u : (real)0;
         const real d = sqrt(two_ell * u);
-        Drow[p] = d;
+        if (streaming) {
+            const real mm = A.M ? A.M[p0 + p] : d;
+            sacc += (double)(d < mm ? d : mm);
+        } else {
+            Drow[p] = d;
+        }
         tmax = d > tmax ? d : tmax;
     };
     if (keyed) {
@@ -921,6 +934,35 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     }
     const double wmax = warp_max(tmax);
     if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(wmax));
+    if (streaming) {  // this tile's area share: warps in order, then one store
+        __shared__ double red[16];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(FULL, sacc, o);
+        if (lane == 0) red[tid >> 5] = sacc;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (BD >> 5); ++w) tot += red[w];
+            A.part[(int64_t)(s - row_base) * A.ntiles + tt] = tot;
+        }
+    }
+}
+
+// Streaming form over segments s_begin .. s_begin + gridDim.y - 1: grid (ntiles, segments).
+template <typename real, int V>
+__global__ void __launch_bounds__(512) stream_tiles_kernel(ProfileArgs<real> A, TileGeom G, int s_begin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    profile_tile<real, V>(A, G, s_begin + (int)blockIdx.y, blockIdx.x, smem, s_begin);
+}
+
+// The profile rows of a list of segments: CTA (tile, y) computes segment
+// segs[y] into row y of A.D.  Grid: (ntiles, number of segments).
+template <typename real, int V>
+__global__ void __launch_bounds__(512) rows_tiles_kernel(ProfileArgs<real> A, TileGeom G,
+                                                         const int32_t* __restrict__ segs) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int s = segs[blockIdx.y];
+    profile_tile<real, V>(A, G, s, blockIdx.x, smem, s - (int)blockIdx.y);
 }
 
 // One CTA per (tile, segment): grid (ntiles, S).

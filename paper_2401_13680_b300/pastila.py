@@ -106,6 +106,9 @@ def load(path: str | None = None):
         lib.pastila_tile_time.restype = S
         lib.pastila_greedy_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp]
         lib.pastila_greedy_noalloc.restype = S
+        lib.pastila_snippets_streamed.argtypes = [_vp, ctypes.c_int32, MParams, ctypes.c_int32,
+                                                  ctypes.POINTER(Snippet), _vp, _vp, ctypes.POINTER(ctypes.c_int64)]
+        lib.pastila_snippets_streamed.restype = S
         lib.pastila_tune.argtypes = [_vp, _vp, ctypes.c_int32, MParams, ctypes.c_int32, ctypes.POINTER(TuneResult)]
         lib.pastila_tune.restype = S
         lib.pastila_tune_clear.argtypes = []
@@ -236,6 +239,20 @@ class Series:
                                        _ptr(labels) if want_labels else None,
                                        _ptr(prof) if want_profiles else None))
         return _recs(out), labels, prof
+
+    def snippets_streamed(self, m: int, K: int, ell: int = 0, k: int = 0, want_labels: bool = False,
+                          want_profiles: bool = False):
+        """``pastila_snippets_streamed``: the same results as ``snippets`` without
+        the S x P profile set; returns (records, labels, profiles, (passes, rows))."""
+        P = self.n - m + 1
+        out = (Snippet * K)()
+        labels = np.empty(P, dtype=np.int32) if want_labels else None
+        prof = np.empty((K, P), dtype=self.dtype) if want_profiles else None
+        work = (ctypes.c_int64 * 2)()
+        _check(load().pastila_snippets_streamed(self._h, m, MParams(ell, k), K, out,
+                                                _ptr(labels) if want_labels else None,
+                                                _ptr(prof) if want_profiles else None, work))
+        return _recs(out), labels, prof, (work[0], work[1])
 
     def tune(self, ms, max_candidates: int = 8, ell: int = 0, k: int = 0):
         """``pastila_tune``: time candidate tile layouts per m and keep the fastest

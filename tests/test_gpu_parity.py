@@ -296,3 +296,44 @@ def test_large_drift_series_full_size_sampled(lib):
         recs, _, _ = h.snippets(m, K)
     assert len({r[0] for r in recs}) == K
     assert sum(r[2] for r in recs) == pytest.approx(1.0)
+
+
+def _purity(s, m, recs, labels):
+    """Share of the positions whose window lies inside one planted regime that
+    are labelled with a snippet from that regime, over the regimes that hold a
+    snippet; a snippet belongs to the regime of its middle point (segments may
+    straddle a regime boundary)."""
+    snip_regime = {r[0]: s.regime_of(r[0] * m + m // 2) for r in recs}
+    P = s.T.shape[0] - m + 1
+    truth = np.array([s.regime_of(p) for p in range(P)])
+    inside = truth == np.array([s.regime_of(p + m - 1) for p in range(P)])
+    covered = np.isin(truth, list(set(snip_regime.values())))
+    got = np.array([snip_regime[int(l)] for l in labels])
+    sel = inside & covered
+    return set(snip_regime.values()), float(np.mean(got[sel] == truth[sel]))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_planted_regimes_recovered_and_labels_pure(lib, prec):
+    """Four planted regimes, K = 4 (m = 128): the greedy snippets fall in the four
+    regimes and the eq. 6 neighbour labels segment the series (label purity)."""
+    s = synth.four_regimes()
+    with _series(s.T, prec) as h:
+        recs, labels, _ = h.snippets(128, 4, want_labels=True)
+    regimes, purity = _purity(s, 128, recs, labels)
+    assert regimes == {0, 1, 2, 3}
+    assert purity >= 0.9, purity
+
+
+def test_six_regime_labels(lib):
+    """The six-regime sweep series, m = 256, K = 6 (FP32): the chirp, whose
+    frequency drifts across its regime, takes two snippets, so five of the six
+    regimes hold one (the AR(1) noise, which repeats no pattern, is labelled by
+    its nearest neighbours); the labels follow the planted regimes."""
+    s = synth.six_regime_sweep()
+    with _series(s.T, 0) as h:
+        recs, labels, _ = h.snippets(256, 6, want_labels=True)
+    regimes, purity = _purity(s, 256, recs, labels)
+    print("six-regime snippets in regimes", sorted(regimes), "label purity", purity)
+    assert len(regimes) >= 5
+    assert purity >= 0.9, purity

@@ -1,0 +1,68 @@
+"""The greedy snippet search without the profile set (pastila_snippets_streamed
+and the automatic switch to it in pastila_snippets): the same records, labels
+and chosen profiles as the search on the materialised D, bit for bit, with
+two full passes over the segments and a few recomputed rows."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _both(pastila, T, m, K, prec, budget=0):
+    with pastila.Series(T, precision=prec) as h:
+        ref = h.snippets(m, K, want_labels=True, want_profiles=True)
+    with pastila.Series(T, precision=prec, mem_budget=budget) as h:
+        got = h.snippets_streamed(m, K, want_labels=True, want_profiles=True)
+    return ref, got
+
+
+def _same(ref, got):
+    assert got[0] == ref[0]                      # records: index, rank, frac, area_after
+    np.testing.assert_array_equal(got[1], ref[1])  # labels
+    np.testing.assert_array_equal(got[2], ref[2])  # chosen profiles, greedy order
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_streamed_equals_materialised(lib, prec):
+    from paper_2401_13680_b300 import pastila
+    cases = [(synth.four_regimes().T, 128, 4), (synth.four_regimes().T, 96, 1),
+             (synth.random_planted(np.random.default_rng(3), 20_000, 5).T, 160, 6)]
+    if prec == 0:
+        cases.append((synth.six_regime_sweep().T, 256, 6))
+    for T, m, K in cases:
+        ref, got = _both(pastila, T, m, K, prec)
+        _same(ref, got)
+        passes, rows = got[3]
+        assert passes == min(K, 2)
+        assert rows >= K
+        S = T.shape[0] // m
+        assert rows <= K * S  # never more than the materialised search's rows
+
+
+def test_streamed_exact_ties(lib):
+    """A periodic series whose period divides m: every segment has the same
+    profile, all areas tie exactly at every step, and the lowest index wins."""
+    from paper_2401_13680_b300 import pastila
+    base = synth.white_noise(7, 64)
+    T = np.tile(base, 60)
+    ref, got = _both(pastila, T, 128, 3, 0)
+    _same(ref, got)
+    assert [r[0] for r in sorted(got[0], key=lambda r: r[1])] == [0, 1, 2]
+
+
+def test_snippets_switches_to_streaming_when_d_does_not_fit(lib):
+    from paper_2401_13680_b300 import pastila
+    s = synth.six_regime_sweep()
+    m, K = 256, 4
+    S, P = s.T.shape[0] // m, s.T.shape[0] - m + 1
+    d_bytes = 4 * S * P
+    with pastila.Series(s.T, precision=pastila.FP32) as h:
+        ref = h.snippets(m, K, want_labels=True, want_profiles=True)
+    budget = d_bytes // 4  # far too small for D, enough for the streamed search
+    with pastila.Series(s.T, precision=pastila.FP32, mem_budget=budget) as h:
+        got = h.snippets(m, K, want_labels=True, want_profiles=True)
+        with pytest.raises(pastila.PastilaError, match="ENOMEM"):
+            h.profiles(m)  # the profile set itself still cannot be produced
+    _same(ref, got)
