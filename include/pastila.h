@@ -294,10 +294,11 @@ void pastila_engine_destroy(pastila_engine* e);
  * (pastila_snippets switches to it by itself when allocating D fails with
  * ENOMEM).  Rows of D are recomputed by the profile kernel: one pass over all
  * segments for each of the first two greedy steps, then only the rows whose
- * area bound can still beat the best (the gain sum_p max(0, M_p - D_s(p)) of a
- * segment never grows as M shrinks, so its last known gain bounds its next
- * area).  Memory: K + 9 rows of P values, the FP64 partial sums of at most
- * 256 MiB, and S doubles.  Results (records, labels, chosen profiles) are
+ * area bound can still beat the best (M only shrinks, so a segment's area over
+ * a block of positions falls by at most the block's drop in M and not below 0:
+ * its last known block areas bound its next area).  Memory: K + 9 rows of P
+ * values, the FP64 partial sums of at most 256 MiB, and 65 doubles per
+ * segment.  Results (records, labels, chosen profiles) are
  * identical to pastila_snippets on the materialised D: every area it compares
  * is computed exactly as there.  work_out (may be NULL) receives two values:
  * full passes over the segments and rows recomputed.  No counterpart in the

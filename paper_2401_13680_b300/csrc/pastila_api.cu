@@ -557,13 +557,15 @@ pastila_status snippets_on_device(pastila_series* h, const MParams& q, const voi
 //
 // Steps 0 and 1 run one streaming pass over all segments, which gives every
 // segment's area sum_p min(M_p, D_s(p)) up to FP64 rounding (relative error far
-// below 1e-9); the segments whose area lies within that margin of the best are
-// recomputed exactly (their rows, then the same per-row sum as the
-// materialized path), and the exact minimum wins (lowest index on ties).  From
-// step 2 the gain of a segment, sum_p M_p - area, can only shrink as M shrinks,
-// so the last gain known for it bounds its area from below; segments are
-// recomputed in order of that bound until the bound passes the best exact area.
-// Every choice and area is therefore the one the materialized search makes.
+// below 1e-9), whole and over 64 blocks of positions; the segments whose area
+// lies within that margin of the best are recomputed exactly (their rows, then
+// the same per-row sum as the materialized path), and the exact minimum wins
+// (lowest index on ties).  From step 2 on, M only shrinks, so the area of a
+// segment over a block can fall by at most that block's drop in M, and not
+// below 0: the block areas last known for a segment bound its area from below;
+// segments are recomputed in order of that bound until the bound passes the
+// best exact area.  Every choice and area is therefore the one the
+// materialized search makes.
 // ---------------------------------------------------------------------------
 template <typename real, int V>
 pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, int32_t* labels_out,
@@ -578,17 +580,22 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     TRY(ensure_stats(h, q.ell, &st));
     const int ntiles = (int)((P + g.W - 1) / g.W);
     const int chunk = std::max(1, std::min(S, (int)((size_t)(32u << 20) / (size_t)ntiles)));  // <= 256 MiB of partials
-    void *part, *apx, *keep, *M, *rows, *segs, *rarea, *dk, *msum;
+    // position blocks for the bounds: NB blocks of TB whole tiles (L positions)
+    const int TB = (ntiles + 63) / 64, NB = (ntiles + TB - 1) / TB;
+    const int64_t L = (int64_t)TB * g.W;
+    void *part, *apx, *blk, *keep, *M, *rows, *segs, *rarea, *rblk, *dk, *mblk;
     void *chosen_d, *aafter_d, *counts, *oi, *orank, *ofrac, *oarea, *lab = nullptr;
     TRY(scratch(h, "st_part", 8 * (size_t)chunk * ntiles, &part));
     TRY(scratch(h, "st_apx", 8 * (size_t)S, &apx));
+    TRY(scratch(h, "st_blk", 8 * (size_t)S * NB, &blk));
     TRY(scratch(h, "st_keep", rs * (size_t)K * P, &keep));
     TRY(scratch(h, "st_M", rs * (size_t)P, &M));
     TRY(scratch(h, "st_rows", rs * (size_t)BATCH * P, &rows));
     TRY(scratch(h, "st_segs", 4 * BATCH, &segs));
     TRY(scratch(h, "st_rarea", 8 * BATCH, &rarea));
+    TRY(scratch(h, "st_rblk", 8 * (size_t)BATCH * NB, &rblk));
     TRY(scratch(h, "dmax", 8, &dk));
-    TRY(scratch(h, "st_msum", 8, &msum));
+    TRY(scratch(h, "st_mblk", 8 * 64, &mblk));
     TRY(scratch(h, "sn_chosen", 4 * 64, &chosen_d));
     TRY(scratch(h, "sn_aafter", 8 * 64, &aafter_d));
     TRY(scratch(h, "sn_counts", 8 * 64, &counts));
@@ -604,10 +611,9 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     init_dmax_kernel<<<1, 1, 0, h->stream>>>((unsigned long long*)dk);
     h->launches += 1;
     ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, nullptr, (unsigned long long*)dk);
-    A.M = nullptr;
-    A.part = nullptr;
     int64_t passes = 0, nrows = 0;
-    std::vector<double> hapx(S), ex(BATCH);
+    std::vector<double> hapx(S), hblk((size_t)S * NB), ex(BATCH), exb((size_t)BATCH * NB);
+    // one streaming pass: approximate areas of every segment, whole and per block
     auto stream_pass = [&](const real* Mc) -> pastila_status {
         ProfileArgs<real> B = A;
         B.M = Mc;
@@ -615,16 +621,18 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
         for (int s0 = 0; s0 < S; s0 += chunk) {
             const int ns = std::min(chunk, S - s0);
             stream_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)ns), g.NT, g.bytes, h->stream>>>(B, g, s0);
-            segment_sum_kernel<<<(ns + 255) / 256, 256, 0, h->stream>>>((const double*)part, ns, ntiles,
-                                                                        (double*)apx + s0);
+            segment_blocks_kernel<<<ns, 64, 0, h->stream>>>((const double*)part, ntiles, TB, NB,
+                                                            (double*)blk + (size_t)s0 * NB, (double*)apx + s0);
             h->launches += 2;
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(hapx.data(), apx, 8 * (size_t)S, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(hblk.data(), blk, 8 * (size_t)S * NB, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         passes++;
         return PASTILA_OK;
     };
+    // exact areas (the materialized path's per-row sums) and block areas of up to BATCH rows
     auto exact = [&](const std::vector<int32_t>& ss, const real* Mc) -> pastila_status {
         const int nb = (int)ss.size();
         CK(cudaMemcpyAsync(segs, ss.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, h->stream));
@@ -633,40 +641,55 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
         rows_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)nb), g.NT, g.bytes, h->stream>>>(
             B, g, (const int32_t*)segs);
         row_area_kernel<real><<<nb, AREA_THREADS, 0, h->stream>>>((const real*)rows, P, Mc, (double*)rarea);
+        row_blocks_kernel<real><<<dim3((unsigned)NB, (unsigned)nb), AREA_THREADS, 0, h->stream>>>(
+            (const real*)rows, P, Mc, L, NB, (double*)rblk);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(ex.data(), rarea, 8 * (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(exb.data(), rblk, 8 * (size_t)nb * NB, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
-        h->launches += 2;
+        h->launches += 3;
         nrows += nb;
         return PASTILA_OK;
     };
-    auto curve_sum = [&](double* out) -> pastila_status {
-        curve_sum_kernel<real><<<1, AREA_THREADS, 0, h->stream>>>((const real*)M, P, (double*)msum);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(out, msum, 8, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        h->launches += 1;
-        return PASTILA_OK;
-    };
-    const double REL = 1e-9;  // far above the FP64 rounding of sums of at most 2^31 terms in these orders
+    const double REL = 1e-9;  // far above the FP64 rounding of these sums
     std::vector<int32_t> chosen;
     std::vector<double> aafter;
     std::vector<char> taken(S, 0);
-    std::vector<double> U(S, 0.0), lb(S);  // gain bounds (from step 1 on), area bounds
+    // per segment: block areas at the step ts[s] they were taken; block sums of M per step
+    std::vector<double> Ab((size_t)S * NB, 0.0), MB((size_t)(K + 1) * NB, 0.0), lb(S);
+    std::vector<int> ts(S, 1);
     std::vector<int32_t> order;
     order.reserve(S);
     for (int t = 0; t < K; ++t) {
         const real* Mc = t ? (const real*)M : nullptr;
-        double msum_t = 0.0;
-        if (t >= 1) TRY(curve_sum(&msum_t));
+        double mtot = 0.0;
+        if (t >= 1) {
+            curve_blocks_kernel<real><<<NB, AREA_THREADS, 0, h->stream>>>((const real*)M, P, L, (double*)mblk);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&MB[(size_t)t * NB], mblk, 8 * (size_t)NB, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            h->launches += 1;
+            for (int b = 0; b < NB; ++b) mtot += MB[(size_t)t * NB + b];
+        }
         if (t <= 1) {
             TRY(stream_pass(Mc));
-            for (int s = 0; s < S; ++s) {
-                lb[s] = hapx[s] - REL * std::fabs(hapx[s]);
-                if (t == 1) U[s] = msum_t - hapx[s] + REL * (msum_t + std::fabs(hapx[s]));
-            }
+            for (int s = 0; s < S; ++s) lb[s] = hapx[s] - REL * (std::fabs(hapx[s]) + mtot);
+            if (t == 1) Ab = hblk;  // ts = 1 for every segment
         } else {
-            for (int s = 0; s < S; ++s) lb[s] = msum_t - U[s] - REL * msum_t;
+            // M only shrinks: a block's area can fall by at most its drop in M, and not below 0
+            for (int s = 0; s < S; ++s) {
+                if (taken[s]) continue;
+                const double* ab = &Ab[(size_t)s * NB];
+                const double* m0 = &MB[(size_t)ts[s] * NB];
+                const double* m1 = &MB[(size_t)t * NB];
+                double v = 0.0, scale = 0.0;
+                for (int b = 0; b < NB; ++b) {
+                    const double x = ab[b] - (m0[b] - m1[b]);
+                    v += x > 0.0 ? x : 0.0;
+                    scale += m0[b];
+                }
+                lb[s] = v - REL * scale;
+            }
         }
         order.clear();
         for (int s = 0; s < S; ++s)
@@ -684,7 +707,10 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
             for (int j = 0; j < (int)batch.size(); ++j) {
                 const int32_t s = batch[j];
                 const double ar = ex[j];
-                if (t >= 1) U[s] = msum_t - ar + REL * msum_t;
+                if (t >= 1) {
+                    std::copy(exb.begin() + (size_t)j * NB, exb.begin() + (size_t)(j + 1) * NB, Ab.begin() + (size_t)s * NB);
+                    ts[s] = t;
+                }
                 if (ar < best || (ar == best && s < bs)) {
                     best = ar;
                     bs = s;

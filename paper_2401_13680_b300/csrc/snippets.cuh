@@ -76,6 +76,59 @@ row_area_kernel(const real* __restrict__ rows, int64_t P, const real* __restrict
     if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
+// Block sums of the tile partials: blocks[s][b] = sum of part[s][tile] over the
+// tiles b*TB .. (b+1)*TB-1, in tile order, and tot[s] = the sum of the blocks in
+// order.  Grid (segments), 64 threads (NB <= 64).
+__global__ void segment_blocks_kernel(const double* __restrict__ part, int ntiles, int TB, int NB,
+                                      double* __restrict__ blocks, double* __restrict__ tot) {
+    __shared__ double bs[64];
+    const int s = blockIdx.x, b = threadIdx.x;
+    double acc = 0.0;
+    if (b < NB) {
+        const int t1 = (b + 1) * TB < ntiles ? (b + 1) * TB : ntiles;
+        for (int t = b * TB; t < t1; ++t) acc += part[(int64_t)s * ntiles + t];
+        blocks[(int64_t)s * NB + b] = acc;
+    }
+    bs[b] = acc;
+    __syncthreads();
+    if (b == 0) {
+        double t = 0.0;
+        for (int i = 0; i < NB; ++i) t += bs[i];
+        tot[s] = t;
+    }
+}
+
+// out[y][b] = sum over positions b*L .. min(P, (b+1)*L) - 1 of min(M_p, rows[y][p])
+// (M = nullptr: of rows[y][p]).  Grid (NB, rows).
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS) row_blocks_kernel(const real* __restrict__ rows, int64_t P,
+                                                                   const real* __restrict__ M, int64_t L, int NB,
+                                                                   double* __restrict__ out) {
+    __shared__ double red[AREA_THREADS / 32];
+    const int b = blockIdx.x, y = blockIdx.y;
+    const real* row = rows + (int64_t)y * P;
+    const int64_t p0 = (int64_t)b * L, p1 = p0 + L < P ? p0 + L : P;
+    double acc = 0.0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += AREA_THREADS) {
+        const real d = row[p];
+        acc += (double)(M && M[p] < d ? M[p] : d);
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) out[(int64_t)y * NB + b] = tot;
+}
+
+// out[b] = sum of M over positions b*L .. min(P, (b+1)*L) - 1.  Grid (NB).
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS) curve_blocks_kernel(const real* __restrict__ M, int64_t P, int64_t L,
+                                                                     double* __restrict__ out) {
+    __shared__ double red[AREA_THREADS / 32];
+    const int64_t p0 = (int64_t)blockIdx.x * L, p1 = p0 + L < P ? p0 + L : P;
+    double acc = 0.0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += AREA_THREADS) acc += (double)M[p];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = tot;
+}
+
 // out[s] = sum over its tiles of part[s][tile], in tile order.  One thread per segment.
 __global__ void segment_sum_kernel(const double* __restrict__ part, int S, int ntiles, double* __restrict__ out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
