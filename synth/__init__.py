@@ -232,3 +232,39 @@ def serving_jobs(n_jobs: int = 1000, rate: float = 20.0, seed: int = 3, n_lo: in
         n_reg = int(rng.integers(3, 9))
         jobs.append(Job(t, n, ms, K, n_reg, int(rng.integers(0, 2**31 - 1))))
     return jobs
+
+
+# ----------------------------------------------------------------------------
+# ECG-like stress series
+# ----------------------------------------------------------------------------
+
+# PQRST beat template: five Gaussian waves (centre offset in samples from the R
+# peak, width in samples, amplitude) at the RR scale of 800 samples
+_PQRST = ((-200.0, 25.0, 0.12), (-45.0, 8.0, -0.10), (0.0, 10.0, 1.00), (40.0, 9.0, -0.25), (260.0, 45.0, 0.30))
+
+
+def ecg_like(n: int = 10_000_000, seed: int = 4, n_regimes: int = 12, noise_sd: float = 0.02) -> Series:
+    """n samples of beats at RR ~ N(800, 40) samples; n_regimes consecutive
+    morphology regimes of equal length, each scaling every wave's amplitude by
+    U[0.6, 1.4] and width by U[0.7, 1.3] (drawn once per regime); plus
+    N(0, 0.02^2) noise."""
+    rng = np.random.default_rng(seed)
+    amp = rng.uniform(0.6, 1.4, size=(n_regimes, len(_PQRST)))
+    wid = rng.uniform(0.7, 1.3, size=(n_regimes, len(_PQRST)))
+    T = np.zeros(n)
+    bounds, per = [], n // n_regimes
+    for q in range(n_regimes):
+        a, b = q * per, (n if q == n_regimes - 1 else (q + 1) * per)
+        bounds.append((a, b, f"morphology{q}"))
+    pos = 300.0
+    while pos < n + 600:
+        q = min(int(pos) // per, n_regimes - 1) if pos < n else n_regimes - 1
+        lo, hi = max(0, int(pos) - 400), min(n, int(pos) + 500)
+        if lo < hi:
+            i = np.arange(lo, hi, dtype=np.float64)
+            for w, (c, sd, A) in enumerate(_PQRST):
+                s = sd * wid[q, w]
+                T[lo:hi] += A * amp[q, w] * np.exp(-0.5 * ((i - pos - c) / s) ** 2)
+        pos += rng.normal(800.0, 40.0)
+    T += rng.normal(0.0, noise_sd, size=n)
+    return Series(np.ascontiguousarray(T), bounds, f"ecg_like_n{n}")

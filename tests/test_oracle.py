@@ -274,3 +274,4 @@ def test_profiles_range_matches_full():
     D = oracle.profiles(T, 32, 16, 4)
     segs = [0, 5, 11]
     np.testing.assert_array_equal(oracle.profiles_range(T, 32, 16, 4, segs, 17, 201), D[segs, 17:201])
+

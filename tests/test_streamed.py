@@ -66,3 +66,12 @@ def test_snippets_switches_to_streaming_when_d_does_not_fit(lib):
         with pytest.raises(pastila.PastilaError, match="ENOMEM"):
             h.profiles(m)  # the profile set itself still cannot be produced
     _same(ref, got)
+
+
+def test_streamed_on_ecg_like_series(lib):
+    """The stress workload's kind of series (ECG-like beats, morphology regimes)
+    at n = 200,000, m = 256, K = 8: streamed equals materialised."""
+    from paper_2401_13680_b300 import pastila
+    s = synth.ecg_like(n=200_000)
+    ref, got = _both(pastila, s.T, 256, 8, 0)
+    _same(ref, got)
