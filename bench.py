@@ -339,7 +339,7 @@ def run_ours(args):
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "batched_tiles_kernel<float,8> (one launch per step: every length of the sweep)",
+                "kernel": "batched_tiles_kernel<float,4> (one launch per step: every length of the sweep)",
                 "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (max SM clock), derived",
                 "launches": tile_launches, "avg_launch_ms": tile_ms / max(tile_launches, 1),
                 "ed_cells_per_s": ed_cells * args.steps / tile_s,

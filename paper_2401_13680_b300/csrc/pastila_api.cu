@@ -51,7 +51,7 @@ pastila_status fail(pastila_status st, const char* fmt, ...) {
         if (st_ != PASTILA_OK) return st_;      \
     } while (0)
 
-constexpr int V_F32 = 8;
+constexpr int V_F32 = 4;
 constexpr int V_F64 = 4;
 constexpr int MAX_NT = 512;
 
