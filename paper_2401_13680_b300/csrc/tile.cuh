@@ -193,9 +193,10 @@ constexpr int SEL_CACHE = 9;  // keys of one position held per lane, per half (r
 // CB[p+gl], CB[p+gl+G], ... in registers.  Every position after the first of
 // a run starts from the previous answer tau (consecutive positions share all
 // but a few of their 2R values, so the rank of tau moves little): a pass counts
-// the keys >= tau and > tau and finds the nearest keys below and above tau,
-// which settles the answer when its rank moved by at most one; otherwise tau
-// steps to that neighbour and the pass repeats.  The first position of a run,
+// the keys >= tau and > tau, which settles most positions; otherwise a second
+// pass finds the nearest key on the side the answer lies, which settles the
+// answer when its rank moved by one, and tau steps to that key and the
+// counting repeats.  The first position of a run,
 // and a position still open after three steps, is searched inside its bracket
 // of keys: the pivot interpolates between the values of two bounds with known
 // counts (#{>= L} >= kk > #{>= H}) at the rank kk, and once a bound's count is
@@ -232,40 +233,45 @@ __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int R
         bool done = false;
         if (it > 0) {
             for (int step = 0; step < 3; ++step) {
+                // counts alone settle most positions (the rank of tau did not move)
                 uint32_t c = 0;
-                key_t xb = KMAX, ya = KMAX;
 #pragma unroll
                 for (int j = 0; j < SEL_CACHE; ++j) {
                     if (j < nr) {
                         const key_t a = va[j], b = vb[j];
                         c += (a >= tau ? 1u : 0u) + (a > tau ? 65536u : 0u);
                         c += (b >= tau ? 1u : 0u) + (b > tau ? 65536u : 0u);
-                        const key_t xa = tau - (key_t)1 - a, xb2 = tau - (key_t)1 - b;
-                        const key_t ya1 = a - tau - (key_t)1, yb = b - tau - (key_t)1;
-                        xb = xa < xb ? xa : xb;
-                        xb = xb2 < xb ? xb2 : xb;
-                        ya = ya1 < ya ? ya1 : ya;
-                        ya = yb < ya ? yb : ya;
                     }
                 }
                 c = grp_sum(c, G);
-                xb = grp_min(xb, G);
-                ya = grp_min(ya, G);
                 const int cge = (int)(c & 0xffffu), cgt = (int)(c >> 16);
-                const bool res = cgt < kk && kk <= cge;
+                if (!done) done = cgt < kk && kk <= cge;
+                if (__all_sync(FULL, done)) break;
+                // otherwise the nearest key on the side the answer lies: below tau when
+                // fewer than kk keys are >= tau, above it when kk or more are > tau;
+                // distance d = tau - 1 - a (below) or a - tau - 1 (above), both as
+                // (a ^ s) + base, and keys on the wrong side wrap to large values
                 const bool down = cge < kk;
-                const key_t below = tau - (key_t)1 - xb, above = tau + (key_t)1 + ya;
+                const key_t s = down ? ~(key_t)0 : (key_t)0, base = down ? tau : ~tau;
+                key_t x = KMAX;
+#pragma unroll
+                for (int j = 0; j < SEL_CACHE; ++j) {
+                    if (j < nr) {
+                        const key_t da = (va[j] ^ s) + base, db = (vb[j] ^ s) + base;
+                        x = da < x ? da : x;
+                        x = db < x ? db : x;
+                    }
+                }
+                x = grp_min(x, G);
                 if (!done) {
-                    if (res) {
-                        done = true;
-                    } else if (down) {
-                        hi = below;
-                        tau = below;
-                        done = cge == kk - 1;
+                    if (down) {
+                        tau = tau - (key_t)1 - x;
+                        hi = tau;
+                        done = cge == kk - 1;  // exactly one key short: the next key down is the answer
                     } else {
-                        lo = above;
-                        tau = above;
-                        done = cgt == kk;
+                        tau = tau + (key_t)1 + x;
+                        lo = tau;
+                        done = cgt == kk;      // exactly kk keys above: the smallest of them
                     }
                 }
                 if (__all_sync(FULL, done)) break;
