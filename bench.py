@@ -276,7 +276,7 @@ def run_ours(args):
     tune = None
     if not args.no_tune:
         res = h.tune(ms, max_candidates=8)
-        tune = {"per_m": [{"m": r["m"], "W": r["W"], "NG": r["NG"], "NT": r["NT"], "GS": r["GS"], "candidates": r["candidates"],
+        tune = {"per_m": [{"m": r["m"], "W": r["W"], "NG": r["NG"], "NT": r["NT"], "GS": r["GS"], "CS": r["CS"], "candidates": r["candidates"],
                            "ms_model": r["ms_model"], "ms_best": r["ms_best"]} for r in res],
                 "sample_speedup_over_model": sum(r["ms_model"] for r in res) / sum(r["ms_best"] for r in res),
                 "sample": "first min(S, 64) segments of each length, all positions; best of 2 timed launches"}

@@ -328,6 +328,7 @@ typedef struct {
     int32_t m;
     int32_t W, NG, NT;     /* the chosen layout */
     int32_t GS;            /* lanes per k-th selection group */
+    int32_t CS;            /* CTAs per tile: 1, or 2 (a thread-block cluster splitting the rows) */
     int32_t candidates;    /* layouts timed */
     double ms_model;       /* device time of the cost model's layout on the sample */
     double ms_best;        /* device time of the chosen layout */
@@ -338,6 +339,23 @@ pastila_status pastila_tune(pastila_series* h, const int32_t* m_list, int32_t n_
 
 /* Forgets every tuned layout (the cost model decides again). */
 void pastila_tune_clear(void);
+
+/* Writes (pastila_tune_set) or reads (pastila_tune_get) one entry of the tuned
+ * table: for (prec, m, ell, k), tile width W (a multiple of 32), NG row groups
+ * asked per CTA, GS lanes per selection group (4, 8, 16 or 32, and at least
+ * R / 9 when R <= 288), CS CTAs per tile (1 or 2).  A table saved with
+ * pastila_tune_get and restored with pastila_tune_set reproduces the tuned
+ * runs' results bit for bit.  A layout that does not fit the device's shared
+ * memory is ignored when it is looked up (the cost model decides instead).
+ * Errors: EINVAL (out of range; get: no entry). */
+pastila_status pastila_tune_set(pastila_precision prec, int32_t m, int32_t ell, int32_t k, int32_t W, int32_t NG,
+                                int32_t GS, int32_t CS);
+pastila_status pastila_tune_get(pastila_precision prec, int32_t m, int32_t ell, int32_t k, int32_t* W, int32_t* NG,
+                                int32_t* GS, int32_t* CS);
+
+/* The tile layout that h's calls use for length m with mp: out5 = {W, NG (row
+ * groups per CTA), NT (threads per CTA), GS, CS}.  Errors: EINVAL. */
+pastila_status pastila_tile_layout(pastila_series* h, int32_t m, pastila_mparams mp, int32_t* out5);
 
 /* ------------------------------------------------------------- tracing ---- */
 

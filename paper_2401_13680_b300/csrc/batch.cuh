@@ -2,7 +2,8 @@
 // a wave) is one item; one launch of each kernel covers all items.
 //
 //   tiles      one flattened grid: CTA b belongs to the item whose CTA range
-//              [cta_begin, cta_begin + S * ntiles) contains b
+//              [cta_begin, cta_begin + S * ntiles * CS) contains b (CS = 2: the
+//              launch has clusters of two CTAs, one per half of a tile's rows)
 //   greedy     per step t, one 2-D grid (segments x items) for the areas, one
 //              CTA per item for the argmin, one 2-D grid for the curve update
 //   criterion  one 2-D grid of partial sums, one thread per item to finish
@@ -22,7 +23,8 @@ template <typename real>
 struct BatchItem {
     ProfileArgs<real> A;   // profile arguments (series, statistics, D, D max key)
     TileGeom G;            // tile layout of this item
-    long long cta_begin;   // first CTA of this item in the flattened tile grid
+    long long cta_begin;   // first CTA of this item in the flattened tile grid (even for cluster tiles)
+    long long ctas;        // its CTA count (CTAs past it, alignment padding, do nothing)
     int s_begin;           // first segment of this launch's share of the item (the
                            // engine splits an item's segments over several waves)
     real* M;               // representativeness curve, P values
@@ -53,7 +55,10 @@ __global__ void __launch_bounds__(512) batched_tiles_kernel(const BatchItem<real
     }
     __syncthreads();
     const long long local = b - items[lo].cta_begin;
-    const int s = items[lo].s_begin + (int)(local / sA.ntiles), tt = (int)(local % sA.ntiles);
+    if (local >= items[lo].ctas) return;  // padding: its cluster partner is a one-CTA tile
+    const int cs = sG.CS;  // an item of cluster tiles starts at an even CTA of a cluster launch
+    const long long per_seg = (long long)sA.ntiles * cs;
+    const int s = items[lo].s_begin + (int)(local / per_seg), tt = (int)((local % per_seg) / cs);
     profile_tile<real, V>(sA, sG, s, tt, smem);
 }
 

@@ -656,6 +656,7 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
     real** h_keep = (real**)(hd + 2 * bi_bytes);
     JobFinal<real>* h_fin = (JobFinal<real>*)(hd + 2 * bi_bytes + kp_bytes);
     long long ctas = 0;
+    int wave_cs = 1;
     int block = 0;
     size_t smem = 0;
     double wave_cells = 0.0;
@@ -663,9 +664,12 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         const Chunk& ch = merged[c];
         const EItem& it = ch.job->items[ch.item];
         h_tiles[c] = item_desc<real>(*ch.job, it);
+        if (it.g.CS > 1 && (ctas & 1)) ++ctas;  // cluster tiles start at an even CTA
         h_tiles[c].cta_begin = ctas;
         h_tiles[c].s_begin = ch.s0;
-        ctas += (long long)ch.segs * it.ntiles;
+        h_tiles[c].ctas = (long long)ch.segs * it.ntiles * it.g.CS;
+        ctas += h_tiles[c].ctas;
+        wave_cs = it.g.CS > wave_cs ? it.g.CS : wave_cs;
         block = std::max(block, it.g.NT);
         smem = std::max(smem, it.g.bytes);
         wave_cells += ch.segs * it.cells_per_seg;
@@ -748,7 +752,8 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         launches += 1;
     }
     if (!merged.empty()) {
-        batched_tiles_kernel<real, V><<<(unsigned)ctas, block, smem, s>>>(d_tiles, (int)merged.size());
+        CK(launch_tiles(batched_tiles_kernel<real, V>, dim3((unsigned)(wave_cs > 1 ? (ctas + 1) & ~1ll : ctas)), block,
+                        smem, s, wave_cs, d_tiles, (int)merged.size()));
         launches += 1;
     }
     if (!greedy.empty()) {

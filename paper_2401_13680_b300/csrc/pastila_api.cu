@@ -55,6 +55,26 @@ constexpr int V_F32 = 4;
 constexpr int V_F64 = 4;
 constexpr int MAX_NT = 512;
 
+// Launch of a tile kernel: plain for one-CTA tiles, with clusters of cs CTAs
+// (along x) otherwise.
+template <typename... P, typename... Q>
+cudaError_t launch_tiles(void (*kernel)(P...), dim3 grid, unsigned block, size_t smem, cudaStream_t st, int cs,
+                         Q&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs > 1 ? cs : 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cs > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Q>(args)...);
+}
+
 struct Stats {
     bool stale = false;
     int64_t C = 0;
@@ -238,23 +258,30 @@ struct TileCand {
     TileGeom g;
 };
 
+constexpr int CLUSTER_MIN_R = 65;  // two-CTA cluster tiles are considered from R = 65 up
+
 template <typename real, int V>
-void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out) {
+void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out, bool clusters = true) {
     out->clear();
     const int64_t Pmax = ((q.P + 31) / 32) * 32;
-    for (int W = 32; W <= MAX_NT * V && W <= Pmax; W += 32) {
-        const int Wb = W + q.R - 1;
-        const int NTc = ((Wb + V - 1) / V + 31) / 32 * 32;
-        if (NTc > MAX_NT) break;
-        const int ng_max = MAX_NT / NTc;
-        for (int ngw = 1; ngw <= ng_max; ++ngw) {
-            TileGeom t = tile_geom<real>(q.m, q.ell, W, V, ngw);
-            if (t.NT > MAX_NT || t.bytes > limit) continue;
-            if (t.NG > 1 && t.Rg < 4) continue;
-            const double rows = 17.0 + 2.0 * t.NG * (double)q.ell / q.R;
-            const double sel = 23.0;
-            const double eff = t.NT >= 384 ? 1.0 : t.NT / 384.0;
-            out->push_back(TileCand{((double)Wb / W * rows + sel) / eff, W, ngw, t});
+    for (int cs = 1; cs <= (clusters && q.R >= CLUSTER_MIN_R ? 2 : 1); ++cs) {
+        for (int W = 32; W <= MAX_NT * V && W <= Pmax; W += 32) {
+            const int Wb = W + q.R - 1;
+            const int NTc = ((Wb + V - 1) / V + 31) / 32 * 32;
+            if (NTc > MAX_NT) break;
+            const int ng_max = MAX_NT / NTc;
+            for (int ngw = 1; ngw <= ng_max; ++ngw) {
+                TileGeom t = tile_geom<real>(q.m, q.ell, W, V, ngw, cs);
+                if (t.NT > MAX_NT || t.bytes > limit) continue;
+                if (t.NG > 1 && t.Rg < 4) continue;
+                // per ED cell: the rows of the Wb columns (plus CS NG seed rows of
+                // ell products) over the W positions, the selection, threads
+                const double rows = 17.0 + 2.0 * cs * t.NG * (double)q.ell / q.R;
+                const double sel = 23.0;
+                const double eff = t.NT >= 384 ? 1.0 : t.NT / 384.0;
+                const double cl = cs > 1 ? 1.1 : 1.0;  // partner writes and cluster barriers
+                out->push_back(TileCand{cl * ((double)Wb / W * rows + sel) / eff, W, ngw, t});
+            }
         }
     }
 }
@@ -262,7 +289,7 @@ void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out)
 // Layouts chosen by the autotuner (pastila_tune), process-wide, keyed by
 // (precision, m, ell, k): tile width and row groups asked.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int>> g_tuned;  // W, row groups asked, GS
+std::map<std::tuple<int, int, int, int>, std::tuple<int, int, int, int>> g_tuned;  // W, row groups asked, GS, CS
 uint64_t g_tune_gen = 0;  // bumped by every change of the table (captured graphs depend on it)
 
 uint64_t tune_generation() {
@@ -276,12 +303,13 @@ std::tuple<int, int, int, int> tune_key(const MParams& q) {
 }
 
 template <typename real, int V>
-pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
+pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g, bool clusters = true) {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key<real>(q));
-        if (it != g_tuned.end()) {
-            TileGeom t = tile_geom<real>(q.m, q.ell, std::get<0>(it->second), V, std::get<1>(it->second));
+        if (it != g_tuned.end() && (clusters || std::get<3>(it->second) == 1)) {
+            TileGeom t = tile_geom<real>(q.m, q.ell, std::get<0>(it->second), V, std::get<1>(it->second),
+                                         std::get<3>(it->second));
             t.GS = std::get<2>(it->second);
             if (t.NT <= MAX_NT && t.bytes <= limit) {
                 *g = t;
@@ -290,7 +318,7 @@ pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
         }
     }
     std::vector<TileCand> c;
-    tile_candidates<real, V>(limit, q, &c);
+    tile_candidates<real, V>(limit, q, &c, clusters);
     if (c.empty()) return fail(PASTILA_EINVAL, "m = %d, ell = %d: the tile does not fit in shared memory", q.m, q.ell);
     size_t b = 0;
     for (size_t i = 1; i < c.size(); ++i)
@@ -300,8 +328,8 @@ pastila_status choose_tile_s(size_t limit, const MParams& q, TileGeom* g) {
 }
 
 template <typename real, int V>
-pastila_status choose_tile(const pastila_series* h, const MParams& q, TileGeom* g) {
-    return choose_tile_s<real, V>((size_t)h->smem_optin, q, g);
+pastila_status choose_tile(const pastila_series* h, const MParams& q, TileGeom* g, bool clusters = true) {
+    return choose_tile_s<real, V>((size_t)h->smem_optin, q, g, clusters);
 }
 
 pastila_status get_event(pastila_series* h, cudaEvent_t* e) {
@@ -386,7 +414,8 @@ pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st,
         TRY(get_event(h, &e1));
         CK(cudaEventRecord(e0, h->stream));
     }
-    profile_tiles_kernel<real, V><<<dim3(A.ntiles, q.S), g.NT, g.bytes, h->stream>>>(A, g);
+    CK(launch_tiles(profile_tiles_kernel<real, V>, dim3((unsigned)(A.ntiles * g.CS), (unsigned)q.S), g.NT, g.bytes,
+                    h->stream, g.CS, A, g));
     CK(cudaGetLastError());
     h->launches += 2;
     if (h->timing) {
@@ -417,17 +446,18 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     std::stable_sort(c.begin(), c.end(), [](const TileCand& x, const TileCand& y) { return x.cost < y.cost; });
     std::vector<TileCand> pick;
     std::vector<int> nts;
-    for (const TileCand& t : c) {  // cheapest layout of every thread count
+    for (const TileCand& t : c) {  // cheapest layout of every thread count and cluster size
         if ((int)pick.size() >= max_cand || t.cost > 1.5 * c[0].cost) break;
-        if (std::find(nts.begin(), nts.end(), t.g.NT) == nts.end()) {
-            nts.push_back(t.g.NT);
+        const int key = t.g.NT * 4 + t.g.CS;
+        if (std::find(nts.begin(), nts.end(), key) == nts.end()) {
+            nts.push_back(key);
             pick.push_back(t);
         }
     }
     for (const TileCand& t : c) {  // then by modelled cost
         if ((int)pick.size() >= max_cand || t.cost > 1.5 * c[0].cost) break;
         bool have = false;
-        for (const TileCand& u : pick) have |= u.W == t.W && u.g.NG == t.g.NG;
+        for (const TileCand& u : pick) have |= u.W == t.W && u.g.NG == t.g.NG && u.g.CS == t.g.CS;
         if (!have) pick.push_back(t);
     }
     Stats* st;
@@ -457,12 +487,12 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     for (size_t i = 0; i < pick.size(); ++i) {
         const TileGeom& g = pick[i].g;
         const ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, (real*)D, (unsigned long long*)dk);
-        const dim3 grid((unsigned)A.ntiles, (unsigned)S_sub);
-        profile_tiles_kernel<real, V><<<grid, g.NT, g.bytes, h->stream>>>(A, g);  // warm-up
+        const dim3 grid((unsigned)(A.ntiles * g.CS), (unsigned)S_sub);
+        CK(launch_tiles(profile_tiles_kernel<real, V>, grid, g.NT, g.bytes, h->stream, g.CS, A, g));  // warm-up
         float best = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaEventRecord(e0, h->stream));
-            profile_tiles_kernel<real, V><<<grid, g.NT, g.bytes, h->stream>>>(A, g);
+            CK(launch_tiles(profile_tiles_kernel<real, V>, grid, g.NT, g.bytes, h->stream, g.CS, A, g));
             CK(cudaEventRecord(e1, h->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -481,7 +511,7 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     h->ev_free.push_back(e1);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key<real>(q)] = std::make_tuple(pick[bi].W, pick[bi].ngw, pick[bi].g.GS);
+        g_tuned[tune_key<real>(q)] = std::make_tuple(pick[bi].W, pick[bi].ngw, pick[bi].g.GS, pick[bi].g.CS);
         g_tune_gen++;
     }
     if (res) {
@@ -490,6 +520,7 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
         res->NG = pick[bi].g.NG;
         res->NT = pick[bi].g.NT;
         res->GS = pick[bi].g.GS;
+        res->CS = pick[bi].g.CS;
         res->candidates = (int32_t)pick.size();
         res->ms_model = model_ms;
         res->ms_best = best_ms;
@@ -575,7 +606,7 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     const size_t rs = sizeof(real);
     constexpr int BATCH = 8;
     TileGeom g;
-    TRY(choose_tile<real, V>(h, q, &g));
+    TRY(choose_tile<real, V>(h, q, &g, false));  // one-CTA tiles: per-tile partial sums
     Stats* st;
     TRY(ensure_stats(h, q.ell, &st));
     const int ntiles = (int)((P + g.W - 1) / g.W);
@@ -778,6 +809,7 @@ pastila_status read_snippets(pastila_series* h, int K, pastila_snippet* out) {
 // graph and replayed).
 // ---------------------------------------------------------------------------
 struct SweepBufs {
+    int cs = 1;  // cluster size of the tile launch (2 when any length uses cluster tiles)
     void* items = nullptr;
     void* best = nullptr;
     void* counts = nullptr;
@@ -801,6 +833,7 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
     for (int i = 0; i < n; ++i) {
         TRY(choose_tile<real, V>(h, qs[i], &geo[i]));
         block = geo[i].NT > block ? geo[i].NT : block;
+        sb->cs = geo[i].CS > sb->cs ? geo[i].CS : sb->cs;
         smem = geo[i].bytes > smem ? geo[i].bytes : smem;
     }
     // one region for every item's D, curve and small arrays
@@ -850,8 +883,10 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
         A.D = (real*)dp;
         dp += up256(sizeof(real) * (size_t)q.S * (size_t)q.P);
         it.G = geo[i];
+        if (geo[i].CS > 1 && (cta & 1)) ++cta;  // cluster tiles start at an even CTA
         it.cta_begin = cta;
-        cta += (long long)q.S * A.ntiles;
+        it.ctas = (long long)q.S * A.ntiles * geo[i].CS;
+        cta += it.ctas;
         it.M = (real*)sp;
         sp += up256(sizeof(real) * (size_t)q.P);
         it.area = (double*)sp;
@@ -887,12 +922,14 @@ pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs
                                int block, size_t smem, long long ctas, int64_t maxS, int64_t maxP, int phase) {
     const int n = (int)qs.size();
     const BatchItem<real>* items = (const BatchItem<real>*)sb.items;
+    const int cs = sb.cs;
     if (phase == 1) {
         // the attribute is process-wide: every caller sets the same device maximum, so
         // concurrent callers (handles, the engine) never lower it under one another
         CK(cudaFuncSetAttribute(batched_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 h->smem_optin));
-        batched_tiles_kernel<real, V><<<(unsigned)ctas, block, smem, h->stream>>>(items, n);
+        CK(launch_tiles(batched_tiles_kernel<real, V>, dim3((unsigned)(cs > 1 ? (ctas + 1) & ~1ll : ctas)), block, smem,
+                        h->stream, cs, items, n));
         CK(cudaGetLastError());
         h->launches += 1;
         return PASTILA_OK;
@@ -1095,6 +1132,55 @@ pastila_status pastila_tune(pastila_series* h, const int32_t* m_list, int32_t n_
         else
             TRY(tune_t<float, V_F32>(h, q, max_candidates, out ? out + i : nullptr));
     }
+    return PASTILA_OK;
+}
+
+pastila_status pastila_tune_set(pastila_precision prec, int32_t m, int32_t ell, int32_t k, int32_t W, int32_t NG,
+                                int32_t GS, int32_t CS) {
+    g_err.clear();
+    if (prec != PASTILA_FP32 && prec != PASTILA_FP64) return fail(PASTILA_EINVAL, "unknown precision %d", (int)prec);
+    if (m < 4 || ell < 2 || ell > m || k < 1) return fail(PASTILA_EINVAL, "m = %d, ell = %d, k = %d out of range", m, ell, k);
+    if (W < 32 || W % 32) return fail(PASTILA_EINVAL, "W = %d: a positive multiple of 32", W);
+    if (NG < 1 || NG > 64) return fail(PASTILA_EINVAL, "NG = %d: 1 .. 64 row groups", NG);
+    if (GS != 4 && GS != 8 && GS != 16 && GS != 32) return fail(PASTILA_EINVAL, "GS = %d: 4, 8, 16 or 32", GS);
+    if (CS != 1 && CS != 2) return fail(PASTILA_EINVAL, "CS = %d: 1 or 2", CS);
+    const int R = m - ell + 1;
+    if (R <= 32 * SEL_CACHE && R > GS * SEL_CACHE)
+        return fail(PASTILA_EINVAL, "GS = %d holds at most %d values per half; R = %d", GS, GS * SEL_CACHE, R);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[std::make_tuple(prec == PASTILA_FP64 ? 8 : 4, m, ell, k)] = std::make_tuple(W, NG, GS, CS);
+    g_tune_gen++;
+    return PASTILA_OK;
+}
+
+pastila_status pastila_tune_get(pastila_precision prec, int32_t m, int32_t ell, int32_t k, int32_t* W, int32_t* NG,
+                                int32_t* GS, int32_t* CS) {
+    g_err.clear();
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(prec == PASTILA_FP64 ? 8 : 4, m, ell, k));
+    if (it == g_tuned.end()) return fail(PASTILA_EINVAL, "no tuned layout for m = %d, ell = %d, k = %d", m, ell, k);
+    if (W) *W = std::get<0>(it->second);
+    if (NG) *NG = std::get<1>(it->second);
+    if (GS) *GS = std::get<2>(it->second);
+    if (CS) *CS = std::get<3>(it->second);
+    return PASTILA_OK;
+}
+
+pastila_status pastila_tile_layout(pastila_series* h, int32_t m, pastila_mparams mp, int32_t* out5) {
+    g_err.clear();
+    if (!h || !out5) return fail(PASTILA_EINVAL, "handle or out is NULL");
+    MParams q;
+    TRY(resolve(h, m, mp, &q));
+    TileGeom g;
+    if (h->prec == PASTILA_FP64)
+        TRY(choose_tile<double, V_F64>(h, q, &g));
+    else
+        TRY(choose_tile<float, V_F32>(h, q, &g));
+    out5[0] = g.W;
+    out5[1] = g.NG;
+    out5[2] = g.NT;
+    out5[3] = g.GS;
+    out5[4] = g.CS;
     return PASTILA_OK;
 }
 

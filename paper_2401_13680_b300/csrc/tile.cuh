@@ -39,6 +39,7 @@
 //      on values with incrementally updated counts beyond that (select_runs);
 //      D = sqrt(2 ell max(0, 1-rho*))
 #pragma once
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cfloat>
 
@@ -79,8 +80,14 @@ struct ProfileArgs {
 struct TileGeom {
     int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, LP, ell, m;
     int GS;  // lanes per selection group (R <= 288: 4, 8, 16 or 32 with R <= 9 GS)
+    // tiles of a thread-block cluster of CS CTAs (1 or 2): CTA c computes rows
+    // c Rh .. c Rh + Rh - 1 over every column of the tile and selects positions
+    // c Wc .. c Wc + Wc - 1; AB holds all R rows of its own Wc positions (the
+    // partner writes the rows it computes into it through distributed shared
+    // memory), CBx/CBy the two CTAs' partial column maxima
+    int CS, Rh, Wc;
     size_t off_AB, off_CB, off_PRE, off_CM, off_PSW, off_SSW, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
-        off_Ts, off_Tsl, off_q, bytes;
+        off_Ts, off_Tsl, off_q, off_CBx, off_CBy, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -88,7 +95,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 // NG_want row groups are asked for; the geometry uses Rg = ceil(R / NG_want)
 // rows per group and as many groups as that needs.
 template <typename real>
-__host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int NG_want) {
+__host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int NG_want, int CS = 1) {
     typedef typename KeyOf<real>::type key_t;
     TileGeom g;
     g.m = m;
@@ -99,13 +106,16 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.V = V;
     g.NTc = ((g.Wb + V - 1) / V + 31) / 32 * 32;
     g.NWc = g.NTc / 32;
-    g.Rg = (g.R + NG_want - 1) / NG_want;
-    g.NG = (g.R + g.Rg - 1) / g.Rg;
+    g.CS = CS;
+    g.Rh = (g.R + CS - 1) / CS;
+    g.Wc = W / CS;
+    g.Rg = (g.Rh + NG_want - 1) / NG_want;
+    g.NG = (g.Rh + g.Rg - 1) / g.Rg;
     g.NT = g.NG * g.NTc;
     // AB row: position p at (p mod V) * LA + p / V, so the V-strided writes of a
     // row (thread t writes tV + i) are consecutive; an odd row stride keeps the
     // column reads of the selection (one position, many rows) in distinct banks
-    g.LA = (W + V - 1) / V;
+    g.LA = (g.Wc + V - 1) / V;
     g.RS = (V * g.LA) | 1;
     g.LP = g.NTc + 1;  // chunk prefix maxima: [V][LP], thread t at t (+ chunk offset)
     g.GS = g.R <= 36 ? 4 : (g.R <= 72 ? 8 : (g.R <= 144 ? 16 : 32));  // the narrowest that fits 9 values per half
@@ -126,6 +136,8 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.off_Ts = o;   o = align16(o + sizeof(real) * (size_t)m);
     g.off_Tsl = o;  o = align16(o + sizeof(real) * (size_t)m);
     g.off_q = o;    o = align16(o + sizeof(real) * NG * (size_t)(ell + 1));
+    g.off_CBx = o;  o = align16(o + (CS > 1 ? sizeof(real) * (size_t)(g.Wb + 32) : 0));
+    g.off_CBy = o;  o = align16(o + (CS > 1 ? sizeof(real) * (size_t)(g.Wb + 32) : 0));
     g.bytes = o;
     return g;
 }
@@ -207,7 +219,8 @@ constexpr int SEL_CACHE = 9;  // keys of one position held per lane, per half (r
 template <typename key_t, typename Out>
 __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int RS, int LA, int V,
                                              const key_t* __restrict__ CB, int R, int kk, int p_begin,
-                                             int npos, int npos_warp, int G, int gl, Out out) {
+                                             int npos, int npos_warp, int G, int gl, int pofs, Out out) {
+    // AB column of tile position p: p - pofs in this CTA's AB
     // requires R <= G * SEL_CACHE: every value of a position sits in the registers of its group
     typedef KeyOf<typename KeyReal<key_t>::type> K;
     typedef typename KeyReal<key_t>::type real;
@@ -220,7 +233,7 @@ __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int R
         const int p = valid ? p_begin + it : 0;  // an idle group reads position 0
         key_t va[SEL_CACHE], vb[SEL_CACHE];
         {
-            const key_t* col = AB + (p % V) * LA + p / V + (size_t)gl * RS;
+            const key_t* col = AB + ((p - pofs) % V) * LA + (p - pofs) / V + (size_t)gl * RS;
             const key_t* win = CB + p + gl;
 #pragma unroll
             for (int j = 0; j < SEL_CACHE; ++j) {
@@ -398,7 +411,7 @@ constexpr int SEL_CAP = 12;  // AB values of a column held per lane in registers
 template <typename real, typename Out>
 __device__ __forceinline__ void select_runs(const real* __restrict__ AB, int RS, int LA, int V,
                                             const real* __restrict__ CB, int R, int kk, int p_begin,
-                                            int npos, Out out) {
+                                            int npos, int pofs, Out out) {
     typedef KeyOf<real> K;
     typedef typename K::type key_t;
     const unsigned FULL = 0xffffffffu;
@@ -500,7 +513,7 @@ __device__ __forceinline__ void select_runs(const real* __restrict__ AB, int RS,
     for (int it = 0; it < npos; ++it) {
         p = p_begin + it;
         cprev = cp;
-        cp = (p % V) * LA + p / V;
+        cp = ((p - pofs) % V) * LA + (p - pofs) / V;
         if (it == 0) {
 #pragma unroll
             for (int j = 0; j < SEL_CAP; ++j) {
@@ -567,7 +580,12 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int RS = G.RS, LA = G.LA, LP = G.LP, NG = G.NG;  // read once: hot loops use registers
     const int g = worker ? tid / NTc : 0, t = tid % NTc, wc = t >> 5;  // row group, column thread, warp in group
     const int R = A.R, ell = A.ell, m = A.m, Rg = G.Rg;
-    const int r0 = g * Rg;
+    // cluster tiles: this CTA's rows and positions (one CTA: all of them)
+    const int CS = G.CS;
+    const int crank = CS > 1 ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+    const int rbase = crank * G.Rh, rend = rbase + G.Rh < R ? rbase + G.Rh : R;
+    const int Wc = G.Wc;
+    const int r0 = rbase + g * Rg;
     const int64_t p0 = (int64_t)tt * A.W;
     const int Wp = (int)((A.P - p0) < (int64_t)A.W ? (A.P - p0) : (int64_t)A.W);
     const int Wb = Wp + R - 1;
@@ -623,7 +641,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     }
     for (int e = tid; e < NG * ell; e += BD) {
         const int gg = e / ell, u = e - gg * ell;
-        const int64_t ig = i0 + (int64_t)gg * Rg;
+        const int64_t ig = i0 + rbase + (int64_t)gg * Rg;
         q[gg * (ell + 1) + u] = (real)(A.T[ig + u] - A.mu[ig]);
     }
     __syncthreads();
@@ -640,7 +658,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0); the row
     // values are centred term by term from their hi + lo parts, and mu of
     // column 0 is the reference of Tc
-    for (int r = 1 + tid; r < R; r += BD) {
+    for (int r = (rbase > 1 ? rbase : 1) + tid; r < rend; r += BD) {
         const real mh = rmu[r], ml = rmul[r];
         real acc = 0;
         for (int u = 0; u < ell; ++u) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
@@ -725,7 +743,19 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int xdiag0 = (int)(i0 - p0) - xb;  // column (relative to xb) where i == j at row 0
     const bool owns_positions = worker && xb < Wp;
     const bool full_positions = xb + V <= Wp;
-    const int nrows = !worker ? 0 : (r0 + Rg <= R ? Rg : R - r0);
+    const int nrows = !worker || r0 >= rend ? 0 : (r0 + Rg <= rend ? Rg : rend - r0);
+    // the AB rows of this thread's V positions: in this CTA or, for the partner's
+    // positions, in the partner's shared memory (all V positions share an owner:
+    // Wc is a multiple of V)
+    key_t* ABo = AB;
+    int tofs = 0;
+    if (CS > 1) {
+        const int owner = owns_positions ? xb / Wc : crank;  // xb < Wp <= CS Wc when it owns positions
+        tofs = owner * (Wc / V);
+        if (owner != crank) ABo = cooperative_groups::this_cluster().map_shared_rank(AB, owner);
+        // the partner must be running before its shared memory is written
+        cooperative_groups::this_cluster().sync();
+    }
 
     for (int c0 = 0; c0 < Rg; c0 += V) {
 #pragma unroll
@@ -846,7 +876,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 suf[V - 1] = rho[V - 1];
 #pragma unroll
                 for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
-                key_t* ABr = AB + (size_t)r * RS + t;
+                key_t* ABr = ABo + (size_t)r * RS + (t - tofs);
                 if (!small_R) {
                     // whole chunks strictly inside the window: t+1 .. t+q0-1 (mid) for small
                     // i, one more (t+q0) once the window end moves into chunk t+q0+1
@@ -893,10 +923,30 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         }
     }
     __syncthreads();
-    for (int x = tid; x < Wb; x += BD) {
-        real mx = top[x];
-        for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
-        CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
+    if (CS == 1) {
+        for (int x = tid; x < Wb; x += BD) {
+            real mx = top[x];
+            for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
+            CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
+        }
+    } else {
+        // this CTA's column maxima into its CBx and the partner's CBy; after the
+        // cluster barrier (which also completes every AB write into this CTA),
+        // the maximum of both
+        real* CBx = (real*)(sm + G.off_CBx);
+        real* CBy_peer = cooperative_groups::this_cluster().map_shared_rank((real*)(sm + G.off_CBy), crank ^ 1);
+        for (int x = tid; x < Wb; x += BD) {
+            real mx = top[x];
+            for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
+            CBx[x] = mx;
+            CBy_peer[x] = mx;
+        }
+        cooperative_groups::this_cluster().sync();
+        const real* CBy = (const real*)(sm + G.off_CBy);
+        for (int x = tid; x < Wb; x += BD) {
+            const real mx = rmax(CBx[x], CBy[x]);
+            CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
+        }
     }
     __syncthreads();
 
@@ -919,24 +969,27 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         }
         tmax = d > tmax ? d : tmax;
     };
+    // this CTA's positions: pofs .. pofs + Wn - 1 of the tile
+    const int pofs = crank * Wc;
+    const int Wn = Wp - pofs < 0 ? 0 : (Wp - pofs < Wc ? Wp - pofs : Wc);
     if (keyed) {
         // groups of GS lanes, each with a run of positions; a lane caches at most
         // SEL_CACHE values of each half
         const int GS = G.GS;
         const int ngroups = BD / GS;
         const int grp = tid / GS, gl = tid % GS;
-        const int PW = (Wp + ngroups - 1) / ngroups;
+        const int PW = (Wn + ngroups - 1) / ngroups;
         const int pb = grp * PW;
-        const int npos = pb >= Wp ? 0 : (pb + PW <= Wp ? PW : Wp - pb);
-        select_track<key_t>(AB, RS, LA, V, CB, R, kk, pb, npos, PW, GS, gl,
+        const int npos = pb >= Wn ? 0 : (pb + PW <= Wn ? PW : Wn - pb);
+        select_track<key_t>(AB, RS, LA, V, CB, R, kk, pofs + pb, npos, PW, GS, gl, pofs,
                             [&](int p, key_t kb) { emit(p, K::dec(kb)); });
     } else {
         // one run per warp; values beyond the register cache are read from shared memory
         const int nwarps = BD >> 5;
-        const int PW = (Wp + nwarps - 1) / nwarps;
+        const int PW = (Wn + nwarps - 1) / nwarps;
         const int pb = (tid >> 5) * PW;
-        const int npos = pb >= Wp ? 0 : (pb + PW <= Wp ? PW : Wp - pb);
-        select_runs<real>((const real*)AB, RS, LA, V, (const real*)CB, R, kk, pb, npos, emit);
+        const int npos = pb >= Wn ? 0 : (pb + PW <= Wn ? PW : Wn - pb);
+        select_runs<real>((const real*)AB, RS, LA, V, (const real*)CB, R, kk, pofs + pb, npos, pofs, emit);
     }
     const double wmax = warp_max(tmax);
     if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(wmax));
@@ -949,33 +1002,33 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         if (tid == 0) {
             double tot = 0.0;
             for (int w = 0; w < (BD >> 5); ++w) tot += red[w];
-            A.part[(int64_t)(s - row_base) * A.ntiles + tt] = tot;
+            A.part[((int64_t)(s - row_base) * A.ntiles + tt) * CS + crank] = tot;
         }
     }
 }
 
-// Streaming form over segments s_begin .. s_begin + gridDim.y - 1: grid (ntiles, segments).
+// Streaming form over segments s_begin .. s_begin + gridDim.y - 1: grid (ntiles CS, segments).
 template <typename real, int V>
 __global__ void __launch_bounds__(512) stream_tiles_kernel(ProfileArgs<real> A, TileGeom G, int s_begin) {
     extern __shared__ __align__(16) unsigned char smem[];
-    profile_tile<real, V>(A, G, s_begin + (int)blockIdx.y, blockIdx.x, smem, s_begin);
+    profile_tile<real, V>(A, G, s_begin + (int)blockIdx.y, (int)blockIdx.x / G.CS, smem, s_begin);
 }
 
 // The profile rows of a list of segments: CTA (tile, y) computes segment
-// segs[y] into row y of A.D.  Grid: (ntiles, number of segments).
+// segs[y] into row y of A.D.  Grid: (ntiles CS, number of segments).
 template <typename real, int V>
 __global__ void __launch_bounds__(512) rows_tiles_kernel(ProfileArgs<real> A, TileGeom G,
                                                          const int32_t* __restrict__ segs) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int s = segs[blockIdx.y];
-    profile_tile<real, V>(A, G, s, blockIdx.x, smem, s - (int)blockIdx.y);
+    profile_tile<real, V>(A, G, s, (int)blockIdx.x / G.CS, smem, s - (int)blockIdx.y);
 }
 
-// One CTA per (tile, segment): grid (ntiles, S).
+// One CTA (CS CTAs, a cluster) per (tile, segment): grid (ntiles CS, S).
 template <typename real, int V>
 __global__ void __launch_bounds__(512) profile_tiles_kernel(ProfileArgs<real> A, TileGeom G) {
     extern __shared__ __align__(16) unsigned char smem[];
-    profile_tile<real, V>(A, G, blockIdx.y, blockIdx.x, smem);
+    profile_tile<real, V>(A, G, blockIdx.y, (int)blockIdx.x / G.CS, smem);
 }
 
 }  // namespace pastila

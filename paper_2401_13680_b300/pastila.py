@@ -52,7 +52,7 @@ class EngineCounters(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("W", ctypes.c_int32), ("NG", ctypes.c_int32), ("NT", ctypes.c_int32),
-                ("GS", ctypes.c_int32), ("candidates", ctypes.c_int32), ("ms_model", ctypes.c_double), ("ms_best", ctypes.c_double)]
+                ("GS", ctypes.c_int32), ("CS", ctypes.c_int32), ("candidates", ctypes.c_int32), ("ms_model", ctypes.c_double), ("ms_best", ctypes.c_double)]
 
 
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE, JOB_FAILED, JOB_CANCELLED = range(5)
@@ -111,6 +111,15 @@ def load(path: str | None = None):
         lib.pastila_snippets_streamed.restype = S
         lib.pastila_tune.argtypes = [_vp, _vp, ctypes.c_int32, MParams, ctypes.c_int32, ctypes.POINTER(TuneResult)]
         lib.pastila_tune.restype = S
+        lib.pastila_tune_set.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        lib.pastila_tune_set.restype = S
+        _i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.pastila_tune_get.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                                         _i32p, _i32p]
+        lib.pastila_tune_get.restype = S
+        lib.pastila_tile_layout.argtypes = [_vp, ctypes.c_int32, MParams, _vp]
+        lib.pastila_tile_layout.restype = S
         lib.pastila_tune_clear.argtypes = []
         lib.pastila_tune_clear.restype = None
         lib.pastila_engine_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(EngineConfig)]
@@ -262,6 +271,12 @@ class Series:
         _check(load().pastila_tune(self._h, _ptr(ms), ms.shape[0], MParams(ell, k), max_candidates, out))
         return [{f: getattr(r, f) for f, _ in TuneResult._fields_} for r in out]
 
+    def tile_layout(self, m: int, ell: int = 0, k: int = 0) -> dict:
+        """``pastila_tile_layout``: the layout the calls use for length m."""
+        out = np.zeros(5, dtype=np.int32)
+        _check(load().pastila_tile_layout(self._h, m, MParams(ell, k), _ptr(out)))
+        return dict(zip(("W", "NG", "NT", "GS", "CS"), (int(x) for x in out)))
+
     def select_length(self, ms, K: int, ell: int = 0, k: int = 0):
         """(m_best, crit per m, K records of m_best) -- ``pastila_select_length``."""
         ms = np.ascontiguousarray(ms, dtype=np.int32)
@@ -345,6 +360,18 @@ class Engine:
         c = EngineCounters()
         _check(load().pastila_engine_stats(self._h, ctypes.byref(c)))
         return {f: getattr(c, f) for f, _ in EngineCounters._fields_}
+
+
+def tune_set(precision: int, m: int, ell: int, k: int, W: int, NG: int, GS: int, CS: int = 1):
+    """``pastila_tune_set``: one entry of the tuned layout table."""
+    _check(load().pastila_tune_set(precision, m, ell, k, W, NG, GS, CS))
+
+
+def tune_get(precision: int, m: int, ell: int, k: int):
+    """``pastila_tune_get``: (W, NG, GS, CS) of an entry of the tuned layout table."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(load().pastila_tune_get(precision, m, ell, k, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def tune_clear():

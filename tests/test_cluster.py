@@ -1,0 +1,109 @@
+"""Tiles computed by a thread-block cluster of two CTAs (each computes half the
+rows of a tile twice as wide and writes its row-window maxima for the
+partner's positions into the partner's shared memory): parity with the oracle
+in both precisions, a sweep mixing one- and two-CTA tiles in one launch, the
+engine, and the tuned-table entry points that force and report the layout."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tolerance import assert_profiles_close
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 1: 1e-9}
+
+
+@pytest.fixture
+def table(lib):
+    from paper_2401_13680_b300 import pastila
+    pastila.tune_clear()
+    yield pastila
+    pastila.tune_clear()
+
+
+def _force(pastila, prec, m, ell, k, W, NG, GS, CS=2):
+    pastila.tune_set(prec, m, ell, k, W, NG, GS, CS)
+    assert pastila.tune_get(prec, m, ell, k) == (W, NG, GS, CS)
+
+
+# (n, m, ell, k, W, NG, GS): R = 65, 101, 129 (grouped selector), 321 (warp
+# selector) with a ragged last tile and a tail segment
+CLUSTER_CASES = [
+    (4096, 128, 64, 13, 256, 2, 8),
+    (3001, 200, 100, 20, 192, 2, 16),
+    (5003, 256, 128, 26, 192, 3, 16),
+    (4000, 640, 320, 64, 64, 2, 32),
+]
+
+
+@pytest.mark.parametrize("n,m,ell,k,W,NG,GS", CLUSTER_CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cluster_tiles_match_the_oracle(table, prec, n, m, ell, k, W, NG, GS):
+    pastila = table
+    rng = np.random.default_rng(n + m)
+    T = synth.random_planted(rng, n, 3).T if prec == 1 else np.cumsum(rng.normal(0, 0.2, n)) + rng.normal(0, 1.0, n)
+    _force(pastila, prec, m, ell, k, W, NG, GS)
+    with pastila.Series(T, precision=prec) as h:
+        lay = h.tile_layout(m, ell=ell, k=k)
+        assert lay["CS"] == 2 and lay["W"] == W, lay
+        D, dmax = h.profiles(m, ell=ell, k=k)
+    ref = oracle.profiles(T, m, ell, k)
+    assert_profiles_close(D, ref, ell, TOL[prec])
+    assert dmax == pytest.approx(float(D.max()), rel=1e-7)
+
+
+def test_sweep_mixing_one_and_two_cta_tiles(table):
+    """One batched launch holds lengths with one-CTA tiles (odd CTA counts, so
+    the two-CTA items need alignment padding) and lengths with cluster tiles;
+    each criterion equals eq. 18 on the GPU's own profiles."""
+    pastila = table
+    s = synth.four_regimes(per_regime=750)  # n = 3000
+    ms, K = [96, 128, 160, 192], 3
+    # m = 96: 31 segments x 5 tiles = 155 CTAs, so the next (cluster) item is padded
+    _force(pastila, 0, 96, 48, 10, 608, 1, 8, CS=1)
+    _force(pastila, 0, 128, 64, 13, 192, 2, 8)
+    _force(pastila, 0, 192, 96, 20, 160, 2, 16)
+    with pastila.Series(s.T, precision=pastila.FP32) as h:
+        assert [h.tile_layout(m)["CS"] for m in ms] == [1, 2, 1, 2]
+        runs = [h.select_length(ms, K) for _ in range(3)]  # direct, captured, replayed
+        for r in runs[1:]:
+            assert r[0] == runs[0][0] and np.array_equal(r[1], runs[0][1]) and r[2] == runs[0][2]
+        for i, m in enumerate(ms):
+            D, _ = h.profiles(m)
+            Dd = D.astype(np.float64)
+            c, _ = oracle.greedy(Dd, K)
+            assert runs[0][1][i] == pytest.approx(oracle.criterion(Dd, c), rel=1e-12)
+            ref = oracle.profiles(s.T, m, m // 2, (m + 9) // 10)
+            assert_profiles_close(D, ref, m // 2, 1e-4)
+
+
+def test_engine_with_cluster_tiles(table):
+    pastila = table
+    rng = np.random.default_rng(77)
+    T = synth.random_planted(rng, 30_000, 4).T
+    ms, K = [128, 160, 256], 4
+    _force(pastila, 0, 128, 64, 13, 256, 2, 8)
+    _force(pastila, 0, 256, 128, 26, 192, 3, 16)
+    with pastila.Series(T, precision=pastila.FP32) as h:
+        ref = h.select_length(ms, K)
+    with pastila.Engine(wave_ed_cells=5e7) as e:
+        j = e.submit(T, ms, K)
+        assert e.wait(j)["state"] == pastila.JOB_DONE
+        got = e.result(j)
+    assert got[0] == ref[0]
+    np.testing.assert_array_equal(got[1], ref[1])
+    assert got[2] == ref[2]
+
+
+def test_tune_set_argument_errors(lib):
+    from paper_2401_13680_b300 import pastila
+    with pytest.raises(pastila.PastilaError, match="CS = 3"):
+        pastila.tune_set(0, 128, 64, 13, 256, 2, 8, 3)
+    with pytest.raises(pastila.PastilaError, match="multiple of 32"):
+        pastila.tune_set(0, 128, 64, 13, 250, 2, 8, 1)
+    with pytest.raises(pastila.PastilaError, match="GS = 4 holds"):
+        pastila.tune_set(0, 128, 64, 13, 256, 2, 4, 1)
+    with pytest.raises(pastila.PastilaError, match="no tuned layout"):
+        pastila.tune_get(0, 123, 61, 13)
