@@ -86,7 +86,7 @@ struct TileGeom {
     // partner writes the rows it computes into it through distributed shared
     // memory), CBx/CBy the two CTAs' partial column maxima
     int CS, Rh, Wc;
-    size_t off_AB, off_CB, off_PRE, off_CM, off_PSW, off_SSW, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
+    size_t off_AB, off_CB, off_PRE, off_CM, off_LV, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
         off_Ts, off_Tsl, off_q, off_CBx, off_CBy, bytes;
 };
 
@@ -125,8 +125,7 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.off_CB = o;   o = align16(o + sizeof(key_t) * (size_t)(g.Wb + 32));
     g.off_PRE = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)V * g.LP);
     g.off_CM = o;   o = align16(o + sizeof(real) * NG * 2 * (size_t)(g.NTc + 1));
-    g.off_PSW = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)g.NTc);
-    g.off_SSW = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)g.NTc);
+    g.off_LV = o;   o = align16(o + sizeof(real) * NG * 2 * 4 * (size_t)g.NTc);
     g.off_XCH = o;  o = align16(o + sizeof(real) * NG * 4 * (size_t)g.NWc);
     g.off_row = o;  o = align16(o + sizeof(real) * 5 * (size_t)g.R);
     g.off_left = o; o = align16(o + sizeof(real) * (size_t)g.R);
@@ -599,8 +598,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     key_t* CB = (key_t*)(sm + G.off_CB);
     real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * LP;  // this group's [parity][V][LP]
     real* CM = (real*)(sm + G.off_CM) + (size_t)g * 2 * (NTc + 1);   // [parity][NTc + 1]
-    real* PSW = (real*)(sm + G.off_PSW) + (size_t)g * 2 * NTc;       // [parity][NTc]: CM prefix maxima
-    real* SSW = (real*)(sm + G.off_SSW) + (size_t)g * 2 * NTc;       // and suffix maxima within each warp
+    real* LV = (real*)(sm + G.off_LV) + (size_t)g * 2 * 4 * NTc;     // [parity][k-1][NTc]: max of the 2^k chunk
+                                                                      // maxima from a chunk on, within its warp
     real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][hi/lo][warp]
     real* rdf = (real*)(sm + G.off_row);
     real* rdg = rdf + R;
@@ -766,8 +765,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             const int par = sidx & 1;
             real* PREp = PRE + par * V * LP;
             real* CMp = CM + par * (NTc + 1);
-            real* PSWp = PSW + par * NTc;
-            real* SSWp = SSW + par * NTc;
+            real* LVp = LV + par * 4 * NTc;
             // logical column v of this thread lives in register (v - jj) mod V
             real rho[V];
             real pre = NEG;  // this thread's chunk maximum
@@ -832,43 +830,35 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 }
                 CMp[t] = pre;
                 if (t == 0) CMp[NTc] = NEG;
-                if (!small_R && q0 >= 2) {  // prefix and suffix maxima of the chunk maxima within each warp
-                    real ps = pre, ss = pre;
+                if (!small_R && q0 >= 2) {  // sparse table of the chunk maxima within each warp
+                    real d = pre;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const real u = __shfl_up_sync(FULL, ps, o);
-                        const real d = __shfl_down_sync(FULL, ss, o);
-                        if (lane >= o) ps = rmax(ps, u);
-                        if (lane + o < 32) ss = rmax(ss, d);
+                    for (int k = 0; k < 4; ++k) {  // entries reaching past the warp's end are never read
+                        d = rmax(d, __shfl_down_sync(FULL, d, 1 << k));
+                        LVp[k * NTc + t] = d;
                     }
-                    PSWp[t] = ps;
-                    SSWp[t] = ss;
                 }
             }
             __syncthreads();
             // maximum of the whole chunks t+1 .. t+q0-1 strictly inside the windows of
-            // this thread's positions: a window inside this warp from a sparse table
-            // of shuffles (max over 2^k chunks from a lane, twice); a window reaching
-            // into later warps from the suffix maximum of its first warp, the warp
-            // maxima in between and the prefix maximum of its last warp
+            // this thread's positions, from the sparse tables: two overlapping spans of
+            // 2^k chunks for the part in each warp the range touches, two spans of 16
+            // for every whole warp in between
             real mid = NEG;
-            if (active && !small_R && q0 >= 2) {
-                const int L = q0 - 1, z = t + L;
-                const bool inwarp = (z >> 5) == (t >> 5);
-                if (L <= 31) {  // uniform: some windows of the warp stay inside it (two spans of 2^k <= 16)
-                    const int k = 31 - __clz(L);
-                    real lv = pre;
-                    for (int s2 = 0; s2 < k; ++s2) lv = rmax(lv, __shfl_down_sync(FULL, lv, 1 << s2));
-                    const real m1 = __shfl_sync(FULL, lv, (lane + 1) & 31);
-                    const real m2 = __shfl_sync(FULL, lv, (lane + L - (1 << k) + 1) & 31);
-                    if (inwarp) mid = rmax(m1, m2);
-                }
-                if (!inwarp && owns_positions) {
-                    const int wa = (t + 1) >> 5, wz = z >> 5;
-                    // t + 1 opens the next warp (lane 31) and the window ends in it: a prefix
-                    real x = wa == wz ? PSWp[z] : rmax(SSWp[t + 1], PSWp[z]);
-                    for (int w = wa + 1; w < wz; ++w) x = rmax(x, PSWp[w * 32 + 31]);
-                    mid = x;
+            if (active && owns_positions && !small_R && q0 >= 2) {
+                auto span = [&](int x, int y) {  // x <= y in one warp
+                    const int k = 31 - __clz(y - x + 1);
+                    const real* Lk = k == 0 ? CMp : LVp + (k > 4 ? 3 : k - 1) * NTc;
+                    const int w = k > 4 ? 16 : 1 << k;
+                    return rmax(Lk[x], Lk[y - w + 1]);
+                };
+                const int a = t + 1, z = t + q0 - 1;
+                const int wa = a >> 5, wz = z >> 5;
+                if (wa == wz) {
+                    mid = span(a, z);
+                } else {
+                    mid = rmax(span(a, wa * 32 + 31), span(wz * 32, z));
+                    for (int w = wa + 1; w < wz; ++w) mid = rmax(mid, rmax(LVp[3 * NTc + w * 32], LVp[3 * NTc + w * 32 + 16]));
                 }
             }
             if (active && owns_positions) {
