@@ -657,11 +657,26 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0); the row
     // values are centred term by term from their hi + lo parts, and mu of
     // column 0 is the reference of Tc
-    for (int r = (rbase > 1 ? rbase : 1) + tid; r < rend; r += BD) {
-        const real mh = rmu[r], ml = rmul[r];
-        real acc = 0;
-        for (int u = 0; u < ell; ++u) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
-        lseed[r] = acc;
+    {
+        // SPLIT consecutive lanes per row, each a contiguous part of the ell terms,
+        // then a fixed-order shuffle sum: short dependent chains, every thread busy
+        const int rfirst = rbase > 1 ? rbase : 1;
+        const int nrow = rend - rfirst;
+        int SPLIT = 1;  // from the tile's own thread count: the same sums in every launch
+        while (SPLIT < 32 && nrow > 0 && nrow * SPLIT * 2 <= G.NT) SPLIT *= 2;
+        const int part = (ell + SPLIT - 1) / SPLIT;
+        for (int base = 0; base < nrow * SPLIT; base += BD) {
+            const int idx = base + tid;
+            const int r = rfirst + idx / SPLIT, sp = idx % SPLIT;
+            real acc = 0;
+            if (r < rend) {
+                const real mh = rmu[r], ml = rmul[r];
+                const int u1 = (sp + 1) * part < ell ? (sp + 1) * part : ell;
+                for (int u = sp * part; u < u1; ++u) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
+            }
+            for (int o = SPLIT >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SPLIT);
+            if (r < rend && sp == 0) lseed[r] = acc;
+        }
     }
     __syncthreads();
     // first row of every group: cov(r0, x) = sum_t q[t] * (T[x+t] - c) - (mu_x - c) * sum_t q[t]
