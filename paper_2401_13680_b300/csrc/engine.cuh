@@ -655,23 +655,31 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
     BatchItem<real>* h_greedy = (BatchItem<real>*)(hd + bi_bytes);
     real** h_keep = (real**)(hd + 2 * bi_bytes);
     JobFinal<real>* h_fin = (JobFinal<real>*)(hd + 2 * bi_bytes + kp_bytes);
-    long long ctas = 0;
-    int wave_cs = 1;
-    int block = 0;
-    size_t smem = 0;
     double wave_cells = 0.0;
+    // one tile launch per cluster size (a launch has a single cluster shape), each
+    // numbering its own CTAs; chunks ordered by cluster size
+    std::stable_sort(merged.begin(), merged.end(), [](const Chunk& x, const Chunk& y) {
+        return x.job->items[x.item].g.CS < y.job->items[y.item].g.CS;
+    });
+    std::vector<TileGroup> groups;
     for (size_t c = 0; c < merged.size(); ++c) {
         const Chunk& ch = merged[c];
         const EItem& it = ch.job->items[ch.item];
+        if (groups.empty() || groups.back().cs != it.g.CS) {
+            TileGroup tg;
+            tg.cs = it.g.CS;
+            tg.first = (int)c;
+            groups.push_back(tg);
+        }
+        TileGroup& tg = groups.back();
         h_tiles[c] = item_desc<real>(*ch.job, it);
-        if (it.g.CS > 1 && (ctas & 1)) ++ctas;  // cluster tiles start at an even CTA
-        h_tiles[c].cta_begin = ctas;
+        h_tiles[c].cta_begin = tg.ctas;
         h_tiles[c].s_begin = ch.s0;
         h_tiles[c].ctas = (long long)ch.segs * it.ntiles * it.g.CS;
-        ctas += h_tiles[c].ctas;
-        wave_cs = it.g.CS > wave_cs ? it.g.CS : wave_cs;
-        block = std::max(block, it.g.NT);
-        smem = std::max(smem, it.g.bytes);
+        tg.ctas += h_tiles[c].ctas;
+        tg.n++;
+        tg.block = std::max(tg.block, it.g.NT);
+        tg.smem = std::max(tg.smem, it.g.bytes);
         wave_cells += ch.segs * it.cells_per_seg;
         if (ch.job->first_wave < 0) ch.job->first_wave = wave_id;
         ch.job->last_wave = wave_id;
@@ -751,9 +759,9 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         engine_init_keys_kernel<<<1, 64, 0, s>>>(j.items[0].dmax, (int)j.items.size());
         launches += 1;
     }
-    if (!merged.empty()) {
-        CK(launch_tiles(batched_tiles_kernel<real, V>, dim3((unsigned)(wave_cs > 1 ? (ctas + 1) & ~1ll : ctas)), block,
-                        smem, s, wave_cs, d_tiles, (int)merged.size()));
+    for (const TileGroup& tg : groups) {
+        CK(launch_tiles(batched_tiles_kernel<real, V>, dim3((unsigned)tg.ctas), tg.block, tg.smem, s, tg.cs,
+                        d_tiles + tg.first, tg.n));
         launches += 1;
     }
     if (!greedy.empty()) {

@@ -258,13 +258,14 @@ struct TileCand {
     TileGeom g;
 };
 
-constexpr int CLUSTER_MIN_R = 65;  // two-CTA cluster tiles are considered from R = 65 up
+constexpr int CLUSTER_MIN_R = 65;    // two-CTA cluster tiles are considered from R = 65 up
+constexpr int CLUSTER4_MIN_R = 129;  // four-CTA cluster tiles from R = 129 up
 
 template <typename real, int V>
 void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out, bool clusters = true) {
     out->clear();
     const int64_t Pmax = ((q.P + 31) / 32) * 32;
-    for (int cs = 1; cs <= (clusters && q.R >= CLUSTER_MIN_R ? 2 : 1); ++cs) {
+    for (int cs = 1; cs <= (clusters ? (q.R >= CLUSTER4_MIN_R ? 4 : (q.R >= CLUSTER_MIN_R ? 2 : 1)) : 1); cs *= 2) {
         for (int W = 32; W <= MAX_NT * V && W <= Pmax; W += 32) {
             const int Wb = W + q.R - 1;
             const int NTc = ((Wb + V - 1) / V + 31) / 32 * 32;
@@ -452,6 +453,15 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
         if (std::find(nts.begin(), nts.end(), key) == nts.end()) {
             nts.push_back(key);
             pick.push_back(t);
+        }
+    }
+    for (int cs : {2, 4}) {  // the model's best of every cluster size is always timed
+        for (const TileCand& t : c) {
+            if (t.g.CS != cs) continue;
+            bool have = false;
+            for (const TileCand& u : pick) have |= u.g.CS == cs;
+            if (!have && (int)pick.size() < max_cand) pick.push_back(t);
+            break;
         }
     }
     for (const TileCand& t : c) {  // then by modelled cost
@@ -808,8 +818,18 @@ pastila_status read_snippets(pastila_series* h, int K, pastila_snippet* out) {
 // no host synchronisation in between (so the sequence can be captured in a CUDA
 // graph and replayed).
 // ---------------------------------------------------------------------------
+// One tile launch of a sweep: the lengths whose tiles use clusters of cs CTAs
+// (a launch has a single cluster shape), as items [first, first + n) of the
+// tile-item array, with their own CTA numbering.
+struct TileGroup {
+    int cs = 1, first = 0, n = 0, block = 0;
+    size_t smem = 0;
+    long long ctas = 0;
+};
+
 struct SweepBufs {
-    int cs = 1;  // cluster size of the tile launch (2 when any length uses cluster tiles)
+    std::vector<TileGroup> groups;
+    void* tiles = nullptr;  // tile items, grouped by cluster size
     void* items = nullptr;
     void* best = nullptr;
     void* counts = nullptr;
@@ -824,18 +844,11 @@ inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 template <typename real, int V>
 pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs, int K, SweepBufs* sb,
-                               std::vector<BatchItem<real>>* items_out, int* block_out, size_t* smem_out,
-                               long long* ctas_out, int64_t* maxS_out, int64_t* maxP_out) {
+                               std::vector<BatchItem<real>>* items_out, std::vector<BatchItem<real>>* tiles_out,
+                               int64_t* maxS_out, int64_t* maxP_out) {
     const int n = (int)qs.size();
     std::vector<TileGeom> geo(n);
-    int block = 0;
-    size_t smem = 0;
-    for (int i = 0; i < n; ++i) {
-        TRY(choose_tile<real, V>(h, qs[i], &geo[i]));
-        block = geo[i].NT > block ? geo[i].NT : block;
-        sb->cs = geo[i].CS > sb->cs ? geo[i].CS : sb->cs;
-        smem = geo[i].bytes > smem ? geo[i].bytes : smem;
-    }
+    for (int i = 0; i < n; ++i) TRY(choose_tile<real, V>(h, qs[i], &geo[i]));
     // one region for every item's D, curve and small arrays
     size_t dbytes = 0, sbytes = 0;
     for (int i = 0; i < n; ++i) {
@@ -847,6 +860,7 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
     TRY(scratch(h, "sweep_D", dbytes, &dreg));
     TRY(scratch(h, "sweep_small", sbytes, &sreg));
     TRY(scratch(h, "sweep_items", sizeof(BatchItem<real>) * (size_t)n, &sb->items));
+    TRY(scratch(h, "sweep_tiles", sizeof(BatchItem<real>) * (size_t)n, &sb->tiles));
     TRY(scratch(h, "sweep_best", 16, &sb->best));
     TRY(scratch(h, "sweep_counts", 8 * 64, &sb->counts));
     TRY(scratch(h, "sweep_rec_index", 4 * 64, &sb->rec_index));
@@ -859,7 +873,6 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
     items.assign(n, BatchItem<real>{});
     char* dp = (char*)dreg;
     char* sp = (char*)sreg;
-    long long cta = 0;
     int64_t maxS = 0, maxP = 0;
     for (int i = 0; i < n; ++i) {
         const MParams& q = qs[i];
@@ -883,10 +896,7 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
         A.D = (real*)dp;
         dp += up256(sizeof(real) * (size_t)q.S * (size_t)q.P);
         it.G = geo[i];
-        if (geo[i].CS > 1 && (cta & 1)) ++cta;  // cluster tiles start at an even CTA
-        it.cta_begin = cta;
         it.ctas = (long long)q.S * A.ntiles * geo[i].CS;
-        cta += it.ctas;
         it.M = (real*)sp;
         sp += up256(sizeof(real) * (size_t)q.P);
         it.area = (double*)sp;
@@ -905,9 +915,27 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
         maxS = q.S > maxS ? q.S : maxS;
         maxP = q.P > maxP ? q.P : maxP;
     }
-    *block_out = block;
-    *smem_out = smem;
-    *ctas_out = cta;
+    // tile launches: one per cluster size, each numbering its own CTAs (counts are
+    // multiples of the cluster size, so every item starts a cluster)
+    std::vector<BatchItem<real>>& tiles = *tiles_out;
+    tiles.clear();
+    sb->groups.clear();
+    for (int cs : {1, 2, 4}) {
+        TileGroup tg;
+        tg.cs = cs;
+        tg.first = (int)tiles.size();
+        for (int i = 0; i < n; ++i) {
+            if (geo[i].CS != cs) continue;
+            BatchItem<real> t = items[i];
+            t.cta_begin = tg.ctas;
+            tg.ctas += t.ctas;
+            tg.block = geo[i].NT > tg.block ? geo[i].NT : tg.block;
+            tg.smem = geo[i].bytes > tg.smem ? geo[i].bytes : tg.smem;
+            tiles.push_back(t);
+        }
+        tg.n = (int)tiles.size() - tg.first;
+        if (tg.n) sb->groups.push_back(tg);
+    }
     *maxS_out = maxS;
     *maxP_out = maxP;
     return PASTILA_OK;
@@ -919,19 +947,20 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
 // greedy steps, the criterion, m_best and its eq. 8 records
 template <typename real, int V>
 pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs, int K, const SweepBufs& sb,
-                               int block, size_t smem, long long ctas, int64_t maxS, int64_t maxP, int phase) {
+                               int64_t maxS, int64_t maxP, int phase) {
     const int n = (int)qs.size();
     const BatchItem<real>* items = (const BatchItem<real>*)sb.items;
-    const int cs = sb.cs;
     if (phase == 1) {
         // the attribute is process-wide: every caller sets the same device maximum, so
         // concurrent callers (handles, the engine) never lower it under one another
         CK(cudaFuncSetAttribute(batched_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 h->smem_optin));
-        CK(launch_tiles(batched_tiles_kernel<real, V>, dim3((unsigned)(cs > 1 ? (ctas + 1) & ~1ll : ctas)), block, smem,
-                        h->stream, cs, items, n));
+        for (const TileGroup& tg : sb.groups) {
+            CK(launch_tiles(batched_tiles_kernel<real, V>, dim3((unsigned)tg.ctas), tg.block, tg.smem, h->stream,
+                            tg.cs, (const BatchItem<real>*)sb.tiles + tg.first, tg.n));
+            h->launches += 1;
+        }
         CK(cudaGetLastError());
-        h->launches += 1;
         return PASTILA_OK;
     }
     if (phase == 2) {
@@ -977,13 +1006,12 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
                                        const std::vector<MParams>& qs, int K, int32_t* m_best, double* crit_out,
                                        pastila_snippet* best_out) {
     SweepBufs sb;
-    std::vector<BatchItem<real>> items;
-    int block;
-    size_t smem;
-    long long ctas;
+    std::vector<BatchItem<real>> items, tiles;
     int64_t maxS, maxP;
-    TRY(sweep_prepare_t<real, V>(h, qs, K, &sb, &items, &block, &smem, &ctas, &maxS, &maxP));
+    TRY(sweep_prepare_t<real, V>(h, qs, K, &sb, &items, &tiles, &maxS, &maxP));
     CK(cudaMemcpyAsync(sb.items, items.data(), sizeof(BatchItem<real>) * items.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(sb.tiles, tiles.data(), sizeof(BatchItem<real>) * tiles.size(), cudaMemcpyHostToDevice,
                        h->stream));
     auto& gr = h->graph;
     double cells = 0.0;  // ED cells of the tile launch, halo columns included
@@ -1015,7 +1043,7 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
         for (int ph = 0; ph < 3; ++ph) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            pastila_status st = sweep_enqueue_t<real, V>(h, qs, K, sb, block, smem, ctas, maxS, maxP, ph);
+            pastila_status st = sweep_enqueue_t<real, V>(h, qs, K, sb, maxS, maxP, ph);
             cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
             if (st != PASTILA_OK) return st;
             if (ec != cudaSuccess) return fail(PASTILA_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
@@ -1032,11 +1060,11 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
         if (gr.exec[ph]) {
             CK(cudaGraphLaunch(gr.exec[ph], h->stream));
         } else {
-            TRY(sweep_enqueue_t<real, V>(h, qs, K, sb, block, smem, ctas, maxS, maxP, ph));
+            TRY(sweep_enqueue_t<real, V>(h, qs, K, sb, maxS, maxP, ph));
         }
         if (ph == 1 && h->timing) CK(cudaEventRecord(gr.ev1, h->stream));
     }
-    if (gr.exec[0]) h->launches = l_before + 2 * (uint64_t)n_m + 1 + 1 + 3 * K - 1 + 4;
+    if (gr.exec[0]) h->launches = l_before + 2 * (uint64_t)n_m + 1 + sb.groups.size() + 3 * K - 1 + 4;
     gr.gen = h->alloc_gen;
     int32_t b = 0;
     std::vector<double> cv(n_m);
@@ -1143,7 +1171,7 @@ pastila_status pastila_tune_set(pastila_precision prec, int32_t m, int32_t ell, 
     if (W < 32 || W % 32) return fail(PASTILA_EINVAL, "W = %d: a positive multiple of 32", W);
     if (NG < 1 || NG > 64) return fail(PASTILA_EINVAL, "NG = %d: 1 .. 64 row groups", NG);
     if (GS != 4 && GS != 8 && GS != 16 && GS != 32) return fail(PASTILA_EINVAL, "GS = %d: 4, 8, 16 or 32", GS);
-    if (CS != 1 && CS != 2) return fail(PASTILA_EINVAL, "CS = %d: 1 or 2", CS);
+    if (CS != 1 && CS != 2 && CS != 4) return fail(PASTILA_EINVAL, "CS = %d: 1, 2 or 4", CS);
     const int R = m - ell + 1;
     if (R <= 32 * SEL_CACHE && R > GS * SEL_CACHE)
         return fail(PASTILA_EINVAL, "GS = %d holds at most %d values per half; R = %d", GS, GS * SEL_CACHE, R);

@@ -80,14 +80,14 @@ struct ProfileArgs {
 struct TileGeom {
     int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, LP, ell, m;
     int GS;  // lanes per selection group (R <= 288: 4, 8, 16 or 32 with R <= 9 GS)
-    // tiles of a thread-block cluster of CS CTAs (1 or 2): CTA c computes rows
+    // tiles of a thread-block cluster of CS CTAs (1, 2 or 4): CTA c computes rows
     // c Rh .. c Rh + Rh - 1 over every column of the tile and selects positions
     // c Wc .. c Wc + Wc - 1; AB holds all R rows of its own Wc positions (the
-    // partner writes the rows it computes into it through distributed shared
-    // memory), CBx/CBy the two CTAs' partial column maxima
+    // other CTAs write the rows they compute into it through distributed shared
+    // memory), CBp[c'] the partial column maxima of CTA c'
     int CS, Rh, Wc;
     size_t off_AB, off_CB, off_PRE, off_CM, off_LV, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
-        off_Ts, off_Tsl, off_q, off_CBx, off_CBy, bytes;
+        off_Ts, off_Tsl, off_q, off_CBp, bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -135,8 +135,7 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.off_Ts = o;   o = align16(o + sizeof(real) * (size_t)m);
     g.off_Tsl = o;  o = align16(o + sizeof(real) * (size_t)m);
     g.off_q = o;    o = align16(o + sizeof(real) * NG * (size_t)(ell + 1));
-    g.off_CBx = o;  o = align16(o + (CS > 1 ? sizeof(real) * (size_t)(g.Wb + 32) : 0));
-    g.off_CBy = o;  o = align16(o + (CS > 1 ? sizeof(real) * (size_t)(g.Wb + 32) : 0));
+    g.off_CBp = o;  o = align16(o + (CS > 1 ? sizeof(real) * (size_t)CS * (g.Wb + 32) : 0));
     g.bytes = o;
     return g;
 }
@@ -658,21 +657,20 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // values are centred term by term from their hi + lo parts, and mu of
     // column 0 is the reference of Tc
     {
-        // SPLIT consecutive lanes per row, each a contiguous part of the ell terms,
-        // then a fixed-order shuffle sum: short dependent chains, every thread busy
+        // SPLIT consecutive lanes per row, lane sp summing the terms sp, sp + SPLIT,
+        // ... (consecutive lanes, consecutive words), then a fixed-order shuffle sum:
+        // short dependent chains, every thread busy
         const int rfirst = rbase > 1 ? rbase : 1;
         const int nrow = rend - rfirst;
         int SPLIT = 1;  // from the tile's own thread count: the same sums in every launch
         while (SPLIT < 32 && nrow > 0 && nrow * SPLIT * 2 <= G.NT) SPLIT *= 2;
-        const int part = (ell + SPLIT - 1) / SPLIT;
         for (int base = 0; base < nrow * SPLIT; base += BD) {
             const int idx = base + tid;
             const int r = rfirst + idx / SPLIT, sp = idx % SPLIT;
             real acc = 0;
             if (r < rend) {
                 const real mh = rmu[r], ml = rmul[r];
-                const int u1 = (sp + 1) * part < ell ? (sp + 1) * part : ell;
-                for (int u = sp * part; u < u1; ++u) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
+                for (int u = sp; u < ell; u += SPLIT) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
             }
             for (int o = SPLIT >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SPLIT);
             if (r < rend && sp == 0) lseed[r] = acc;
@@ -935,21 +933,25 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
         }
     } else {
-        // this CTA's column maxima into its CBx and the partner's CBy; after the
+        // this CTA's column maxima into slot crank of every CTA's CBp; after the
         // cluster barrier (which also completes every AB write into this CTA),
-        // the maximum of both
-        real* CBx = (real*)(sm + G.off_CBx);
-        real* CBy_peer = cooperative_groups::this_cluster().map_shared_rank((real*)(sm + G.off_CBy), crank ^ 1);
+        // the maximum over the slots, in slot order
+        real* CBp = (real*)(sm + G.off_CBp);
+        const int slot = Wb + 32;
         for (int x = tid; x < Wb; x += BD) {
             real mx = top[x];
             for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
-            CBx[x] = mx;
-            CBy_peer[x] = mx;
+            CBp[crank * slot + x] = mx;
+        }
+        for (int c = 0; c < CS; ++c) {
+            if (c == crank) continue;
+            real* CBq = cooperative_groups::this_cluster().map_shared_rank(CBp, c) + crank * slot;
+            for (int x = tid; x < Wb; x += BD) CBq[x] = CBp[crank * slot + x];
         }
         cooperative_groups::this_cluster().sync();
-        const real* CBy = (const real*)(sm + G.off_CBy);
         for (int x = tid; x < Wb; x += BD) {
-            const real mx = rmax(CBx[x], CBy[x]);
+            real mx = CBp[x];
+            for (int c = 1; c < CS; ++c) mx = rmax(mx, CBp[c * slot + x]);
             CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
         }
     }

@@ -1,8 +1,8 @@
-"""Tiles computed by a thread-block cluster of two CTAs (each computes half the
-rows of a tile twice as wide and writes its row-window maxima for the
-partner's positions into the partner's shared memory): parity with the oracle
-in both precisions, a sweep mixing one- and two-CTA tiles in one launch, the
-engine, and the tuned-table entry points that force and report the layout."""
+"""Tiles computed by a thread-block cluster of two or four CTAs (each computes
+its share of the rows of a wider tile and writes its row-window maxima for the
+other CTAs' positions into their shared memory): parity with the oracle in
+both precisions, a sweep mixing one-, two- and four-CTA tiles, the engine, and
+the tuned-table entry points that force and report the layout."""
 import numpy as np
 import pytest
 
@@ -28,26 +28,28 @@ def _force(pastila, prec, m, ell, k, W, NG, GS, CS=2):
     assert pastila.tune_get(prec, m, ell, k) == (W, NG, GS, CS)
 
 
-# (n, m, ell, k, W, NG, GS): R = 65, 101, 129 (grouped selector), 321 (warp
+# (n, m, ell, k, W, NG, GS, CS): R = 65, 101, 129 (grouped selector), 321 (warp
 # selector) with a ragged last tile and a tail segment
 CLUSTER_CASES = [
-    (4096, 128, 64, 13, 256, 2, 8),
-    (3001, 200, 100, 20, 192, 2, 16),
-    (5003, 256, 128, 26, 192, 3, 16),
-    (4000, 640, 320, 64, 64, 2, 32),
+    (4096, 128, 64, 13, 256, 2, 8, 2),
+    (3001, 200, 100, 20, 192, 2, 16, 2),
+    (5003, 256, 128, 26, 192, 3, 16, 2),
+    (4000, 640, 320, 64, 64, 2, 32, 2),
+    (5003, 256, 128, 26, 256, 2, 16, 4),
+    (4000, 640, 320, 64, 128, 2, 32, 4),
 ]
 
 
-@pytest.mark.parametrize("n,m,ell,k,W,NG,GS", CLUSTER_CASES)
+@pytest.mark.parametrize("n,m,ell,k,W,NG,GS,CS", CLUSTER_CASES)
 @pytest.mark.parametrize("prec", [0, 1])
-def test_cluster_tiles_match_the_oracle(table, prec, n, m, ell, k, W, NG, GS):
+def test_cluster_tiles_match_the_oracle(table, prec, n, m, ell, k, W, NG, GS, CS):
     pastila = table
     rng = np.random.default_rng(n + m)
     T = synth.random_planted(rng, n, 3).T if prec == 1 else np.cumsum(rng.normal(0, 0.2, n)) + rng.normal(0, 1.0, n)
-    _force(pastila, prec, m, ell, k, W, NG, GS)
+    _force(pastila, prec, m, ell, k, W, NG, GS, CS)
     with pastila.Series(T, precision=prec) as h:
         lay = h.tile_layout(m, ell=ell, k=k)
-        assert lay["CS"] == 2 and lay["W"] == W, lay
+        assert lay["CS"] == CS and lay["W"] == W, lay
         D, dmax = h.profiles(m, ell=ell, k=k)
     ref = oracle.profiles(T, m, ell, k)
     assert_profiles_close(D, ref, ell, TOL[prec])
@@ -55,18 +57,17 @@ def test_cluster_tiles_match_the_oracle(table, prec, n, m, ell, k, W, NG, GS):
 
 
 def test_sweep_mixing_one_and_two_cta_tiles(table):
-    """One batched launch holds lengths with one-CTA tiles (odd CTA counts, so
-    the two-CTA items need alignment padding) and lengths with cluster tiles;
-    each criterion equals eq. 18 on the GPU's own profiles."""
+    """One sweep holds lengths with one-, two- and four-CTA tiles (one tile launch
+    per cluster size); each criterion equals eq. 18 on the GPU's own profiles."""
     pastila = table
     s = synth.four_regimes(per_regime=750)  # n = 3000
-    ms, K = [96, 128, 160, 192], 3
-    # m = 96: 31 segments x 5 tiles = 155 CTAs, so the next (cluster) item is padded
+    ms, K = [96, 128, 160, 192, 256], 3
     _force(pastila, 0, 96, 48, 10, 608, 1, 8, CS=1)
     _force(pastila, 0, 128, 64, 13, 192, 2, 8)
     _force(pastila, 0, 192, 96, 20, 160, 2, 16)
+    _force(pastila, 0, 256, 128, 26, 256, 2, 16, CS=4)
     with pastila.Series(s.T, precision=pastila.FP32) as h:
-        assert [h.tile_layout(m)["CS"] for m in ms] == [1, 2, 1, 2]
+        assert [h.tile_layout(m)["CS"] for m in ms] == [1, 2, 1, 2, 4]
         runs = [h.select_length(ms, K) for _ in range(3)]  # direct, captured, replayed
         for r in runs[1:]:
             assert r[0] == runs[0][0] and np.array_equal(r[1], runs[0][1]) and r[2] == runs[0][2]
@@ -83,9 +84,10 @@ def test_engine_with_cluster_tiles(table):
     pastila = table
     rng = np.random.default_rng(77)
     T = synth.random_planted(rng, 30_000, 4).T
-    ms, K = [128, 160, 256], 4
+    ms, K = [128, 160, 256, 384], 4
     _force(pastila, 0, 128, 64, 13, 256, 2, 8)
     _force(pastila, 0, 256, 128, 26, 192, 3, 16)
+    _force(pastila, 0, 384, 192, 39, 384, 2, 32, CS=4)
     with pastila.Series(T, precision=pastila.FP32) as h:
         ref = h.select_length(ms, K)
     with pastila.Engine(wave_ed_cells=5e7) as e:
