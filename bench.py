@@ -51,9 +51,10 @@ SM_MAX_MHZ = 2032.0
 # recurrence (4 FLOP), 2 multiplications by the inverse norms (2 FLOP), and the
 # exact seed of every diagonal (ell FMA per R cells, about 2 FLOP at ell = m/2)
 FLOP_PER_ED_CELL = 8.0
-# dram__bytes_read.sum + dram__bytes_write.sum of the whole-sweep tile launch
-# (91.5 MB + 2.94 GB), measured with ncu on this kernel version
-SWEEP_TILE_DRAM_BYTES = 3.03e9
+# dram__bytes_read.sum + dram__bytes_write.sum of the tile launches of one sweep
+# step (one-CTA tiles: 59 MB + 2.10 GB; two-CTA tiles: 46 MB + 0.78 GB), measured
+# with ncu on this kernel version
+SWEEP_TILE_DRAM_BYTES = 2.99e9
 
 
 def workload(m_list=None):
@@ -340,12 +341,13 @@ def run_ours(args):
     tile_s = tile_ms / 1e3
     achieved = FLOP_PER_ED_CELL * ed_cells * args.steps / tile_s / 1e12
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    # DRAM bytes of one whole-sweep tile launch, from an ncu capture of the current
+    # DRAM bytes of one sweep's tile launches, from an ncu capture of the current
     # kernel (read + write; the algorithmic bytes are the profile set D, 2.97 GB)
     traffic = SWEEP_TILE_DRAM_BYTES if ms == synth.sweep_lengths() else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "kernel": "batched_tiles_kernel<float,4> (one launch per step: every length of the sweep)",
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per sweep step's tile launches",
+                "kernel": "batched_tiles_kernel<float,4> (every length of the sweep; one launch per cluster size, "
+                          "timed together)",
                 "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (max SM clock), derived",
                 "launches": tile_launches, "avg_launch_ms": tile_ms / max(tile_launches, 1),
                 "ed_cells_per_s": ed_cells * args.steps / tile_s,
