@@ -239,6 +239,29 @@ def run_serving(args, pastila, device, ed_rate, fp64_ed_rate):
     return out
 
 
+def run_serving_plain(args, pastila, device, rate, precision):
+    """The serving stream run one job at a time, in arrival order, on handles of
+    the given precision (select_length per job, no engine): arrival -> results
+    latency measured against the same arrival clock as the engine's run."""
+    jobs = synth.serving_jobs(n_jobs=args.serve_jobs, rate=20.0, seed=3)
+    series = [j.series() for j in jobs]
+    arrivals = [j.arrival * 20.0 / rate for j in jobs]
+    lat = []
+    t0 = time.perf_counter()
+    for T, j, at in zip(series, jobs, arrivals):
+        wait = t0 + at - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        with pastila.Series(T, device=device, precision=precision) as h:
+            h.select_length(j.ms, j.K)
+        lat.append(time.perf_counter() - t0 - at)
+    lat = np.array(lat)
+    return {"precision": "f64" if precision == pastila.FP64 else "f32", "jobs": len(jobs),
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "latency_mean_s": float(lat.mean()), "makespan_s": float(time.perf_counter() - t0),
+            "basis": "measured: one job at a time in arrival order, select_length on a handle per job"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args):
@@ -379,6 +402,10 @@ def run_ours(args):
     if args.serve_jobs > 0 and world == 1:
         serving = run_serving(args, pastila, local, ed_cells * args.steps / tot_s,
                               fp64["ed_cells_per_s"] if fp64 else None)
+        if args.serve_plain:
+            serving["plain_fifo_measured"] = [
+                run_serving_plain(args, pastila, local, serving["arrival_rate_jobs_per_s"], prec)
+                for prec in (pastila.FP32, pastila.FP64)]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
@@ -410,6 +437,8 @@ def main():
     ap.add_argument("--m-list", type=lambda x: [int(v) for v in x.split(",")], default=None,
                     help="comma-separated lengths replacing the sweep (profiling runs on a small case)")
     ap.add_argument("--serve-jobs", type=int, default=32, help="serving-leg jobs (0: no serving leg)")
+    ap.add_argument("--serve-plain", action="store_true",
+                    help="also run the serving stream one job at a time on FP32 and FP64 handles (slow)")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="offered load of the serving leg, as a fraction of the measured ED-cell rate")
     args = ap.parse_args()
