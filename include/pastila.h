@@ -214,6 +214,9 @@ typedef struct {
     int32_t max_waves_in_flight; /* 1..8; 0: 2 */
     int32_t fail_alloc_at;       /* fault injection for tests: the n-th device allocation (1-based) of the
                                     engine reports ENOMEM and fails the job it was for; 0: off */
+    double age_weight_s;         /* share of a wave per active job: 0 (default) equal shares; > 0 shares in
+                                    proportion to 1 + (time since submission) / age_weight_s, which moves
+                                    the engine from processor sharing toward arrival order */
 } pastila_engine_config;
 
 typedef enum {

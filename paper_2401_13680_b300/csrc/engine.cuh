@@ -249,6 +249,7 @@ struct pastila_engine {
     size_t budget = 0, held = 0, peak = 0, reserve = 0;
     int max_active = 0, max_inflight = 0;
     double wave_cells = 0.0;
+    double age_weight = 0.0;
     int fail_at = 0;
     int64_t alloc_count = 0;
     int smem_optin = 0;
@@ -598,8 +599,15 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         return PASTILA_OK;
     };
     if (!with_work.empty()) {
-        const double share = e->wave_cells / (double)with_work.size();
-        for (EJob* j : with_work) TRY(take(*j, share));
+        // equal shares, or shares growing with the time since submission
+        const double now = eng_now(e);
+        std::vector<double> wt(with_work.size(), 1.0);
+        double wsum = 0.0;
+        for (size_t i = 0; i < with_work.size(); ++i) {
+            if (e->age_weight > 0.0) wt[i] = 1.0 + (now - with_work[i]->t_submit) / e->age_weight;
+            wsum += wt[i];
+        }
+        for (size_t i = 0; i < with_work.size(); ++i) TRY(take(*with_work[i], e->wave_cells * wt[i] / wsum));
         for (EJob* j : with_work)
             if (used < e->wave_cells) TRY(take(*j, e->wave_cells - used));
     }
@@ -951,6 +959,7 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
         return fail(PASTILA_EINVAL, "max_waves_in_flight = %d: must be in [0, 8]", c.max_waves_in_flight);
     if (!(c.wave_ed_cells >= 0.0)) return fail(PASTILA_EINVAL, "wave_ed_cells must be >= 0");
     if (c.fail_alloc_at < 0) return fail(PASTILA_EINVAL, "fail_alloc_at must be >= 0");
+    if (!(c.age_weight_s >= 0.0)) return fail(PASTILA_EINVAL, "age_weight_s must be >= 0");
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
     if (c.device < 0 || c.device >= ndev) return fail(PASTILA_EINVAL, "device %d: %d device(s) visible", c.device, ndev);
@@ -962,6 +971,7 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
     e->max_inflight = c.max_waves_in_flight ? c.max_waves_in_flight : 2;
     e->wave_cells = c.wave_ed_cells > 0.0 ? c.wave_ed_cells : 4e9;
     e->fail_at = c.fail_alloc_at;
+    e->age_weight = c.age_weight_s;
     int smem = 0;
     CK(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
     e->smem_optin = smem - 1024;

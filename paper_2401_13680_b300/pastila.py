@@ -32,7 +32,8 @@ class MParams(ctypes.Structure):
 class EngineConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("prec", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
                 ("max_active_jobs", ctypes.c_int32), ("wave_ed_cells", ctypes.c_double),
-                ("max_waves_in_flight", ctypes.c_int32), ("fail_alloc_at", ctypes.c_int32)]
+                ("max_waves_in_flight", ctypes.c_int32), ("fail_alloc_at", ctypes.c_int32),
+                ("age_weight_s", ctypes.c_double)]
 
 
 class JobInfo(ctypes.Structure):
@@ -293,10 +294,11 @@ class Engine:
     select_length jobs on one GPU."""
 
     def __init__(self, device: int = 0, precision: int = FP32, mem_budget: int = 0, max_active: int = 0,
-                 wave_ed_cells: float = 0.0, max_waves_in_flight: int = 0, fail_alloc_at: int = 0):
+                 wave_ed_cells: float = 0.0, max_waves_in_flight: int = 0, fail_alloc_at: int = 0,
+                 age_weight_s: float = 0.0):
         lib = load()
         cfg = EngineConfig(device, precision, mem_budget, max_active, wave_ed_cells, max_waves_in_flight,
-                           fail_alloc_at)
+                           fail_alloc_at, age_weight_s)
         h = _vp()
         _check(lib.pastila_engine_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h

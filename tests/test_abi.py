@@ -49,10 +49,10 @@ def test_engine_host_side_validation():
     lib = pastila.load()
     e = ctypes.c_void_p()
     assert lib.pastila_engine_create(None, None) == pastila.EINVAL
-    bad = pastila.EngineConfig(0, 7, 0, 0, 0.0, 0, 0)
+    bad = pastila.EngineConfig(0, 7, 0, 0, 0.0, 0, 0, 0.0)
     assert lib.pastila_engine_create(ctypes.byref(e), ctypes.byref(bad)) == pastila.EINVAL
     assert "precision" in pastila.last_error()
-    bad = pastila.EngineConfig(0, pastila.FP32, 0, 1000, 0.0, 0, 0)
+    bad = pastila.EngineConfig(0, pastila.FP32, 0, 1000, 0.0, 0, 0, 0.0)
     assert lib.pastila_engine_create(ctypes.byref(e), ctypes.byref(bad)) == pastila.EINVAL
     job = ctypes.c_int64()
     T = np.zeros(100)
