@@ -358,6 +358,14 @@ pastila_status pastila_tune_get(pastila_precision prec, int32_t m, int32_t ell, 
 
 /* The tile layout that h's calls use for length m with mp: out5 = {W, NG (row
  * groups per CTA), NT (threads per CTA), GS, CS}.  Errors: EINVAL. */
+
+/* The same choice without a device (host code only): the tuned table's entry
+ * if it fits smem_limit bytes of dynamic shared memory per CTA, else the cost
+ * model's layout for a series of n values.  out8 = {W, NG, NT, GS, CS, Rg (rows
+ * per group), Rh (rows per CTA), shared-memory bytes}.  Errors: EINVAL (no
+ * layout fits). */
+pastila_status pastila_plan_layout(pastila_precision prec, int64_t n, int32_t m, pastila_mparams mp,
+                                   size_t smem_limit, int32_t* out8);
 pastila_status pastila_tile_layout(pastila_series* h, int32_t m, pastila_mparams mp, int32_t* out5);
 
 /* ------------------------------------------------------------- tracing ---- */

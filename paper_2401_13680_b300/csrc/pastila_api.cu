@@ -1194,6 +1194,23 @@ pastila_status pastila_tune_get(pastila_precision prec, int32_t m, int32_t ell, 
     return PASTILA_OK;
 }
 
+pastila_status pastila_plan_layout(pastila_precision prec, int64_t n, int32_t m, pastila_mparams mp,
+                                   size_t smem_limit, int32_t* out8) {
+    g_err.clear();
+    if (!out8) return fail(PASTILA_EINVAL, "out is NULL");
+    if (prec != PASTILA_FP32 && prec != PASTILA_FP64) return fail(PASTILA_EINVAL, "unknown precision %d", (int)prec);
+    MParams q;
+    TRY(resolve_n(n, m, mp, &q));
+    TileGeom g;
+    if (prec == PASTILA_FP64)
+        TRY(choose_tile_s<double, V_F64>(smem_limit, q, &g));
+    else
+        TRY(choose_tile_s<float, V_F32>(smem_limit, q, &g));
+    const int32_t v[8] = {g.W, g.NG, g.NT, g.GS, g.CS, g.Rg, g.Rh, (int32_t)g.bytes};
+    memcpy(out8, v, sizeof v);
+    return PASTILA_OK;
+}
+
 pastila_status pastila_tile_layout(pastila_series* h, int32_t m, pastila_mparams mp, int32_t* out5) {
     g_err.clear();
     if (!h || !out5) return fail(PASTILA_EINVAL, "handle or out is NULL");

@@ -119,6 +119,9 @@ def load(path: str | None = None):
         lib.pastila_tune_get.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                          _i32p, _i32p]
         lib.pastila_tune_get.restype = S
+        lib.pastila_plan_layout.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, MParams, ctypes.c_size_t,
+                                            _vp]
+        lib.pastila_plan_layout.restype = S
         lib.pastila_tile_layout.argtypes = [_vp, ctypes.c_int32, MParams, _vp]
         lib.pastila_tile_layout.restype = S
         lib.pastila_tune_clear.argtypes = []
@@ -362,6 +365,13 @@ class Engine:
         c = EngineCounters()
         _check(load().pastila_engine_stats(self._h, ctypes.byref(c)))
         return {f: getattr(c, f) for f, _ in EngineCounters._fields_}
+
+
+def plan_layout(precision: int, n: int, m: int, smem_limit: int, ell: int = 0, k: int = 0) -> dict:
+    """``pastila_plan_layout``: the layout chosen for a length, without a device."""
+    out = np.zeros(8, dtype=np.int32)
+    _check(load().pastila_plan_layout(precision, n, m, MParams(ell, k), smem_limit, _ptr(out)))
+    return dict(zip(("W", "NG", "NT", "GS", "CS", "Rg", "Rh", "bytes"), (int(x) for x in out)))
 
 
 def tune_set(precision: int, m: int, ell: int, k: int, W: int, NG: int, GS: int, CS: int = 1):
