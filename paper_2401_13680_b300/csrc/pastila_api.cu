@@ -388,24 +388,7 @@ pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st,
                                  unsigned long long* dmax) {
     TileGeom g;
     TRY(choose_tile<real, V>(h, q, &g));
-    ProfileArgs<real> A{};  // every field zero (M, part: the plain, non-streaming form)
-    A.T = h->T;
-    A.mu = st->mu;
-    A.a = (const real*)st->a;
-    A.df = (const real*)st->df;
-    A.dg = (const real*)st->dg;
-    A.n = h->n;
-    A.C = q.C;
-    A.P = q.P;
-    A.m = q.m;
-    A.ell = q.ell;
-    A.k = q.k;
-    A.R = q.R;
-    A.S = q.S;
-    A.W = g.W;
-    A.ntiles = (int)((q.P + g.W - 1) / g.W);
-    A.D = D;
-    A.dmax_key = dmax;
+    const ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, D, dmax);
     CK(cudaFuncSetAttribute(profile_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             h->smem_optin));
     init_dmax_kernel<<<1, 1, 0, h->stream>>>(dmax);
@@ -877,23 +860,8 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
     for (int i = 0; i < n; ++i) {
         const MParams& q = qs[i];
         BatchItem<real>& it = items[i];
+        it.A = profile_args<real, V>(h, q, st[i], geo[i], (real*)dp, nullptr);  // D max key below
         ProfileArgs<real>& A = it.A;
-        A.T = h->T;
-        A.mu = st[i]->mu;
-        A.a = (const real*)st[i]->a;
-        A.df = (const real*)st[i]->df;
-        A.dg = (const real*)st[i]->dg;
-        A.n = h->n;
-        A.C = q.C;
-        A.P = q.P;
-        A.m = q.m;
-        A.ell = q.ell;
-        A.k = q.k;
-        A.R = q.R;
-        A.S = q.S;
-        A.W = geo[i].W;
-        A.ntiles = (int)((q.P + geo[i].W - 1) / geo[i].W);
-        A.D = (real*)dp;
         dp += up256(sizeof(real) * (size_t)q.S * (size_t)q.P);
         it.G = geo[i];
         it.ctas = (long long)q.S * A.ntiles * geo[i].CS;
