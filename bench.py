@@ -200,14 +200,15 @@ def fifo_latencies(arrivals, service):
     return out
 
 
-def run_serving(args, pastila, device, ed_rate, fp64_ed_rate, age_weight=0.0):
+def run_serving(args, pastila, device, ed_rate, fp64_ed_rate, age_weight=0.0, policy="share"):
     jobs = synth.serving_jobs(n_jobs=args.serve_jobs, rate=20.0, seed=3)
     series = [j.series() for j in jobs]  # drawn before the clock starts
     ed = np.array([job_ed_cells(j) for j in jobs], dtype=np.float64)
     prof = np.array([job_profile_cells(j) for j in jobs], dtype=np.float64)
     rate = args.serve_load * ed_rate / ed.mean()  # jobs/s
     arrivals = [j.arrival * 20.0 / rate for j in jobs]
-    with pastila.Engine(device=device, age_weight_s=age_weight) as e, ClockSampler(device) as clk:
+    pol = pastila.POLICY_SRPT if policy == "srpt" else pastila.POLICY_SHARE
+    with pastila.Engine(device=device, age_weight_s=age_weight, policy=pol) as e, ClockSampler(device) as clk:
         t0 = time.perf_counter()
         ids = []
         for T, j, at in zip(series, jobs, arrivals):
@@ -221,7 +222,7 @@ def run_serving(args, pastila, device, ed_rate, fp64_ed_rate, age_weight=0.0):
     lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
     span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
     out = {"jobs": len(jobs), "arrival_rate_jobs_per_s": rate, "offered_load": args.serve_load,
-           "age_weight_s": age_weight,
+           "age_weight_s": age_weight, "policy": policy,
            "workload": "serving stream seed 3: n log-uniform [1e4, 5e5], 3-8 planted regimes + N(0, 0.05^2), "
                        "3-10 lengths from {64, 96, ..., 768}, ell = m/2, K in [3, 6]; Poisson arrivals, "
                        "time-scaled from 20 jobs/s to the offered load",
@@ -230,6 +231,7 @@ def run_serving(args, pastila, device, ed_rate, fp64_ed_rate, age_weight=0.0):
            "makespan_s": span, "profile_cells_per_s": float(prof.sum() / span),
            "ed_cells_per_s": float(ed.sum() / span), "waves": st["waves"], "launches": st["launches"],
            "device_busy_frac": st["busy_ms"] / 1e3 / span, "mem_peak_gb": st["mem_peak"] / 1e9,
+           "runtime_model": {"waves_observed": st["model_waves"], "wave_rel_err": st["model_rel_err"]},
            "clocks": clk.summary()}
     if fp64_ed_rate:
         lat64 = np.array(fifo_latencies(arrivals, ed / fp64_ed_rate))
@@ -402,7 +404,11 @@ def run_ours(args):
     serving = None
     if args.serve_jobs > 0 and world == 1:
         serving = run_serving(args, pastila, local, ed_cells * args.steps / tot_s,
-                              fp64["ed_cells_per_s"] if fp64 else None, args.serve_age_weight)
+                              fp64["ed_cells_per_s"] if fp64 else None, args.serve_age_weight,
+                              "srpt" if args.serve_policy == "srpt" else "share")
+        if args.serve_policy == "both":
+            serving["srpt"] = run_serving(args, pastila, local, ed_cells * args.steps / tot_s, None,
+                                          args.serve_age_weight, "srpt")
         if args.serve_plain:
             serving["plain_fifo_measured"] = [
                 run_serving_plain(args, pastila, local, serving["arrival_rate_jobs_per_s"], prec)
@@ -440,6 +446,9 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=32, help="serving-leg jobs (0: no serving leg)")
     ap.add_argument("--serve-age-weight", type=float, default=0.0,
                     help="engine wave shares grow with job age (seconds per unit weight); 0: equal shares")
+    ap.add_argument("--serve-policy", choices=["share", "srpt", "both"], default="srpt",
+                    help="engine policy of the serving leg: processor sharing, shortest predicted remaining "
+                         "first, or both one after the other (same arrivals)")
     ap.add_argument("--serve-plain", action="store_true",
                     help="also run the serving stream one job at a time on FP32 and FP64 handles (slow)")
     ap.add_argument("--serve-load", type=float, default=0.7,

@@ -186,14 +186,15 @@ pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, int64_t P, 
  * time).  Jobs are whole select_length problems -- a series, its sweep of
  * lengths m_list, the ell/k rule and K -- submitted from any host thread and
  * run by one scheduler thread with continuous batching on one GPU:
- *   - admission: queued jobs are admitted in submission order while fewer than
+ *   - admission: queued jobs are admitted in submission order (policy SHARE)
+ *     or by predicted device time (policy SRPT) while fewer than
  *     max_active_jobs are resident and the job's resident memory (series,
  *     window statistics, K chosen profiles per length, small state) plus its
  *     largest S x P profile set fit in the memory budget; a job that can never
  *     fit is refused by pastila_engine_submit with ENOMEM;
  *   - waves: each wave is one tile launch over segment ranges of every active
- *     job's lengths (the wave's eq. 9 cells are shared equally among the active
- *     jobs), then one batched greedy search (eqs. 16-17) and criterion (eq. 18)
+ *     job's lengths (the wave's eq. 9 cells are shared among the active jobs
+ *     as the policy says), then one batched greedy search (eqs. 16-17) and criterion (eq. 18)
  *     for every length whose profiles are complete, then m_best and the eq. 8
  *     records of every job whose lengths are all done; a profile set lives only
  *     from its first wave to its greedy search;
@@ -204,6 +205,15 @@ pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, int64_t P, 
  * summation order), whatever other jobs share its waves.  All entry points
  * are thread-safe. */
 typedef struct pastila_engine pastila_engine;
+
+/* How a wave's tile work is shared among the active jobs, and the admission order. */
+typedef enum {
+    PASTILA_POLICY_SHARE = 0, /* admission in submission order; each wave's cells shared among the active
+                                 jobs (equally, or weighted by age with age_weight_s) */
+    PASTILA_POLICY_SRPT = 1   /* shortest remaining first: queued jobs are admitted in order of their
+                                 predicted device time (runtime model below), and each wave goes to the
+                                 active job with the least predicted remaining time, then the next */
+} pastila_policy;
 
 typedef struct {
     int32_t device;
@@ -217,6 +227,7 @@ typedef struct {
     double age_weight_s;         /* share of a wave per active job: 0 (default) equal shares; > 0 shares in
                                     proportion to 1 + (time since submission) / age_weight_s, which moves
                                     the engine from processor sharing toward arrival order */
+    int32_t policy;              /* pastila_policy; 0: PASTILA_POLICY_SHARE */
 } pastila_engine_config;
 
 typedef enum {
@@ -239,6 +250,7 @@ typedef struct {
     double profile_cells;     /* sum over the sweep of S * P */
     size_t mem_bytes;         /* device memory admission asks for: resident + largest profile set */
     size_t resident_bytes;    /* the part held from admission to the job's last wave */
+    double predicted_ms;      /* the runtime model's device time of the whole job, made at submission */
 } pastila_job_info;
 
 typedef struct {
@@ -249,6 +261,9 @@ typedef struct {
     double busy_ms;            /* device time of the finished waves (events around each wave) */
     size_t mem_budget, mem_held, mem_peak;
     double now;                /* engine clock */
+    uint64_t model_waves;      /* finished waves this engine fed to the runtime model */
+    double model_rel_err;      /* mean |predicted - measured| / measured of this engine's wave times,
+                                  over the waves predicted by a model with >= 8 observations; -1: none */
 } pastila_engine_counters;
 
 /* Creates an engine (its streams, memory pool and scheduler thread) on
@@ -263,6 +278,20 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
  * stopped after a device error). */
 pastila_status pastila_engine_submit(pastila_engine* e, const double* T, int64_t n, const int32_t* m_list,
                                      int32_t n_m, pastila_mparams rule, int32_t K, int64_t* job_out);
+
+/* A multivariate series of d coordinates (Section 3.1; Section 3.2 searches
+ * every coordinate on its own):
+ * T holds d coordinates of n values each, coordinate c at T + c * n.  Queues
+ * d jobs, one per coordinate with the same m_list, rule and K, in one step:
+ * every coordinate is checked and planned first and nothing is queued unless
+ * all are accepted, and the scheduler sees all d jobs at once, so their tiles
+ * share waves (one tile launch per wave for all coordinates) as far as slots
+ * and memory allow.  jobs_out[c] receives coordinate c's job id; each is
+ * polled, read and released as a job of its own.  Errors as
+ * pastila_engine_submit, and EINVAL for d outside 1..4096. */
+pastila_status pastila_engine_submit_multi(pastila_engine* e, const double* T, int64_t n, int32_t d,
+                                           const int32_t* m_list, int32_t n_m, pastila_mparams rule, int32_t K,
+                                           int64_t* jobs_out);
 
 /* Waits up to timeout_ms (0: no wait, < 0: no limit) for the job to reach
  * DONE, FAILED or CANCELLED and fills *info (may be NULL) either way.
@@ -291,6 +320,60 @@ pastila_status pastila_engine_stats(pastila_engine* e, pastila_engine_counters* 
 /* Lets the waves on the device finish, cancels every other job, stops the
  * scheduler and frees everything.  NULL is a no-op. */
 void pastila_engine_destroy(pastila_engine* e);
+
+/* ------------------------------------------------------- runtime model ---- */
+
+/* Section 4.2 predicts the run time of the search for each snippet length
+ * with a polynomial regression trained on earlier runs.  Here one such model
+ * per precision (process-wide, shared by every engine) predicts device time:
+ *   ms = c0 E + c1 E x + c2 E x^2 + c3 G + c4 w
+ * with E the eq. 9 cells of the tile work in units of 1e9 (halo columns
+ * included) at length m, x = m / 256 (summed over the lengths), G the GB of
+ * profile set the greedy search reads (K passes over S x P values per length)
+ * and w the number of engine waves.  Every finished engine wave is one
+ * observation (its features, its time between events around it); the
+ * coefficients are the least-squares fit to all observations so far, each
+ * pulled toward a prior by a ridge term of 1e-4 times its own diagonal entry
+ * of the normal matrix (plus 1e-9), so that directions the data does not
+ * determine (every wave at one length) keep the prior's values.  The engine's SRPT policy and
+ * pastila_job_info.predicted_ms use it.  Not thread-affine; all calls are
+ * thread-safe. */
+typedef struct {
+    int32_t prec;        /* pastila_precision of the model */
+    int32_t n_coef;      /* 5 */
+    double coef[5];      /* c0 .. c4 as above (ms) */
+    double prior[5];     /* the ridge term's target */
+    double xtx[25];      /* normal equations of the observations so far: sum f f^T (row-major) */
+    double xty[5];       /* sum f * ms */
+    uint64_t observations;
+    uint64_t err_count;  /* observations predicted by the model after >= 8 observations */
+    double rel_err;      /* their mean |predicted - measured| / measured; -1 when err_count is 0 */
+} pastila_runtime_model;
+
+/* Copies the model of prec.  Errors: EINVAL. */
+pastila_status pastila_model_get(pastila_precision prec, pastila_runtime_model* out);
+
+/* Replaces the model of in->prec by in's prior and normal equations (a warm
+ * start from an earlier process's pastila_model_get) and refits; coef, the
+ * error fields and n_coef are ignored.  Errors: EINVAL (n_coef != 5, a
+ * non-finite entry, unknown precision). */
+pastila_status pastila_model_set(const pastila_runtime_model* in);
+
+/* Adds one observation: features f[5] = {E, E x, E x^2, G, w} as above and its
+ * measured time ms > 0 (for callers that time their own runs).  Errors: EINVAL. */
+pastila_status pastila_model_observe(pastila_precision prec, const double* f, double ms);
+
+/* Forgets every observation of prec (coefficients back to the prior).  Errors: EINVAL. */
+pastila_status pastila_model_reset(pastila_precision prec);
+
+/* Predicted device time (ms) of one job as the engine plans it: its lengths'
+ * tile cells under the tile layouts chosen for smem_limit bytes of shared
+ * memory per CTA (pastila_plan_layout), K greedy passes per length and one
+ * wave per wave_ed_cells of tile work (0: 4e9).  Host code only.  Errors:
+ * EINVAL (arguments as pastila_engine_submit, no layout fits). */
+pastila_status pastila_model_predict(pastila_precision prec, int64_t n, const int32_t* m_list, int32_t n_m,
+                                     pastila_mparams rule, int32_t K, size_t smem_limit, double wave_ed_cells,
+                                     double* ms_out);
 
 /* The greedy snippet search of pastila_snippets without materialising the S x P
  * profile set, for lengths whose D does not fit the budget or the device
@@ -358,6 +441,7 @@ pastila_status pastila_tune_get(pastila_precision prec, int32_t m, int32_t ell, 
 
 /* The tile layout that h's calls use for length m with mp: out5 = {W, NG (row
  * groups per CTA), NT (threads per CTA), GS, CS}.  Errors: EINVAL. */
+pastila_status pastila_tile_layout(pastila_series* h, int32_t m, pastila_mparams mp, int32_t* out5);
 
 /* The same choice without a device (host code only): the tuned table's entry
  * if it fits smem_limit bytes of dynamic shared memory per CTA, else the cost
@@ -366,7 +450,6 @@ pastila_status pastila_tune_get(pastila_precision prec, int32_t m, int32_t ell, 
  * layout fits). */
 pastila_status pastila_plan_layout(pastila_precision prec, int64_t n, int32_t m, pastila_mparams mp,
                                    size_t smem_limit, int32_t* out8);
-pastila_status pastila_tile_layout(pastila_series* h, int32_t m, pastila_mparams mp, int32_t* out5);
 
 /* ------------------------------------------------------------- tracing ---- */
 

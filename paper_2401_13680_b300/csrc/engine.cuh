@@ -42,6 +42,8 @@
 #include <memory>
 #include <thread>
 
+#include "runtime_model.cuh"
+
 namespace pastila {
 
 template <typename real>
@@ -226,6 +228,7 @@ struct EJob {
     double t_submit = -1, t_admit = -1, t_done = -1;
     int64_t first_wave = -1, last_wave = -1;
     double ed_cells = 0.0, profile_cells = 0.0;
+    double pred_ms = 0.0;  // the runtime model's device time for the whole job, at submission
     int32_t m_best = 0;
     std::vector<double> crit;
     std::vector<pastila_snippet> recs;
@@ -234,12 +237,27 @@ struct EJob {
 struct EWave {
     int64_t id = 0;
     int slot = 0;
+    double feat[RM_NF] = {0, 0, 0, 0, 0};  // runtime-model features of the wave's work
+    double pred = -1.0;                     // the model's prediction when the wave was formed
+    bool trained = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> recycle;
     std::vector<int64_t> finals;
 };
 
 inline size_t up256e(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Runtime-model features of a job's remaining work: the tile cells of the
+// segments not yet issued and the greedy reads of the lengths whose search is
+// not yet issued (the per-wave feature is left at 0).
+template <typename real>
+void job_features(const EJob& j, double* f) {
+    for (int i = 0; i < RM_NF; ++i) f[i] = 0.0;
+    for (const EItem& it : j.items) {
+        if (it.state < 2) rm_add_cells(f, (double)(it.q.S - it.next_seg) * it.cells_per_seg, it.q.m);
+        if (it.state < 3) f[3] += (double)j.K * (double)it.q.S * (double)it.q.P * (double)sizeof(real) * 1e-9;
+    }
+}
 
 }  // namespace
 
@@ -250,6 +268,7 @@ struct pastila_engine {
     int max_active = 0, max_inflight = 0;
     double wave_cells = 0.0;
     double age_weight = 0.0;
+    int policy = PASTILA_POLICY_SHARE;
     int fail_at = 0;
     int64_t alloc_count = 0;
     int smem_optin = 0;
@@ -278,6 +297,8 @@ struct pastila_engine {
     // counters
     uint64_t n_submitted = 0, n_done = 0, n_failed = 0, n_cancelled = 0, n_waves = 0, launches = 0;
     double ed_cells = 0.0, profile_cells = 0.0, busy_ms = 0.0;
+    uint64_t model_obs = 0, model_err_n = 0;
+    double model_err_sum = 0.0;
 };
 
 namespace {
@@ -513,7 +534,11 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         e->active.erase(e->active.begin() + a);
         changed = true;
     }
-    // 2. admission in arrival order
+    // 2. admission in arrival order, or (shortest-remaining-first policy) in
+    // order of the jobs' predicted device time, arrival order among equals
+    if (e->policy == PASTILA_POLICY_SRPT && e->pending.size() > 1)
+        std::stable_sort(e->pending.begin(), e->pending.end(),
+                         [e](int64_t x, int64_t y) { return e->jobs[x]->pred_ms < e->jobs[y]->pred_ms; });
     while (!e->pending.empty() && e->holding < e->max_active) {
         EJob& j = *e->jobs[e->pending.front()];
         if (j.cancel_req) {
@@ -598,7 +623,25 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         }
         return PASTILA_OK;
     };
-    if (!with_work.empty()) {
+    if (!with_work.empty() && e->policy == PASTILA_POLICY_SRPT) {
+        // the whole wave to the job with the least predicted remaining device
+        // time, then the next (admission order among equals)
+        std::vector<double> rem(with_work.size());
+        {
+            std::lock_guard<std::mutex> lk(rm_table().mu);
+            const RuntimeModel& rm = rm_table().m[e->prec == PASTILA_FP64];
+            for (size_t i = 0; i < with_work.size(); ++i) {
+                double f[RM_NF];
+                job_features<real>(*with_work[i], f);
+                rem[i] = rm.predict(f);
+            }
+        }
+        std::vector<size_t> ord(with_work.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return rem[x] < rem[y]; });
+        for (size_t i : ord)
+            if (used < e->wave_cells) TRY(take(*with_work[i], e->wave_cells - used));
+    } else if (!with_work.empty()) {
         // equal shares, or shares growing with the time since submission
         const double now = eng_now(e);
         std::vector<double> wt(with_work.size(), 1.0);
@@ -664,6 +707,7 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
     real** h_keep = (real**)(hd + 2 * bi_bytes);
     JobFinal<real>* h_fin = (JobFinal<real>*)(hd + 2 * bi_bytes + kp_bytes);
     double wave_cells = 0.0;
+    double wfeat[RM_NF] = {0, 0, 0, 0, 1};
     // one tile launch per cluster size (a launch has a single cluster shape), each
     // numbering its own CTAs; chunks ordered by cluster size
     std::stable_sort(merged.begin(), merged.end(), [](const Chunk& x, const Chunk& y) {
@@ -689,6 +733,7 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         tg.block = std::max(tg.block, it.g.NT);
         tg.smem = std::max(tg.smem, it.g.bytes);
         wave_cells += ch.segs * it.cells_per_seg;
+        rm_add_cells(wfeat, ch.segs * it.cells_per_seg, it.q.m);
         if (ch.job->first_wave < 0) ch.job->first_wave = wave_id;
         ch.job->last_wave = wave_id;
     }
@@ -703,6 +748,10 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
         gmaxS = std::max<int64_t>(gmaxS, it.q.S);
         gmaxP = std::max<int64_t>(gmaxP, it.q.P);
         j.last_wave = wave_id;
+    }
+    for (size_t g = 0; g < greedy.size(); ++g) {  // every search runs Kmax area passes
+        const EItem& it = greedy[g].first->items[greedy[g].second];
+        wfeat[3] += (double)Kmax * (double)it.q.S * (double)it.q.P * (double)sizeof(real) * 1e-9;
     }
     int64_t fmaxP = 0;
     for (size_t f = 0; f < finals.size(); ++f) {
@@ -739,6 +788,13 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
     TRY(eng_event(e, &w.ev0));
     TRY(eng_event(e, &w.ev1));
     w.recycle = recycle;
+    memcpy(w.feat, wfeat, sizeof wfeat);
+    {
+        std::lock_guard<std::mutex> lk(rm_table().mu);
+        const RuntimeModel& rm = rm_table().m[e->prec == PASTILA_FP64];
+        w.pred = rm.predict(wfeat);
+        w.trained = rm.n >= RM_TRAINED;
+    }
     cudaStream_t s = e->cs;
     CK(cudaEventRecord(w.ev0, s));
     if (!merged.empty())
@@ -852,7 +908,16 @@ void harvest(pastila_engine* e) {
             return;
         }
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, w.ev0, w.ev1) == cudaSuccess) e->busy_ms += ms;
+        if (cudaEventElapsedTime(&ms, w.ev0, w.ev1) == cudaSuccess) {
+            e->busy_ms += ms;
+            std::lock_guard<std::mutex> lk(rm_table().mu);
+            rm_table().m[e->prec == PASTILA_FP64].observe(w.feat, (double)ms, w.pred, w.trained);
+            e->model_obs++;
+            if (w.trained && ms > 0.f) {
+                e->model_err_sum += std::fabs(w.pred - (double)ms) / (double)ms;
+                e->model_err_n++;
+            }
+        }
         for (int64_t id : w.finals) {
             EJob& j = *e->jobs[id];
             read_results(e, j);
@@ -960,6 +1025,8 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
     if (!(c.wave_ed_cells >= 0.0)) return fail(PASTILA_EINVAL, "wave_ed_cells must be >= 0");
     if (c.fail_alloc_at < 0) return fail(PASTILA_EINVAL, "fail_alloc_at must be >= 0");
     if (!(c.age_weight_s >= 0.0)) return fail(PASTILA_EINVAL, "age_weight_s must be >= 0");
+    if (c.policy != PASTILA_POLICY_SHARE && c.policy != PASTILA_POLICY_SRPT)
+        return fail(PASTILA_EINVAL, "unknown policy %d", (int)c.policy);
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev));
     if (c.device < 0 || c.device >= ndev) return fail(PASTILA_EINVAL, "device %d: %d device(s) visible", c.device, ndev);
@@ -972,6 +1039,7 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
     e->wave_cells = c.wave_ed_cells > 0.0 ? c.wave_ed_cells : 4e9;
     e->fail_at = c.fail_alloc_at;
     e->age_weight = c.age_weight_s;
+    e->policy = c.policy;
     int smem = 0;
     CK(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
     e->smem_optin = smem - 1024;
@@ -1037,10 +1105,19 @@ pastila_status pastila_engine_submit(pastila_engine* e, const double* T, int64_t
     j->n = n;
     j->ms.assign(m_list, m_list + n_m);
     j->K = K;
-    if (e->prec == PASTILA_FP64)
+    double f[RM_NF];
+    if (e->prec == PASTILA_FP64) {
         TRY(plan_job<double, V_F64>(e, *j, rule));
-    else
+        job_features<double>(*j, f);
+    } else {
         TRY(plan_job<float, V_F32>(e, *j, rule));
+        job_features<float>(*j, f);
+    }
+    f[4] = std::ceil(j->ed_cells / e->wave_cells);
+    {
+        std::lock_guard<std::mutex> lk(rm_table().mu);
+        j->pred_ms = rm_table().m[e->prec == PASTILA_FP64].predict(f);
+    }
     if (j->res_bytes + j->max_dbytes > e->budget)
         return fail(PASTILA_ENOMEM, "the job needs %zu bytes of device memory (resident %zu + largest profile set %zu); "
                     "the engine's budget is %zu", j->res_bytes + j->max_dbytes, j->res_bytes, j->max_dbytes, e->budget);
@@ -1054,6 +1131,63 @@ pastila_status pastila_engine_submit(pastila_engine* e, const double* T, int64_t
     e->pending.push_back(j->id);
     e->jobs[j->id] = std::move(j);
     e->n_submitted++;
+    e->cv_sched.notify_one();
+    return PASTILA_OK;
+}
+
+pastila_status pastila_engine_submit_multi(pastila_engine* e, const double* T, int64_t n, int32_t d,
+                                           const int32_t* m_list, int32_t n_m, pastila_mparams rule, int32_t K,
+                                           int64_t* jobs_out) {
+    g_err.clear();
+    if (!e) return fail(PASTILA_EINVAL, "engine is NULL");
+    if (!T) return fail(PASTILA_EINVAL, "T is NULL");
+    if (!jobs_out) return fail(PASTILA_EINVAL, "jobs_out is NULL");
+    if (d < 1 || d > 4096) return fail(PASTILA_EINVAL, "d = %d: 1 to 4096 coordinates", d);
+    if (n < 4) return fail(PASTILA_EINVAL, "n = %lld: the series needs at least 4 values", (long long)n);
+    if (!m_list || n_m < 1 || n_m > ENGINE_MAX_SWEEP)
+        return fail(PASTILA_EINVAL, "n_m = %d: a job sweeps 1 to %d lengths", n_m, ENGINE_MAX_SWEEP);
+    // every coordinate is checked and planned before any is queued
+    std::vector<std::unique_ptr<EJob>> js;
+    for (int c = 0; c < d; ++c) {
+        const double* Tc = T + (size_t)c * (size_t)n;
+        pastila_status st = check_finite(Tc, n);
+        if (st != PASTILA_OK) return fail(st, "coordinate %d: %s", c, g_err.c_str());
+        std::unique_ptr<EJob> j(new EJob());
+        j->n = n;
+        j->ms.assign(m_list, m_list + n_m);
+        j->K = K;
+        double f[RM_NF];
+        if (e->prec == PASTILA_FP64) {
+            TRY(plan_job<double, V_F64>(e, *j, rule));
+            job_features<double>(*j, f);
+        } else {
+            TRY(plan_job<float, V_F32>(e, *j, rule));
+            job_features<float>(*j, f);
+        }
+        f[4] = std::ceil(j->ed_cells / e->wave_cells);
+        {
+            std::lock_guard<std::mutex> lk(rm_table().mu);
+            j->pred_ms = rm_table().m[e->prec == PASTILA_FP64].predict(f);
+        }
+        if (j->res_bytes + j->max_dbytes > e->budget)
+            return fail(PASTILA_ENOMEM, "a coordinate needs %zu bytes of device memory; the engine's budget is %zu",
+                        j->res_bytes + j->max_dbytes, e->budget);
+        j->T.assign(Tc, Tc + n);
+        js.push_back(std::move(j));
+    }
+    std::lock_guard<std::mutex> lk(e->mu);
+    if (e->broken) return fail(PASTILA_ECUDA, "the engine stopped after a device error: %s", e->broken_msg.c_str());
+    if (e->stop) return fail(PASTILA_EINVAL, "the engine is shutting down");
+    const double now = eng_now(e);
+    for (int c = 0; c < d; ++c) {
+        std::unique_ptr<EJob>& j = js[c];
+        j->id = e->next_id++;
+        j->t_submit = now;
+        jobs_out[c] = j->id;
+        e->pending.push_back(j->id);
+        e->jobs[j->id] = std::move(j);
+        e->n_submitted++;
+    }
     e->cv_sched.notify_one();
     return PASTILA_OK;
 }
@@ -1083,6 +1217,7 @@ pastila_status pastila_engine_poll(pastila_engine* e, int64_t job, int32_t timeo
         info->profile_cells = j->profile_cells;
         info->mem_bytes = j->res_bytes + j->max_dbytes;
         info->resident_bytes = j->res_bytes;
+        info->predicted_ms = j->pred_ms;
     }
     if (!job_final(*j)) return fail(PASTILA_ETIMEOUT, "job %lld has not finished", (long long)job);
     return PASTILA_OK;
@@ -1145,6 +1280,8 @@ pastila_status pastila_engine_stats(pastila_engine* e, pastila_engine_counters* 
     out->mem_held = e->held;
     out->mem_peak = e->peak;
     out->now = eng_now(e);
+    out->model_waves = e->model_obs;
+    out->model_rel_err = e->model_err_n ? e->model_err_sum / (double)e->model_err_n : -1.0;
     return PASTILA_OK;
 }
 
@@ -1159,6 +1296,102 @@ void pastila_engine_destroy(pastila_engine* e) {
     cudaSetDevice(e->device);
     engine_release_resources(e);
     delete e;
+}
+
+pastila_status pastila_model_get(pastila_precision prec, pastila_runtime_model* out) {
+    g_err.clear();
+    if (!out) return fail(PASTILA_EINVAL, "out is NULL");
+    if (prec != PASTILA_FP32 && prec != PASTILA_FP64) return fail(PASTILA_EINVAL, "unknown precision %d", (int)prec);
+    std::lock_guard<std::mutex> lk(rm_table().mu);
+    const RuntimeModel& m = rm_table().m[prec == PASTILA_FP64];
+    memset(out, 0, sizeof *out);
+    out->prec = prec;
+    out->n_coef = RM_NF;
+    memcpy(out->coef, m.coef, sizeof m.coef);
+    memcpy(out->prior, m.prior, sizeof m.prior);
+    memcpy(out->xtx, m.xtx, sizeof m.xtx);
+    memcpy(out->xty, m.xty, sizeof m.xty);
+    out->observations = m.n;
+    out->err_count = m.err_n;
+    out->rel_err = m.err_n ? m.err_sum / (double)m.err_n : -1.0;
+    return PASTILA_OK;
+}
+
+pastila_status pastila_model_set(const pastila_runtime_model* in) {
+    g_err.clear();
+    if (!in) return fail(PASTILA_EINVAL, "model is NULL");
+    if (in->prec != PASTILA_FP32 && in->prec != PASTILA_FP64)
+        return fail(PASTILA_EINVAL, "unknown precision %d", (int)in->prec);
+    if (in->n_coef != RM_NF) return fail(PASTILA_EINVAL, "n_coef = %d: the model has %d coefficients", in->n_coef, RM_NF);
+    for (int i = 0; i < RM_NF * RM_NF; ++i)
+        if (!std::isfinite(in->xtx[i])) return fail(PASTILA_EINVAL, "xtx[%d] is not finite", i);
+    for (int i = 0; i < RM_NF; ++i)
+        if (!std::isfinite(in->xty[i]) || !std::isfinite(in->prior[i]))
+            return fail(PASTILA_EINVAL, "xty[%d] or prior[%d] is not finite", i, i);
+    std::lock_guard<std::mutex> lk(rm_table().mu);
+    RuntimeModel& m = rm_table().m[in->prec == PASTILA_FP64];
+    m.reset(in->prior);
+    memcpy(m.xtx, in->xtx, sizeof m.xtx);
+    memcpy(m.xty, in->xty, sizeof m.xty);
+    m.n = in->observations;
+    m.refit();
+    return PASTILA_OK;
+}
+
+pastila_status pastila_model_observe(pastila_precision prec, const double* f, double ms) {
+    g_err.clear();
+    if (!f) return fail(PASTILA_EINVAL, "f is NULL");
+    if (prec != PASTILA_FP32 && prec != PASTILA_FP64) return fail(PASTILA_EINVAL, "unknown precision %d", (int)prec);
+    if (!(ms > 0.0) || !std::isfinite(ms)) return fail(PASTILA_EINVAL, "ms must be finite and > 0");
+    for (int i = 0; i < RM_NF; ++i)
+        if (!std::isfinite(f[i])) return fail(PASTILA_EINVAL, "f[%d] is not finite", i);
+    std::lock_guard<std::mutex> lk(rm_table().mu);
+    RuntimeModel& m = rm_table().m[prec == PASTILA_FP64];
+    m.observe(f, ms, m.predict(f), m.n >= RM_TRAINED);
+    return PASTILA_OK;
+}
+
+pastila_status pastila_model_reset(pastila_precision prec) {
+    g_err.clear();
+    if (prec != PASTILA_FP32 && prec != PASTILA_FP64) return fail(PASTILA_EINVAL, "unknown precision %d", (int)prec);
+    std::lock_guard<std::mutex> lk(rm_table().mu);
+    rm_table().m[prec == PASTILA_FP64].reset(rm_prior(prec == PASTILA_FP64));
+    return PASTILA_OK;
+}
+
+pastila_status pastila_model_predict(pastila_precision prec, int64_t n, const int32_t* m_list, int32_t n_m,
+                                     pastila_mparams rule, int32_t K, size_t smem_limit, double wave_ed_cells,
+                                     double* ms_out) {
+    g_err.clear();
+    if (!ms_out) return fail(PASTILA_EINVAL, "ms_out is NULL");
+    if (prec != PASTILA_FP32 && prec != PASTILA_FP64) return fail(PASTILA_EINVAL, "unknown precision %d", (int)prec);
+    if (!m_list || n_m < 1 || n_m > ENGINE_MAX_SWEEP)
+        return fail(PASTILA_EINVAL, "n_m = %d: a job sweeps 1 to %d lengths", n_m, ENGINE_MAX_SWEEP);
+    if (!(wave_ed_cells >= 0.0)) return fail(PASTILA_EINVAL, "wave_ed_cells must be >= 0");
+    const double rs = prec == PASTILA_FP64 ? 8.0 : 4.0;
+    double f[RM_NF] = {0, 0, 0, 0, 0}, cells = 0.0;
+    int min_S = 1 << 30;
+    for (int u = 0; u < n_m; ++u) {
+        MParams q;
+        TRY(resolve_n(n, m_list[u], rule, &q));
+        TileGeom g;
+        if (prec == PASTILA_FP64)
+            TRY(choose_tile_s<double, V_F64>(smem_limit, q, &g));
+        else
+            TRY(choose_tile_s<float, V_F32>(smem_limit, q, &g));
+        const double ntiles = (double)((q.P + g.W - 1) / g.W);
+        const double c = (double)q.S * ntiles * (double)q.R * (double)g.Wb;
+        rm_add_cells(f, c, q.m);
+        cells += c;
+        f[3] += (double)K * (double)q.S * (double)q.P * rs * 1e-9;
+        min_S = std::min(min_S, q.S);
+    }
+    if (K < 2 || K > min_S || K > ENGINE_MAX_K)
+        return fail(PASTILA_EINVAL, "K = %d: must satisfy 2 <= K <= min(n / max m, 64) = %d", K, std::min(min_S, 64));
+    f[4] = std::ceil(cells / (wave_ed_cells > 0.0 ? wave_ed_cells : 4e9));
+    std::lock_guard<std::mutex> lk(rm_table().mu);
+    *ms_out = rm_table().m[prec == PASTILA_FP64].predict(f);
+    return PASTILA_OK;
 }
 
 }  // extern "C"

@@ -33,14 +33,18 @@ class EngineConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("prec", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
                 ("max_active_jobs", ctypes.c_int32), ("wave_ed_cells", ctypes.c_double),
                 ("max_waves_in_flight", ctypes.c_int32), ("fail_alloc_at", ctypes.c_int32),
-                ("age_weight_s", ctypes.c_double)]
+                ("age_weight_s", ctypes.c_double), ("policy", ctypes.c_int32)]
+
+
+POLICY_SHARE, POLICY_SRPT = 0, 1
 
 
 class JobInfo(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("t_submit", ctypes.c_double),
                 ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("first_wave", ctypes.c_int64),
                 ("last_wave", ctypes.c_int64), ("ed_cells", ctypes.c_double), ("profile_cells", ctypes.c_double),
-                ("mem_bytes", ctypes.c_size_t), ("resident_bytes", ctypes.c_size_t)]
+                ("mem_bytes", ctypes.c_size_t), ("resident_bytes", ctypes.c_size_t),
+                ("predicted_ms", ctypes.c_double)]
 
 
 class EngineCounters(ctypes.Structure):
@@ -48,7 +52,13 @@ class EngineCounters(ctypes.Structure):
                 ("cancelled", ctypes.c_uint64), ("waves", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("ed_cells", ctypes.c_double), ("profile_cells", ctypes.c_double), ("busy_ms", ctypes.c_double),
                 ("mem_budget", ctypes.c_size_t), ("mem_held", ctypes.c_size_t), ("mem_peak", ctypes.c_size_t),
-                ("now", ctypes.c_double)]
+                ("now", ctypes.c_double), ("model_waves", ctypes.c_uint64), ("model_rel_err", ctypes.c_double)]
+
+
+class RuntimeModel(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("n_coef", ctypes.c_int32), ("coef", ctypes.c_double * 5),
+                ("prior", ctypes.c_double * 5), ("xtx", ctypes.c_double * 25), ("xty", ctypes.c_double * 5),
+                ("observations", ctypes.c_uint64), ("err_count", ctypes.c_uint64), ("rel_err", ctypes.c_double)]
 
 
 class TuneResult(ctypes.Structure):
@@ -131,6 +141,9 @@ def load(path: str | None = None):
         lib.pastila_engine_submit.argtypes = [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32, MParams,
                                               ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
         lib.pastila_engine_submit.restype = S
+        lib.pastila_engine_submit_multi.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, ctypes.c_int32,
+                                                    MParams, ctypes.c_int32, _vp]
+        lib.pastila_engine_submit_multi.restype = S
         lib.pastila_engine_poll.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(JobInfo)]
         lib.pastila_engine_poll.restype = S
         lib.pastila_engine_result.argtypes = [_vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), _vp,
@@ -144,6 +157,18 @@ def load(path: str | None = None):
         lib.pastila_engine_stats.restype = S
         lib.pastila_engine_destroy.argtypes = [_vp]
         lib.pastila_engine_destroy.restype = None
+        lib.pastila_model_get.argtypes = [ctypes.c_int, ctypes.POINTER(RuntimeModel)]
+        lib.pastila_model_get.restype = S
+        lib.pastila_model_set.argtypes = [ctypes.POINTER(RuntimeModel)]
+        lib.pastila_model_set.restype = S
+        lib.pastila_model_observe.argtypes = [ctypes.c_int, _vp, ctypes.c_double]
+        lib.pastila_model_observe.restype = S
+        lib.pastila_model_reset.argtypes = [ctypes.c_int]
+        lib.pastila_model_reset.restype = S
+        lib.pastila_model_predict.argtypes = [ctypes.c_int, ctypes.c_int64, _vp, ctypes.c_int32, MParams,
+                                              ctypes.c_int32, ctypes.c_size_t, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_double)]
+        lib.pastila_model_predict.restype = S
         _lib = lib
     return _lib
 
@@ -298,10 +323,10 @@ class Engine:
 
     def __init__(self, device: int = 0, precision: int = FP32, mem_budget: int = 0, max_active: int = 0,
                  wave_ed_cells: float = 0.0, max_waves_in_flight: int = 0, fail_alloc_at: int = 0,
-                 age_weight_s: float = 0.0):
+                 age_weight_s: float = 0.0, policy: int = POLICY_SHARE):
         lib = load()
         cfg = EngineConfig(device, precision, mem_budget, max_active, wave_ed_cells, max_waves_in_flight,
-                           fail_alloc_at, age_weight_s)
+                           fail_alloc_at, age_weight_s, policy)
         h = _vp()
         _check(lib.pastila_engine_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h
@@ -333,6 +358,19 @@ class Engine:
                                             K, ctypes.byref(job)))
         self._sizes[job.value] = (ms.shape[0], K)
         return job.value
+
+    def submit_multivariate(self, T, ms, K: int, ell: int = 0, k: int = 0) -> list:
+        """Queues one job per coordinate of a (d, n) series in one step
+        (``pastila_engine_submit_multi``); returns the d job ids."""
+        T = np.ascontiguousarray(np.atleast_2d(T), dtype=np.float64)
+        ms = np.ascontiguousarray(ms, dtype=np.int32)
+        d, n = T.shape
+        ids = np.zeros(d, dtype=np.int64)
+        _check(load().pastila_engine_submit_multi(self._h, _ptr(T), n, d, _ptr(ms), ms.shape[0], MParams(ell, k),
+                                                  K, _ptr(ids)))
+        for j in ids:
+            self._sizes[int(j)] = (ms.shape[0], K)
+        return [int(j) for j in ids]
 
     def poll(self, job: int, timeout_ms: int = 0):
         """(final?, JobInfo as a dict)."""
@@ -372,6 +410,51 @@ def plan_layout(precision: int, n: int, m: int, smem_limit: int, ell: int = 0, k
     out = np.zeros(8, dtype=np.int32)
     _check(load().pastila_plan_layout(precision, n, m, MParams(ell, k), smem_limit, _ptr(out)))
     return dict(zip(("W", "NG", "NT", "GS", "CS", "Rg", "Rh", "bytes"), (int(x) for x in out)))
+
+
+def model_get(precision: int) -> dict:
+    """``pastila_model_get``: the runtime model of a precision, as a dict of
+    numpy arrays (coef, prior, xtx 5x5, xty) and counts."""
+    r = RuntimeModel()
+    _check(load().pastila_model_get(precision, ctypes.byref(r)))
+    return {"prec": r.prec, "coef": np.array(r.coef[:]), "prior": np.array(r.prior[:]),
+            "xtx": np.array(r.xtx[:]).reshape(5, 5), "xty": np.array(r.xty[:]),
+            "observations": int(r.observations), "err_count": int(r.err_count), "rel_err": r.rel_err}
+
+
+def model_set(model: dict):
+    """``pastila_model_set``: warm start from a dict as model_get returns it."""
+    r = RuntimeModel()
+    r.prec = int(model["prec"])
+    r.n_coef = int(model.get("n_coef", 5))
+    r.prior[:] = [float(x) for x in np.asarray(model["prior"], dtype=np.float64).ravel()]
+    r.xtx[:] = [float(x) for x in np.asarray(model["xtx"], dtype=np.float64).ravel()]
+    r.xty[:] = [float(x) for x in np.asarray(model["xty"], dtype=np.float64).ravel()]
+    r.observations = int(model.get("observations", 0))
+    _check(load().pastila_model_set(ctypes.byref(r)))
+
+
+def model_observe(precision: int, features, ms: float):
+    """``pastila_model_observe``: one measured unit of work (5 features, ms)."""
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    if f.shape != (5,):
+        raise ValueError("features must have 5 entries")
+    _check(load().pastila_model_observe(precision, _ptr(f), ms))
+
+
+def model_reset(precision: int):
+    """``pastila_model_reset``: forget every observation of a precision."""
+    _check(load().pastila_model_reset(precision))
+
+
+def model_predict(precision: int, n: int, ms, K: int, smem_limit: int, ell: int = 0, k: int = 0,
+                  wave_ed_cells: float = 0.0) -> float:
+    """``pastila_model_predict``: predicted device time (ms) of a job, without a device."""
+    ms = np.ascontiguousarray(ms, dtype=np.int32)
+    out = ctypes.c_double()
+    _check(load().pastila_model_predict(precision, n, _ptr(ms), ms.shape[0], MParams(ell, k), K, smem_limit,
+                                        wave_ed_cells, ctypes.byref(out)))
+    return out.value
 
 
 def tune_set(precision: int, m: int, ell: int, k: int, W: int, NG: int, GS: int, CS: int = 1):

@@ -54,12 +54,19 @@ def test_engine_host_side_validation():
     assert "precision" in pastila.last_error()
     bad = pastila.EngineConfig(0, pastila.FP32, 0, 1000, 0.0, 0, 0, 0.0)
     assert lib.pastila_engine_create(ctypes.byref(e), ctypes.byref(bad)) == pastila.EINVAL
+    bad = pastila.EngineConfig(0, pastila.FP32, 0, 0, 0.0, 0, 0, 0.0, 5)
+    assert lib.pastila_engine_create(ctypes.byref(e), ctypes.byref(bad)) == pastila.EINVAL
+    assert "policy" in pastila.last_error()
     job = ctypes.c_int64()
     T = np.zeros(100)
     ms = np.array([16], dtype=np.int32)
     assert lib.pastila_engine_submit(None, T.ctypes.data_as(ctypes.c_void_p), 100,
                                      ms.ctypes.data_as(ctypes.c_void_p), 1, pastila.MParams(0, 0), 2,
                                      ctypes.byref(job)) == pastila.EINVAL
+    ids = np.zeros(2, dtype=np.int64)
+    assert lib.pastila_engine_submit_multi(None, T.ctypes.data_as(ctypes.c_void_p), 50, 2,
+                                           ms.ctypes.data_as(ctypes.c_void_p), 1, pastila.MParams(0, 0), 2,
+                                           ids.ctypes.data_as(ctypes.c_void_p)) == pastila.EINVAL
     assert lib.pastila_engine_poll(None, 1, 0, None) == pastila.EINVAL
     assert lib.pastila_engine_result(None, 1, None, None, None) == pastila.EINVAL
     assert lib.pastila_engine_cancel(None, 1) == pastila.EINVAL

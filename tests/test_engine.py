@@ -208,3 +208,92 @@ def test_submit_argument_errors(lib):
         e.release(j)
         with pytest.raises(pastila.PastilaError, match="unknown"):
             e.result(j)
+
+
+def test_srpt_admits_shortest_predicted_first_with_identical_results(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()
+    rng = np.random.default_rng(12)
+    big = jobs[3]
+    # three small jobs, submitted largest first
+    small = [(synth.random_planted(rng, n, 4).T, [64, 96], 3) for n in (16_000, 11_000, 6_000)]
+    with pastila.Engine(max_active=1, policy=pastila.POLICY_SRPT) as e:
+        ids = [e.submit(*big)] + [e.submit(*s) for s in small]
+        infos = [e.wait(j) for j in ids]
+        res = [e.result(j) for j in ids]
+        st = e.stats()
+    assert all(i["state"] == pastila.JOB_DONE for i in infos)
+    pred = [i["predicted_ms"] for i in infos[1:]]
+    assert pred[0] > pred[1] > pred[2] > 0
+    # the queued small jobs are admitted shortest first, against their arrival order
+    t_admit = [i["t_admit"] for i in infos[1:]]
+    assert t_admit[2] < t_admit[1] < t_admit[0]
+    for (T, ms, K), r in zip([big] + small, res):
+        _same(r, _run_alone(pastila, T, ms, K, pastila.FP32))
+    assert st["model_waves"] == st["waves"]
+
+
+def test_srpt_in_a_mix_gives_the_results_of_each_job_alone(lib):
+    from paper_2401_13680_b300 import pastila
+    jobs = _jobs()
+    alone = [_run_alone(pastila, T, ms, K, pastila.FP32) for T, ms, K in jobs]
+    with pastila.Engine(wave_ed_cells=3e7, max_waves_in_flight=3, policy=pastila.POLICY_SRPT) as e:
+        ids = [e.submit(T, ms, K) for T, ms, K in jobs]
+        infos = [e.wait(j) for j in ids]
+        mixed = [e.result(j) for j in ids]
+    for a, b in zip(alone, mixed):
+        _same(a, b)
+    # shortest remaining first: the job with the least predicted work finishes first
+    order = sorted(range(len(jobs)), key=lambda q: infos[q]["predicted_ms"])
+    assert infos[order[0]]["t_done"] == min(i["t_done"] for i in infos)
+
+
+def test_runtime_model_learns_the_wave_times(lib):
+    from paper_2401_13680_b300 import pastila
+    saved = pastila.model_get(pastila.FP32)
+    try:
+        pastila.model_reset(pastila.FP32)
+        jobs = _jobs()
+        with pastila.Engine(wave_ed_cells=2e8) as e:
+            for T, ms, K in jobs:
+                e.wait(e.submit(T, ms, K))
+            st = e.stats()
+        m = pastila.model_get(pastila.FP32)
+        assert st["model_waves"] == st["waves"] >= 10
+        assert m["observations"] == st["model_waves"]
+        assert np.all(np.isfinite(m["coef"]))
+        # trained predictions of the later waves are within a factor of two on average
+        assert 0.0 <= st["model_rel_err"] < 1.0
+        # a job alone: the trained model's prediction against the engine's device time
+        T, ms, K = jobs[1]
+        with pastila.Engine(wave_ed_cells=2e8) as e:
+            info = e.wait(e.submit(T, ms, K))
+            busy = e.stats()["busy_ms"]
+        assert 0.5 * busy < info["predicted_ms"] < 2.0 * busy
+    finally:
+        pastila.model_set(saved)
+
+
+def test_multivariate_series_shares_waves_and_matches_each_coordinate(lib):
+    from paper_2401_13680_b300 import pastila
+    rng = np.random.default_rng(13)
+    d, n = 3, 15_000
+    T = np.stack([synth.random_planted(rng, n, 4).T for _ in range(d)])
+    ms, K = [64, 128], 3
+    with pastila.Engine() as e:
+        ids = e.submit_multivariate(T, ms, K)
+        infos = [e.wait(j) for j in ids]
+        res = [e.result(j) for j in ids]
+    assert all(i["state"] == pastila.JOB_DONE for i in infos)
+    # the scheduler saw every coordinate at once: one wave carried all their first tiles
+    assert len({i["first_wave"] for i in infos}) == 1
+    for c in range(d):
+        with pastila.Series(T[c], precision=pastila.FP32) as h:
+            _same(res[c], h.select_length(ms, K))
+    # one bad coordinate rejects the whole submission
+    bad = T.copy()
+    bad[2, 5] = np.nan
+    with pastila.Engine() as e:
+        with pytest.raises(pastila.PastilaError, match="coordinate 2"):
+            e.submit_multivariate(bad, ms, K)
+        assert e.stats()["submitted"] == 0
