@@ -52,9 +52,10 @@ SM_MAX_MHZ = 2032.0
 # exact seed of every diagonal (ell FMA per R cells, about 2 FLOP at ell = m/2)
 FLOP_PER_ED_CELL = 8.0
 # dram__bytes_read.sum + dram__bytes_write.sum of the tile launches of one sweep
-# step (one-CTA tiles: 59 MB + 2.10 GB; two-CTA tiles: 46 MB + 0.78 GB), measured
-# with ncu on this kernel version
-SWEEP_TILE_DRAM_BYTES = 2.99e9
+# step (one-CTA tiles of m = 96 .. 256: 44 MB + 1.47 GB; two-CTA-per-SM tiles of
+# m = 64: 9 MB + 0.56 GB; two-CTA cluster tiles of m = 288 .. 512: 47 MB + 0.78 GB),
+# measured with ncu on this kernel version and launch grouping
+SWEEP_TILE_DRAM_BYTES = 2.92e9
 
 
 def workload(m_list=None):
@@ -372,7 +373,7 @@ def run_ours(args):
     traffic = SWEEP_TILE_DRAM_BYTES if ms == synth.sweep_lengths() else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per sweep step's tile launches",
-                "kernel": "batched_tiles_kernel<float,4> (every length of the sweep; one launch per cluster size, "
+                "kernel": "batched_tiles_kernel<float,4> (every length of the sweep; one launch per layout class, "
                           "timed together)",
                 "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (max SM clock), derived",
                 "launches": tile_launches, "avg_launch_ms": tile_ms / max(tile_launches, 1),

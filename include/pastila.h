@@ -399,10 +399,12 @@ pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_m
 /* The tile layout of a length (positions per CTA W, row groups NG, threads NT,
  * lanes per selection group GS) comes from a cost model unless the autotuner
  * has chosen one.  pastila_tune times, for every m of m_list with the ell/k
- * rule, the model's layout and up to max_candidates - 1 rivals (the cheapest
- * of every thread count first, then by modelled cost, all within 1.5x of the
- * model's best), each also with twice the default selection group width
- * where R <= 288, on the first
+ * rule, the model's layout and up to max_candidates - 1 rivals (the model's
+ * best two- and four-CTA cluster layouts and its best layout of at most 256
+ * threads and half an SM's shared memory, so that two CTAs share an SM; then
+ * the cheapest of every thread count, then by modelled cost, these within
+ * 1.5x of the model's best), each also with twice the default selection group
+ * width where R <= 288, on the first
  * min(S, 64) segments of h's series, and keeps the fastest in a process-wide
  * table keyed by (precision, m, ell, k) that every later call uses (handles and
  * engines alike; a captured select_length graph is rebuilt).  Results depend
@@ -414,7 +416,7 @@ typedef struct {
     int32_t m;
     int32_t W, NG, NT;     /* the chosen layout */
     int32_t GS;            /* lanes per k-th selection group */
-    int32_t CS;            /* CTAs per tile: 1, or 2 (a thread-block cluster splitting the rows) */
+    int32_t CS;            /* CTAs per tile: 1, 2 or 4 (a thread-block cluster splitting the rows) */
     int32_t candidates;    /* layouts timed */
     double ms_model;       /* device time of the cost model's layout on the sample */
     double ms_best;        /* device time of the chosen layout */

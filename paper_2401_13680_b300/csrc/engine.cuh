@@ -708,16 +708,20 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
     JobFinal<real>* h_fin = (JobFinal<real>*)(hd + 2 * bi_bytes + kp_bytes);
     double wave_cells = 0.0;
     double wfeat[RM_NF] = {0, 0, 0, 0, 1};
-    // one tile launch per cluster size (a launch has a single cluster shape), each
-    // numbering its own CTAs; chunks ordered by cluster size
-    std::stable_sort(merged.begin(), merged.end(), [](const Chunk& x, const Chunk& y) {
-        return x.job->items[x.item].g.CS < y.job->items[y.item].g.CS;
+    // one tile launch per cluster size (a launch has a single cluster shape) and
+    // apart the layouts that put two CTAs on an SM, each numbering its own CTAs
+    const size_t lim = (size_t)e->smem_optin;
+    auto cls = [lim](const TileGeom& g) { return 2 * g.CS + (pair_layout(g, lim) ? 1 : 0); };
+    std::stable_sort(merged.begin(), merged.end(), [&](const Chunk& x, const Chunk& y) {
+        return cls(x.job->items[x.item].g) < cls(y.job->items[y.item].g);
     });
     std::vector<TileGroup> groups;
+    int gcls = -1;
     for (size_t c = 0; c < merged.size(); ++c) {
         const Chunk& ch = merged[c];
         const EItem& it = ch.job->items[ch.item];
-        if (groups.empty() || groups.back().cs != it.g.CS) {
+        if (groups.empty() || gcls != cls(it.g)) {
+            gcls = cls(it.g);
             TileGroup tg;
             tg.cs = it.g.CS;
             tg.first = (int)c;
@@ -1080,10 +1084,8 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
     if (cudaMallocHost((void**)&e->results_host, ENGINE_RESULT_SLOT * (size_t)e->max_active) != cudaSuccess)
         return bail(fail(PASTILA_ENOMEM, "engine result slots could not be allocated"));
     for (int q = e->max_active - 1; q >= 0; --q) e->slots_free.push_back(q);
-    CK(cudaFuncSetAttribute(batched_tiles_kernel<float, V_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            e->smem_optin));
-    CK(cudaFuncSetAttribute(batched_tiles_kernel<double, V_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            e->smem_optin));
+    CK(tile_attrs(batched_tiles_kernel<float, V_F32>, e->smem_optin));
+    CK(tile_attrs(batched_tiles_kernel<double, V_F64>, e->smem_optin));
     e->t0 = std::chrono::steady_clock::now();
     pastila_engine* ep = e.release();
     ep->thr = std::thread(scheduler, ep);

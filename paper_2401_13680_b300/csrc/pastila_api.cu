@@ -75,6 +75,16 @@ cudaError_t launch_tiles(void (*kernel)(P...), dim3 grid, unsigned block, size_t
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Q>(args)...);
 }
 
+// Shared-memory attributes of a tile kernel: up to `smem` dynamic bytes per CTA,
+// and the largest shared-memory carveout, so that two CTAs of a layout that
+// needs at most half of it share an SM.
+template <typename... P>
+cudaError_t tile_attrs(void (*kernel)(P...), int smem) {
+    cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r != cudaSuccess) return r;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
 struct Stats {
     bool stale = false;
     int64_t C = 0;
@@ -252,10 +262,21 @@ pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, M
 // halo columns are recomputed by the next tile), the selection on its W
 // positions; NG row groups add NG seed rows of ell products per column, and
 // fewer than 12 resident warps leave latency exposed.
+// Two CTAs of a layout share an SM when each takes at most half of its shared
+// memory (the SM has the per-CTA limit plus the 1 KB reserved per CTA; 2 KB
+// more are kept for static shared memory) and at most 256 threads (the
+// kernels compile to at most 128 registers).  Such layouts are launched apart
+// from the others: a launch takes the largest block and shared memory of its
+// items.
+inline bool pair_layout(const TileGeom& g, size_t limit) {
+    return g.NT <= 256 && g.bytes <= (limit + 2048) / 2 - 3072;
+}
+
 struct TileCand {
     double cost;  // modelled cost per ED cell
     int W, ngw;   // tile width and the row groups asked of tile_geom
     TileGeom g;
+    bool pair;    // two CTAs of this layout fit on one SM
 };
 
 constexpr int CLUSTER_MIN_R = 65;    // two-CTA cluster tiles are considered from R = 65 up
@@ -279,9 +300,10 @@ void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out,
                 // ell products) over the W positions, the selection, threads
                 const double rows = 17.0 + 2.0 * cs * t.NG * (double)q.ell / q.R;
                 const double sel = 23.0;
-                const double eff = t.NT >= 384 ? 1.0 : t.NT / 384.0;
+                const bool pair = pair_layout(t, limit);
+                const double eff = pair ? std::min(1.0, 2.0 * t.NT / 512.0) : (t.NT >= 384 ? 1.0 : t.NT / 384.0);
                 const double cl = cs > 1 ? 1.1 : 1.0;  // partner writes and cluster barriers
-                out->push_back(TileCand{cl * ((double)Wb / W * rows + sel) / eff, W, ngw, t});
+                out->push_back(TileCand{cl * ((double)Wb / W * rows + sel) / eff, W, ngw, t, pair});
             }
         }
     }
@@ -389,8 +411,7 @@ pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st,
     TileGeom g;
     TRY(choose_tile<real, V>(h, q, &g));
     const ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, D, dmax);
-    CK(cudaFuncSetAttribute(profile_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            h->smem_optin));
+    CK(tile_attrs(profile_tiles_kernel<real, V>, h->smem_optin));
     init_dmax_kernel<<<1, 1, 0, h->stream>>>(dmax);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->timing) {
@@ -430,21 +451,31 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     std::stable_sort(c.begin(), c.end(), [](const TileCand& x, const TileCand& y) { return x.cost < y.cost; });
     std::vector<TileCand> pick;
     std::vector<int> nts;
-    for (const TileCand& t : c) {  // cheapest layout of every thread count and cluster size
-        if ((int)pick.size() >= max_cand || t.cost > 1.5 * c[0].cost) break;
-        const int key = t.g.NT * 4 + t.g.CS;
-        if (std::find(nts.begin(), nts.end(), key) == nts.end()) {
-            nts.push_back(key);
-            pick.push_back(t);
-        }
-    }
-    for (int cs : {2, 4}) {  // the model's best of every cluster size is always timed
+    auto key = [](const TileCand& t) { return t.g.NT * 4 + t.g.CS; };
+    pick.push_back(c[0]);  // the model's choice, timed first
+    nts.push_back(key(c[0]));
+    // the model's best of every cluster size and of the layouts that put two
+    // CTAs on an SM are always timed
+    auto best_of = [&](auto pred) {
         for (const TileCand& t : c) {
-            if (t.g.CS != cs) continue;
+            if (!pred(t)) continue;
             bool have = false;
-            for (const TileCand& u : pick) have |= u.g.CS == cs;
-            if (!have && (int)pick.size() < max_cand) pick.push_back(t);
-            break;
+            for (const TileCand& u : pick) have |= pred(u);
+            if (!have && (int)pick.size() < max_cand) {
+                pick.push_back(t);
+                nts.push_back(key(t));
+            }
+            return;
+        }
+    };
+    best_of([](const TileCand& t) { return t.g.CS == 2; });
+    best_of([](const TileCand& t) { return t.g.CS == 4; });
+    best_of([](const TileCand& t) { return t.pair; });
+    for (const TileCand& t : c) {  // the cheapest layout of every thread count and cluster size
+        if ((int)pick.size() >= max_cand || t.cost > 1.5 * c[0].cost) break;
+        if (std::find(nts.begin(), nts.end(), key(t)) == nts.end()) {
+            nts.push_back(key(t));
+            pick.push_back(t);
         }
     }
     for (const TileCand& t : c) {  // then by modelled cost
@@ -459,8 +490,7 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     void *D, *dk;
     TRY(scratch(h, "tune_D", sizeof(real) * (size_t)S_sub * (size_t)q.P, &D));
     TRY(scratch(h, "tune_dmax", 8, &dk));
-    CK(cudaFuncSetAttribute(profile_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            h->smem_optin));
+    CK(tile_attrs(profile_tiles_kernel<real, V>, h->smem_optin));
     cudaEvent_t e0, e1;
     TRY(get_event(h, &e0));
     TRY(get_event(h, &e1));
@@ -628,10 +658,8 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     TRY(scratch(h, "sn_ofrac", 8 * 64, &ofrac));
     TRY(scratch(h, "sn_oarea", 8 * 64, &oarea));
     if (labels_out) TRY(scratch(h, "labels", 4 * (size_t)P, &lab));
-    CK(cudaFuncSetAttribute(stream_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            h->smem_optin));
-    CK(cudaFuncSetAttribute(rows_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            h->smem_optin));
+    CK(tile_attrs(stream_tiles_kernel<real, V>, h->smem_optin));
+    CK(tile_attrs(rows_tiles_kernel<real, V>, h->smem_optin));
     init_dmax_kernel<<<1, 1, 0, h->stream>>>((unsigned long long*)dk);
     h->launches += 1;
     ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, nullptr, (unsigned long long*)dk);
@@ -883,17 +911,20 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
         maxS = q.S > maxS ? q.S : maxS;
         maxP = q.P > maxP ? q.P : maxP;
     }
-    // tile launches: one per cluster size, each numbering its own CTAs (counts are
-    // multiples of the cluster size, so every item starts a cluster)
+    // tile launches: one per cluster size, and apart the layouts that put two
+    // CTAs on an SM; each numbers its own CTAs (counts are multiples of the
+    // cluster size, so every item starts a cluster)
     std::vector<BatchItem<real>>& tiles = *tiles_out;
     tiles.clear();
     sb->groups.clear();
-    for (int cs : {1, 2, 4}) {
+    for (int cls = 0; cls < 6; ++cls) {
+        const int cs = 1 << (cls >> 1);
+        const bool pair = cls & 1;
         TileGroup tg;
         tg.cs = cs;
         tg.first = (int)tiles.size();
         for (int i = 0; i < n; ++i) {
-            if (geo[i].CS != cs) continue;
+            if (geo[i].CS != cs || pair_layout(geo[i], (size_t)h->smem_optin) != pair) continue;
             BatchItem<real> t = items[i];
             t.cta_begin = tg.ctas;
             tg.ctas += t.ctas;
@@ -921,8 +952,7 @@ pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs
     if (phase == 1) {
         // the attribute is process-wide: every caller sets the same device maximum, so
         // concurrent callers (handles, the engine) never lower it under one another
-        CK(cudaFuncSetAttribute(batched_tiles_kernel<real, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                h->smem_optin));
+        CK(tile_attrs(batched_tiles_kernel<real, V>, h->smem_optin));
         for (const TileGroup& tg : sb.groups) {
             CK(launch_tiles(batched_tiles_kernel<real, V>, dim3((unsigned)tg.ctas), tg.block, tg.smem, h->stream,
                             tg.cs, (const BatchItem<real>*)sb.tiles + tg.first, tg.n));
