@@ -172,6 +172,8 @@ struct EStats {
     void* a = nullptr;
     void* df = nullptr;
     void* dg = nullptr;
+    void* muh = nullptr;  // mu as hi + lo pairs
+    void* mul = nullptr;
 };
 
 struct EItem {
@@ -210,6 +212,8 @@ struct EJob {
     size_t res_bytes = 0, max_dbytes = 0;
     void* res = nullptr;
     double* T_dev = nullptr;
+    void* Th = nullptr;  // T as hi + lo pairs (written with every length's statistics)
+    void* Tl = nullptr;
     double* inv = nullptr;
     int32_t* flat = nullptr;
     int32_t* ms_dev = nullptr;
@@ -387,10 +391,10 @@ pastila_status plan_job(pastila_engine* e, EJob& j, pastila_mparams rule) {
     if (K < 2 || K > min_S || K > ENGINE_MAX_K)
         return fail(PASTILA_EINVAL, "K = %d: must satisfy 2 <= K <= min(n / max m, 64) = %d", K, std::min(min_S, 64));
     j.Cmax = 0;
-    size_t b = up256e(8 * (size_t)j.n);
+    size_t b = up256e(8 * (size_t)j.n) + 2 * up256e(rs * (size_t)j.n);
     for (auto& st : j.stats) {
         j.Cmax = std::max(j.Cmax, st.C);
-        b += up256e(8 * (size_t)st.C) + 3 * up256e(rs * (size_t)st.C);
+        b += up256e(8 * (size_t)st.C) + 5 * up256e(rs * (size_t)st.C);
     }
     b += up256e(8 * (size_t)j.Cmax) + up256e(4 * (size_t)j.Cmax);
     b += up256e(8 * (size_t)n_m) * 3;  // meta: ms (padded), P, keep_off
@@ -415,11 +419,15 @@ pastila_status admit_job(pastila_engine* e, EJob& j) {
         return (void*)r;
     };
     j.T_dev = (double*)take(8 * (size_t)j.n);
+    j.Th = take(rs * (size_t)j.n);
+    j.Tl = take(rs * (size_t)j.n);
     for (auto& st : j.stats) {
         st.mu = (double*)take(8 * (size_t)st.C);
         st.a = take(rs * (size_t)st.C);
         st.df = take(rs * (size_t)st.C);
         st.dg = take(rs * (size_t)st.C);
+        st.muh = take(rs * (size_t)st.C);
+        st.mul = take(rs * (size_t)st.C);
     }
     j.inv = (double*)take(8 * (size_t)j.Cmax);
     j.flat = (int32_t*)take(4 * (size_t)j.Cmax);
@@ -473,8 +481,10 @@ BatchItem<real> item_desc(const EJob& j, const EItem& it) {
     BatchItem<real> bi{};
     ProfileArgs<real>& A = bi.A;
     const EStats& st = j.stats[it.stats];
-    A.T = j.T_dev;
-    A.mu = st.mu;
+    A.Th = (const real*)j.Th;
+    A.Tl = (const real*)j.Tl;
+    A.muh = (const real*)st.muh;
+    A.mul = (const real*)st.mul;
     A.a = (const real*)st.a;
     A.df = (const real*)st.df;
     A.dg = (const real*)st.dg;
@@ -820,8 +830,9 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
             const int64_t nthr = (st.C + STATS_RUN - 1) / STATS_RUN;
             stats_mu_a_kernel<<<(unsigned)((nthr + 127) / 128), 128, 0, s>>>(j.T_dev, st.C, st.ell, st.mu, j.inv,
                                                                              j.flat);
-            stats_terms_kernel<real><<<(unsigned)((st.C + 255) / 256), 256, 0, s>>>(
-                j.T_dev, st.C, st.ell, st.mu, j.inv, (real*)st.a, (real*)st.df, (real*)st.dg);
+            stats_terms_kernel<real><<<(unsigned)((j.n + 255) / 256), 256, 0, s>>>(
+                j.T_dev, j.n, st.C, st.ell, st.mu, j.inv, (real*)st.a, (real*)st.df, (real*)st.dg,
+                (real*)st.muh, (real*)st.mul, (real*)j.Th, (real*)j.Tl);
             launches += 2;
         }
         engine_init_keys_kernel<<<1, 64, 0, s>>>(j.items[0].dmax, (int)j.items.size());

@@ -92,6 +92,8 @@ struct Stats {
     void* a = nullptr;
     void* df = nullptr;
     void* dg = nullptr;
+    void* muh = nullptr;  // mu as hi + lo pairs of the handle's precision
+    void* mul = nullptr;
 };
 
 struct Buf {
@@ -108,6 +110,8 @@ struct pastila_series {
     bool own_stream = false;
     int64_t n = 0;
     double* T = nullptr;
+    void* Th = nullptr;  // T as hi + lo pairs of the handle's precision, rewritten with every statistic
+    void* Tl = nullptr;
     size_t budget = 0;
     size_t held = 0;
     int smem_optin = 0;
@@ -194,17 +198,25 @@ pastila_status ensure_stats(pastila_series* h, int ell, Stats** out) {
     Stats st;
     st.C = h->n - ell + 1;
     const size_t rs = real_size(h);
-    void *mu, *inv, *flat, *a, *df, *dg;
+    void *mu, *inv, *flat, *a, *df, *dg, *muh, *mul;
     if (it != h->stats.end()) {  // stale: recompute into the same buffers
         mu = it->second.mu;
         a = it->second.a;
         df = it->second.df;
         dg = it->second.dg;
+        muh = it->second.muh;
+        mul = it->second.mul;
     } else {
         TRY(dev_alloc(h, &mu, 8 * st.C));
         TRY(dev_alloc(h, &a, rs * st.C));
         TRY(dev_alloc(h, &df, rs * st.C));
         TRY(dev_alloc(h, &dg, rs * st.C));
+        TRY(dev_alloc(h, &muh, rs * st.C));
+        TRY(dev_alloc(h, &mul, rs * st.C));
+    }
+    if (!h->Th) {
+        TRY(dev_alloc(h, &h->Th, rs * h->n));
+        TRY(dev_alloc(h, &h->Tl, rs * h->n));
     }
     TRY(scratch(h, "stats_inv", 8 * st.C, &inv));
     TRY(scratch(h, "stats_flat", 4 * st.C, &flat));
@@ -212,19 +224,23 @@ pastila_status ensure_stats(pastila_series* h, int ell, Stats** out) {
     stats_mu_a_kernel<<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
         h->T, st.C, ell, (double*)mu, (double*)inv, (int32_t*)flat);
     CK(cudaGetLastError());
-    const unsigned nb = (unsigned)((st.C + 255) / 256);
+    const unsigned nb = (unsigned)((h->n + 255) / 256);
     if (h->prec == PASTILA_FP64)
-        stats_terms_kernel<double><<<nb, 256, 0, h->stream>>>(h->T, st.C, ell, (double*)mu, (double*)inv,
-                                                              (double*)a, (double*)df, (double*)dg);
+        stats_terms_kernel<double><<<nb, 256, 0, h->stream>>>(h->T, h->n, st.C, ell, (double*)mu, (double*)inv,
+                                                              (double*)a, (double*)df, (double*)dg, (double*)muh,
+                                                              (double*)mul, (double*)h->Th, (double*)h->Tl);
     else
-        stats_terms_kernel<float><<<nb, 256, 0, h->stream>>>(h->T, st.C, ell, (double*)mu, (double*)inv,
-                                                             (float*)a, (float*)df, (float*)dg);
+        stats_terms_kernel<float><<<nb, 256, 0, h->stream>>>(h->T, h->n, st.C, ell, (double*)mu, (double*)inv,
+                                                             (float*)a, (float*)df, (float*)dg, (float*)muh,
+                                                             (float*)mul, (float*)h->Th, (float*)h->Tl);
     CK(cudaGetLastError());
     h->launches += 2;
     st.mu = (double*)mu;
     st.a = a;
     st.df = df;
     st.dg = dg;
+    st.muh = muh;
+    st.mul = mul;
     h->stats[ell] = st;
     *out = &h->stats[ell];
     return PASTILA_OK;
@@ -385,8 +401,10 @@ template <typename real, int V>
 ProfileArgs<real> profile_args(const pastila_series* h, const MParams& q, const Stats* st, const TileGeom& g,
                                real* D, unsigned long long* dmax) {
     ProfileArgs<real> A{};  // every field zero (M, part: the plain, non-streaming form)
-    A.T = h->T;
-    A.mu = st->mu;
+    A.Th = (const real*)h->Th;
+    A.Tl = (const real*)h->Tl;
+    A.muh = (const real*)st->muh;
+    A.mul = (const real*)st->mul;
     A.a = (const real*)st->a;
     A.df = (const real*)st->df;
     A.dg = (const real*)st->dg;
@@ -1306,9 +1324,13 @@ void pastila_destroy(pastila_series* h) {
         cudaFree(kv.second.a);
         cudaFree(kv.second.df);
         cudaFree(kv.second.dg);
+        cudaFree(kv.second.muh);
+        cudaFree(kv.second.mul);
     }
     for (auto& kv : h->bufs) cudaFree(kv.second.p);
     cudaFree(h->T);
+    cudaFree(h->Th);
+    cudaFree(h->Tl);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }

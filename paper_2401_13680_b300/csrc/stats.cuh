@@ -11,6 +11,12 @@
 // and the Pearson correlation is rho(i, j) = cov(i, j) * a[i] * a[j]; the
 // z-normalised distance is sqrt(2 ell (1 - rho)) (Section 4.1: the dot-product
 // technique of the matrix-profile work the paper cites as [7]).
+//
+// The tile kernel works in the precision `real` only (FP64 arithmetic is slow
+// on this GPU), so the FP64 series and means are also kept as unevaluated
+// pairs hi + lo of `real` values (hi = the rounded value, lo = the rounded
+// remainder): Th, Tl for T (n values) and muh, mul for mu (C values).  In the
+// FP64 path hi is the value itself and lo is 0.
 #pragma once
 #include <cstdint>
 
@@ -61,12 +67,24 @@ __global__ void stats_mu_a_kernel(const double* __restrict__ T, int64_t C, int e
 }
 
 template <typename real>
-__global__ void stats_terms_kernel(const double* __restrict__ T, int64_t C, int ell,
+__device__ __forceinline__ void split2(double x, real* hi, real* lo) {
+    const real h = (real)x;
+    *hi = h;
+    *lo = (real)(x - (double)h);
+}
+
+// Grid over the n values of T: j < n writes the pair of T[j], j < C the
+// statistics of window j.
+template <typename real>
+__global__ void stats_terms_kernel(const double* __restrict__ T, int64_t n, int64_t C, int ell,
                                    const double* __restrict__ mu,
                                    const double* __restrict__ inv_norm, real* __restrict__ a,
-                                   real* __restrict__ df, real* __restrict__ dg) {
+                                   real* __restrict__ df, real* __restrict__ dg, real* __restrict__ muh,
+                                   real* __restrict__ mul, real* __restrict__ Th, real* __restrict__ Tl) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) split2(T[j], Th + j, Tl + j);
     if (j >= C) return;
+    split2(mu[j], muh + j, mul + j);
     a[j] = (real)inv_norm[j];
     if (j == 0) {
         df[j] = (real)0;

@@ -57,8 +57,10 @@ template <> struct RealLimits<double> {
 
 template <typename real>
 struct ProfileArgs {
-    const double* T;     // n values (FP64)
-    const double* mu;    // C window means (FP64)
+    const real* Th;      // n values of the series as hi + lo pairs (FP64: hi = value, lo = 0)
+    const real* Tl;
+    const real* muh;     // C window means as hi + lo pairs
+    const real* mul;
     const real* a;       // C inverse norms (0 = flat window)
     const real* df;      // C
     const real* dg;      // C
@@ -603,44 +605,97 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     real* rdf = (real*)(sm + G.off_row);
     real* rdg = rdf + R;
     real* ra = rdg + R;
-    real* rmu = ra + R;   // hi part of mu_i - refs
-    real* rmul = rmu + R; // lo part
+    real* rmu = ra + R;   // mu_i as hi + lo
+    real* rmul = rmu + R;
     real* lseed = (real*)(sm + G.off_left);
     real* top = (real*)(sm + G.off_top);  // [group][NTc * V] seeds, later the groups' column maxima
-    real* Tc = (real*)(sm + G.off_Tc);    // T - refc as hi + lo pairs: exact to about
-    real* Tcl = (real*)(sm + G.off_Tcl);  // twice the working precision
-    real* Ts = (real*)(sm + G.off_Ts);
+    real* Tc = (real*)(sm + G.off_Tc);    // the window's T as hi + lo pairs: exact to
+    real* Tcl = (real*)(sm + G.off_Tcl);  // about twice the working precision
+    real* Ts = (real*)(sm + G.off_Ts);    // the segment's T, the same way
     real* Tsl = (real*)(sm + G.off_Tsl);
     real* q = (real*)(sm + G.off_q);      // [group][ell + 1] centred head of the group's first row
 
     // ---------------------------------------------------------------- stage
-    const double refc = A.mu[p0];
-    const double refs = A.mu[i0];
+    // One index space over everything staged: the window's and the segment's
+    // series values (hi + lo pairs), the five row statistics and the groups'
+    // centred heads.  In FP32 each thread issues the global loads of SG
+    // elements before any of their shared stores, so a whole chunk's loads are
+    // in flight together (one CTA per SM hides no latency for them).  No FP64
+    // arithmetic: the series and the means arrive as pairs.
     const int nTc = Wb + ell - 1;
-    for (int y = tid; y < NTc * V + ell + 64; y += BD) {
-        const double d = y < nTc ? A.T[p0 + y] - refc : 0.0;
-        const real h = (real)d;
-        Tc[y] = h;
-        Tcl[y] = (real)(d - (double)h);
-    }
-    for (int u = tid; u < m; u += BD) {
-        const double d = A.T[i0 + u] - refs;
-        const real h = (real)d;
-        Ts[u] = h;
-        Tsl[u] = (real)(d - (double)h);
-    }
-    for (int r = tid; r < R; r += BD) {
-        rdf[r] = A.df[i0 + r];
-        rdg[r] = A.dg[i0 + r];
-        ra[r] = A.a[i0 + r];
-        const double d = A.mu[i0 + r] - refs;
-        rmu[r] = (real)d;
-        rmul[r] = (real)(d - (double)rmu[r]);
-    }
-    for (int e = tid; e < NG * ell; e += BD) {
-        const int gg = e / ell, u = e - gg * ell;
-        const int64_t ig = i0 + rbase + (int64_t)gg * Rg;
-        q[gg * (ell + 1) + u] = (real)(A.T[ig + u] - A.mu[ig]);
+    const real c0h = A.muh[p0], c0l = A.mul[p0];  // mean of column 0, for the left seeds
+    if constexpr (sizeof(real) == 4) {
+        constexpr int SG = 4;
+        const int n1 = NTc * V + ell + 64, n2 = n1 + m, n3 = n2 + 5 * R, n4 = n3 + NG * ell;
+        for (int e0 = tid; e0 < n4; e0 += SG * BD) {
+            real x[SG], y[SG], z[SG], w[SG];
+#pragma unroll
+            for (int u = 0; u < SG; ++u) {
+                const int e = e0 + u * BD;
+                x[u] = y[u] = z[u] = w[u] = (real)0;
+                if (e < n1) {
+                    if (e < nTc) {
+                        x[u] = A.Th[p0 + e];
+                        y[u] = A.Tl[p0 + e];
+                    }
+                } else if (e < n2) {
+                    x[u] = A.Th[i0 + (e - n1)];
+                    y[u] = A.Tl[i0 + (e - n1)];
+                } else if (e < n3) {
+                    const int kind = (e - n2) / R;
+                    const int64_t i = i0 + ((e - n2) - kind * R);
+                    const real* src = kind == 0 ? A.df : kind == 1 ? A.dg : kind == 2 ? A.a : kind == 3 ? A.muh : A.mul;
+                    x[u] = src[i];
+                } else if (e < n4) {
+                    const int gg = (e - n3) / ell, uu = (e - n3) - gg * ell;
+                    const int64_t ig = i0 + rbase + (int64_t)gg * Rg;
+                    x[u] = A.Th[ig + uu];
+                    y[u] = A.Tl[ig + uu];
+                    z[u] = A.muh[ig];
+                    w[u] = A.mul[ig];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SG; ++u) {
+                const int e = e0 + u * BD;
+                if (e < n1) {
+                    Tc[e] = x[u];
+                    Tcl[e] = y[u];
+                } else if (e < n2) {
+                    Ts[e - n1] = x[u];
+                    Tsl[e - n1] = y[u];
+                } else if (e < n3) {
+                    const int kind = (e - n2) / R, r = (e - n2) - kind * R;
+                    real* dst = kind == 0 ? rdf : kind == 1 ? rdg : kind == 2 ? ra : kind == 3 ? rmu : rmul;
+                    dst[r] = x[u];
+                } else if (e < n4) {
+                    const int gg = (e - n3) / ell, uu = (e - n3) - gg * ell;
+                    q[gg * (ell + 1) + uu] = (x[u] - z[u]) + (y[u] - w[u]);
+                }
+            }
+        }
+    } else {  // FP64: plain loops (the merged form costs the FP64 kernels a register spill)
+        for (int y = tid; y < NTc * V + ell + 64; y += BD) {
+            const bool in = y < nTc;
+            Tc[y] = in ? A.Th[p0 + y] : (real)0;
+            Tcl[y] = in ? A.Tl[p0 + y] : (real)0;
+        }
+        for (int u = tid; u < m; u += BD) {
+            Ts[u] = A.Th[i0 + u];
+            Tsl[u] = A.Tl[i0 + u];
+        }
+        for (int r = tid; r < R; r += BD) {
+            rdf[r] = A.df[i0 + r];
+            rdg[r] = A.dg[i0 + r];
+            ra[r] = A.a[i0 + r];
+            rmu[r] = A.muh[i0 + r];
+            rmul[r] = A.mul[i0 + r];
+        }
+        for (int e = tid; e < NG * ell; e += BD) {
+            const int gg = e / ell, u = e - gg * ell;
+            const int64_t ig = i0 + rbase + (int64_t)gg * Rg;
+            q[gg * (ell + 1) + u] = (A.Th[ig + u] - A.muh[ig]) + (A.Tl[ig + u] - A.mul[ig]);
+        }
     }
     __syncthreads();
     if ((tid >> 5) < NG) {  // warp gg: sum of group gg's rounded q, in FP64
@@ -652,10 +707,27 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         if (lane == 0) q[gg * (ell + 1) + ell] = (real)acc;
     }
 
+    // this thread's column statistics for the rows phase, loaded now so that
+    // their latency passes under the seeds (FP32 path; the FP64 path has no
+    // registers to spare and loads them after the seeds)
+    const int xb = t * V;
+    real cdf[V], cdg[V], ca[V];
+    auto load_cols = [&]() {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int x = xb + v;
+            const bool in = x < Wb;
+            cdf[v] = in ? A.df[p0 + x] : (real)0;
+            cdg[v] = in ? A.dg[p0 + x] : (real)0;
+            ca[v] = in ? A.a[p0 + x] : (real)0;
+        }
+    };
+    constexpr bool early_cols = sizeof(real) == 4;
+    if (early_cols) load_cols();
+
     // ---------------------------------------------------------------- seeds
-    // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0); the row
-    // values are centred term by term from their hi + lo parts, and mu of
-    // column 0 is the reference of Tc
+    // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0), both
+    // factors centred term by term from their hi + lo parts
     {
         // SPLIT consecutive lanes per row, lane sp summing the terms sp, sp + SPLIT,
         // ... (consecutive lanes, consecutive words), then a fixed-order shuffle sum:
@@ -670,7 +742,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             real acc = 0;
             if (r < rend) {
                 const real mh = rmu[r], ml = rmul[r];
-                for (int u = sp; u < ell; u += SPLIT) acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * (Tc[u] + Tcl[u]);
+                for (int u = sp; u < ell; u += SPLIT)
+                    acc += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * ((Tc[u] - c0h) + (Tcl[u] - c0l));
             }
             for (int o = SPLIT >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SPLIT);
             if (r < rend && sp == 0) lseed[r] = acc;
@@ -680,9 +753,9 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // first row of every group: cov(r0, x) = sum_t q[t] * (T[x+t] - c) - (mu_x - c) * sum_t q[t]
     // for any constant c (the centred q sums to 0 up to rounding, and its rounded
     // sum is taken exactly).  c is the mean of each block's first column: the
-    // series values of a block are centred once, from their hi + lo parts, as
-    // they enter a sliding register window, so the products never carry the
-    // level of the series, only its local deviations.  Lane-contiguous blocks of
+    // series values of a block are centred once, from their hi + lo parts and
+    // those of c, as they enter a sliding register window, so the products
+    // never carry the level of the series, only its local deviations.  Lane-contiguous blocks of
     // 9 columns (odd stride: conflict-free sliding loads).
     {
         constexpr int J = 9;
@@ -691,8 +764,18 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             const int gg = b / nblk;
             const int x0 = (b - gg * nblk) * J;
             const real* qg = q + gg * (ell + 1);
-            const double cb = x0 < Wb ? A.mu[p0 + x0] - refc : 0.0;
-            const real cbh = (real)cb, cbl = (real)(cb - (double)cbh);
+            // every mean of the block loaded together (FP32 path; the FP64 path has
+            // no registers to spare and loads them where they are used)
+            constexpr bool early = sizeof(real) == 4;
+            real mxh[J], mxl[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const bool in = early && x0 + j < Wb;
+                mxh[j] = in ? A.muh[p0 + x0 + j] : (real)0;
+                mxl[j] = in ? A.mul[p0 + x0 + j] : (real)0;
+            }
+            const real cbh = x0 < Wb ? (early ? mxh[0] : A.muh[p0 + x0]) : (real)0;
+            const real cbl = x0 < Wb ? (early ? mxl[0] : A.mul[p0 + x0]) : (real)0;
             real acc[J], win[J];
 #pragma unroll
             for (int j = 0; j < J; ++j) {
@@ -724,7 +807,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             for (int j = 0; j < J; ++j) {
                 const int x = x0 + j;
                 if (x < Wb) {
-                    const real dm = (real)(A.mu[p0 + x] - refc - cb);
+                    const real dm = ((early ? mxh[j] : A.muh[p0 + x]) - cbh) + ((early ? mxl[j] : A.mul[p0 + x]) - cbl);
                     topg[x] = acc[j] - dm * sq;
                 } else if (x < NTc * V) {
                     topg[x] = 0;
@@ -735,17 +818,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     __syncthreads();
 
     // ---------------------------------------------------------------- rows
-    const int xb = t * V;
+    if (!early_cols) load_cols();
     const real NEG = RealLimits<real>::lowest();
-    real hi[V], lo[V], cmx[V], cdf[V], cdg[V], ca[V];
+    real hi[V], lo[V], cmx[V];
     const bool partial_cols = xb + V > Wb;  // only the last column thread of a tile
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int x = xb + v;
-        const bool in = x < Wb;
-        cdf[v] = in ? A.df[p0 + x] : (real)0;
-        cdg[v] = in ? A.dg[p0 + x] : (real)0;
-        ca[v] = in ? A.a[p0 + x] : (real)0;
         hi[v] = worker ? top[(size_t)g * NTc * V + x] : (real)0;
         lo[v] = 0;
         cmx[v] = NEG;
