@@ -28,6 +28,15 @@
  *    device.  Calls on one handle are not thread-safe; separate handles are.
  *  - Results are deterministic: the same inputs give bit-identical outputs on
  *    the same device, alone or batched with other work.
+ *  - Device-side waits are bounded.  The tile kernels wait once per tile, for
+ *    the bulk copies that stage it; if that wait runs out (about a second) the
+ *    tile raises a host-visible flag and still completes, and the next call
+ *    on the handle that synchronises its stream (profiles, snippets,
+ *    select_length, snippets_streamed, tune) returns PASTILA_ETIMEOUT with
+ *    its outputs unspecified; an engine fails its unfinished jobs with
+ *    PASTILA_ETIMEOUT and stops.  The device context stays usable.
+ *    (PASTILA_TEST_STAGE_WAIT=timeout in the environment when a handle or an
+ *    engine is created makes every such wait run out, for tests.)
  */
 #ifndef PASTILA_H_
 #define PASTILA_H_

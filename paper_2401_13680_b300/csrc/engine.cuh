@@ -274,6 +274,10 @@ struct pastila_engine {
     double age_weight = 0.0;
     int policy = PASTILA_POLICY_SHARE;
     int fail_at = 0;
+    int* err = nullptr;  // host-mapped flag the tile kernels set when a bounded wait runs out
+    long long spin_limit = 1ll << 31;
+    int test_timeout = 0;
+    pastila_status broken_status = PASTILA_ECUDA;
     int64_t alloc_count = 0;
     int smem_optin = 0;
     cudaStream_t cs = nullptr, xs = nullptr;
@@ -391,10 +395,11 @@ pastila_status plan_job(pastila_engine* e, EJob& j, pastila_mparams rule) {
     if (K < 2 || K > min_S || K > ENGINE_MAX_K)
         return fail(PASTILA_EINVAL, "K = %d: must satisfy 2 <= K <= min(n / max m, 64) = %d", K, std::min(min_S, 64));
     j.Cmax = 0;
-    size_t b = up256e(8 * (size_t)j.n) + 2 * up256e(rs * (size_t)j.n);
+    // the tile kernels' bulk copies may read up to 16 bytes past an array's end
+    size_t b = up256e(8 * (size_t)j.n) + 2 * up256e(rs * (size_t)(j.n + ARRAY_PAD));
     for (auto& st : j.stats) {
         j.Cmax = std::max(j.Cmax, st.C);
-        b += up256e(8 * (size_t)st.C) + 5 * up256e(rs * (size_t)st.C);
+        b += up256e(8 * (size_t)st.C) + 5 * up256e(rs * (size_t)(st.C + ARRAY_PAD));
     }
     b += up256e(8 * (size_t)j.Cmax) + up256e(4 * (size_t)j.Cmax);
     b += up256e(8 * (size_t)n_m) * 3;  // meta: ms (padded), P, keep_off
@@ -419,15 +424,15 @@ pastila_status admit_job(pastila_engine* e, EJob& j) {
         return (void*)r;
     };
     j.T_dev = (double*)take(8 * (size_t)j.n);
-    j.Th = take(rs * (size_t)j.n);
-    j.Tl = take(rs * (size_t)j.n);
+    j.Th = take(rs * (size_t)(j.n + ARRAY_PAD));
+    j.Tl = take(rs * (size_t)(j.n + ARRAY_PAD));
     for (auto& st : j.stats) {
         st.mu = (double*)take(8 * (size_t)st.C);
-        st.a = take(rs * (size_t)st.C);
-        st.df = take(rs * (size_t)st.C);
-        st.dg = take(rs * (size_t)st.C);
-        st.muh = take(rs * (size_t)st.C);
-        st.mul = take(rs * (size_t)st.C);
+        st.a = take(rs * (size_t)(st.C + ARRAY_PAD));
+        st.df = take(rs * (size_t)(st.C + ARRAY_PAD));
+        st.dg = take(rs * (size_t)(st.C + ARRAY_PAD));
+        st.muh = take(rs * (size_t)(st.C + ARRAY_PAD));
+        st.mul = take(rs * (size_t)(st.C + ARRAY_PAD));
     }
     j.inv = (double*)take(8 * (size_t)j.Cmax);
     j.flat = (int32_t*)take(4 * (size_t)j.Cmax);
@@ -477,7 +482,7 @@ pastila_status admit_job(pastila_engine* e, EJob& j) {
 }
 
 template <typename real>
-BatchItem<real> item_desc(const EJob& j, const EItem& it) {
+BatchItem<real> item_desc(const pastila_engine* e, const EJob& j, const EItem& it) {
     BatchItem<real> bi{};
     ProfileArgs<real>& A = bi.A;
     const EStats& st = j.stats[it.stats];
@@ -500,6 +505,9 @@ BatchItem<real> item_desc(const EJob& j, const EItem& it) {
     A.ntiles = it.ntiles;
     A.D = (real*)it.D;
     A.dmax_key = it.dmax;
+    A.err = e->err;
+    A.spin_limit = e->spin_limit;
+    A.test_timeout = e->test_timeout;
     bi.G = it.g;
     bi.M = (real*)it.M;
     bi.area = it.area;
@@ -738,7 +746,7 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
             groups.push_back(tg);
         }
         TileGroup& tg = groups.back();
-        h_tiles[c] = item_desc<real>(*ch.job, it);
+        h_tiles[c] = item_desc<real>(e, *ch.job, it);
         h_tiles[c].cta_begin = tg.ctas;
         h_tiles[c].s_begin = ch.s0;
         h_tiles[c].ctas = (long long)ch.segs * it.ntiles * it.g.CS;
@@ -756,7 +764,7 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
     for (size_t g = 0; g < greedy.size(); ++g) {
         EJob& j = *greedy[g].first;
         const EItem& it = j.items[greedy[g].second];
-        h_greedy[g] = item_desc<real>(j, it);
+        h_greedy[g] = item_desc<real>(e, j, it);
         h_keep[g] = (real*)it.keep;
         Kmax = std::max(Kmax, j.K);
         gmaxS = std::max<int64_t>(gmaxS, it.q.S);
@@ -933,6 +941,11 @@ void harvest(pastila_engine* e) {
                 e->model_err_n++;
             }
         }
+        if (*(volatile int*)e->err) {  // a tile of this wave (or an earlier one) gave up waiting
+            e->broken_status = PASTILA_ETIMEOUT;
+            engine_break(e, "a tile's staging copies did not complete within the wait limit");
+            return;
+        }
         for (int64_t id : w.finals) {
             EJob& j = *e->jobs[id];
             read_results(e, j);
@@ -969,7 +982,7 @@ void scheduler(pastila_engine* e) {
     while (true) {
         harvest(e);
         if (e->broken) {
-            end_all(e, PASTILA_JOB_FAILED, PASTILA_ECUDA, e->broken_msg);
+            end_all(e, PASTILA_JOB_FAILED, e->broken_status, e->broken_msg);
             if (e->stop) break;
             e->cv_sched.wait(lk);
             continue;
@@ -1016,6 +1029,7 @@ void engine_release_resources(pastila_engine* e) {
     for (char* p : e->desc_dev)
         if (p) cudaFree(p);
     if (e->results_host) cudaFreeHost(e->results_host);
+    if (e->err) cudaFreeHost(e->err);
     for (cudaEvent_t ev : e->ev_free) cudaEventDestroy(ev);
     if (e->pool) cudaMemPoolDestroy(e->pool);
     if (e->cs) cudaStreamDestroy(e->cs);
@@ -1094,6 +1108,10 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
     }
     if (cudaMallocHost((void**)&e->results_host, ENGINE_RESULT_SLOT * (size_t)e->max_active) != cudaSuccess)
         return bail(fail(PASTILA_ENOMEM, "engine result slots could not be allocated"));
+    if (cudaHostAlloc((void**)&e->err, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+        return bail(fail(PASTILA_ENOMEM, "the engine's error flag could not be allocated"));
+    *e->err = 0;
+    wait_knobs(&e->spin_limit, &e->test_timeout);
     for (int q = e->max_active - 1; q >= 0; --q) e->slots_free.push_back(q);
     CK(tile_attrs(batched_tiles_kernel<float, V_F32>, e->smem_optin));
     CK(tile_attrs(batched_tiles_kernel<double, V_F64>, e->smem_optin));

@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
@@ -54,6 +55,18 @@ pastila_status fail(pastila_status st, const char* fmt, ...) {
 constexpr int V_F32 = 4;
 constexpr int V_F64 = 4;
 constexpr int MAX_NT = 512;
+constexpr int64_t ARRAY_PAD = 16;  // elements past the end of every array a tile stages
+
+// The bounded waits of the tile kernels: about a second of SM cycles, or, with
+// PASTILA_TEST_STAGE_WAIT=timeout in the environment when a handle or an
+// engine is created, an added wait on a phase that nothing completes, with a
+// limit of about half a millisecond (the test that makes the wait run out).
+void wait_knobs(long long* spin_limit, int* test_timeout) {
+    const char* t = getenv("PASTILA_TEST_STAGE_WAIT");
+    const bool test = t && !strcmp(t, "timeout");
+    *test_timeout = test ? 1 : 0;
+    *spin_limit = test ? (1ll << 20) : (1ll << 31);
+}
 
 // Launch of a tile kernel: plain for one-CTA tiles, with clusters of cs CTAs
 // (along x) otherwise.
@@ -112,6 +125,9 @@ struct pastila_series {
     double* T = nullptr;
     void* Th = nullptr;  // T as hi + lo pairs of the handle's precision, rewritten with every statistic
     void* Tl = nullptr;
+    int* err = nullptr;  // host-mapped flag the tile kernels set when a bounded wait runs out
+    long long spin_limit = 1ll << 31;  // SM cycles (about a second)
+    int test_timeout = 0;
     size_t budget = 0;
     size_t held = 0;
     int smem_optin = 0;
@@ -185,6 +201,15 @@ pastila_status set_device(const pastila_series* h) {
     return PASTILA_OK;
 }
 
+// After the handle's stream is synchronised: a tile whose bounded wait ran out
+// leaves results that must not be used.
+pastila_status stage_check(pastila_series* h) {
+    if (!*(volatile int*)h->err) return PASTILA_OK;
+    *(volatile int*)h->err = 0;
+    return fail(PASTILA_ETIMEOUT, "a tile's staging copies did not complete within the wait limit; the outputs are "
+                "unspecified");
+}
+
 void invalidate_stats(pastila_series* h) {
     for (auto& kv : h->stats) kv.second.stale = true;
 }
@@ -207,16 +232,17 @@ pastila_status ensure_stats(pastila_series* h, int ell, Stats** out) {
         muh = it->second.muh;
         mul = it->second.mul;
     } else {
+        // the tile kernels' bulk copies may read up to 16 bytes past an array's end
         TRY(dev_alloc(h, &mu, 8 * st.C));
-        TRY(dev_alloc(h, &a, rs * st.C));
-        TRY(dev_alloc(h, &df, rs * st.C));
-        TRY(dev_alloc(h, &dg, rs * st.C));
-        TRY(dev_alloc(h, &muh, rs * st.C));
-        TRY(dev_alloc(h, &mul, rs * st.C));
+        TRY(dev_alloc(h, &a, rs * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &df, rs * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &dg, rs * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &muh, rs * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &mul, rs * (st.C + ARRAY_PAD)));
     }
     if (!h->Th) {
-        TRY(dev_alloc(h, &h->Th, rs * h->n));
-        TRY(dev_alloc(h, &h->Tl, rs * h->n));
+        TRY(dev_alloc(h, &h->Th, rs * (h->n + ARRAY_PAD)));
+        TRY(dev_alloc(h, &h->Tl, rs * (h->n + ARRAY_PAD)));
     }
     TRY(scratch(h, "stats_inv", 8 * st.C, &inv));
     TRY(scratch(h, "stats_flat", 4 * st.C, &flat));
@@ -420,6 +446,9 @@ ProfileArgs<real> profile_args(const pastila_series* h, const MParams& q, const 
     A.ntiles = (int)((q.P + g.W - 1) / g.W);
     A.D = D;
     A.dmax_key = dmax;
+    A.err = h->err;
+    A.spin_limit = h->spin_limit;
+    A.test_timeout = h->test_timeout;
     return A;
 }
 
@@ -1136,6 +1165,14 @@ pastila_status create_common(pastila_series** out, int64_t n, int device, size_t
         }
         h->own_stream = true;
     }
+    wait_knobs(&h->spin_limit, &h->test_timeout);
+    if (cudaHostAlloc((void**)&h->err, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->own_stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return fail(PASTILA_ENOMEM, "the handle's error flag could not be allocated");
+    }
+    *h->err = 0;
     pastila_status st = dev_alloc(h, (void**)&h->T, 8 * (size_t)n);
     if (st != PASTILA_OK) {
         if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -1176,7 +1213,7 @@ pastila_status pastila_tune(pastila_series* h, const int32_t* m_list, int32_t n_
         else
             TRY(tune_t<float, V_F32>(h, q, max_candidates, out ? out + i : nullptr));
     }
-    return PASTILA_OK;
+    return stage_check(h);
 }
 
 pastila_status pastila_tune_set(pastila_precision prec, int32_t m, int32_t ell, int32_t k, int32_t W, int32_t NG,
@@ -1331,6 +1368,7 @@ void pastila_destroy(pastila_series* h) {
     cudaFree(h->T);
     cudaFree(h->Th);
     cudaFree(h->Tl);
+    if (h->err) cudaFreeHost(h->err);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -1396,7 +1434,7 @@ pastila_status pastila_profiles(pastila_series* h, int32_t m, pastila_mparams mp
     CK(cudaMemcpyAsync(&key, dk, 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (D_max_out) *D_max_out = KeyOf<double>::dec(key);
-    return PASTILA_OK;
+    return stage_check(h);
 }
 
 pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp, int32_t K,
@@ -1417,7 +1455,8 @@ pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp
         if (sd == PASTILA_ENOMEM) {  // D does not fit: search without it, same results
             g_err.clear();
             TRY(streamed(h, q, K, labels_out, snippet_profiles_out, nullptr));
-            return read_snippets(h, K, out);
+            TRY(read_snippets(h, K, out));
+            return stage_check(h);
         }
         TRY(sd);
     }
@@ -1436,7 +1475,7 @@ pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp
                                cudaMemcpyDeviceToHost, h->stream));
     }
     TRY(read_snippets(h, K, out));
-    return PASTILA_OK;
+    return stage_check(h);
 }
 
 pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_mparams mp, int32_t K,
@@ -1451,7 +1490,8 @@ pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_m
     if (K < 1 || K > q.S || K > 64)
         return fail(PASTILA_EINVAL, "K = %d: must satisfy 1 <= K <= min(n / m, 64) = %d", K, q.S < 64 ? q.S : 64);
     TRY(streamed(h, q, K, labels_out, snippet_profiles_out, work_out));
-    return read_snippets(h, K, out);
+    TRY(read_snippets(h, K, out));
+    return stage_check(h);
 }
 
 pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, int32_t n_m, pastila_mparams rule,
@@ -1470,8 +1510,10 @@ pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, i
     if (K < 2 || K > min_S || K > 64)
         return fail(PASTILA_EINVAL, "K = %d: must satisfy 2 <= K <= min(n / max m, 64) = %d", K,
                     min_S < 64 ? min_S : 64);
-    if (h->prec == PASTILA_FP32)
-        return select_length_batched_t<float, V_F32>(h, m_list, n_m, rule, qs, K, m_best, crit_out, best_out);
+    if (h->prec == PASTILA_FP32) {
+        TRY(select_length_batched_t<float, V_F32>(h, m_list, n_m, rule, qs, K, m_best, crit_out, best_out));
+        return stage_check(h);
+    }
     // FP64: the plain path, one length after the other
     const size_t rs = real_size(h);
     void *crit, *ms, *bi, *dk;
@@ -1500,7 +1542,7 @@ pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, i
     *m_best = m_list[b];
     if (crit_out) memcpy(crit_out, cv.data(), 8 * (size_t)n_m);
     if (best_out) memcpy(best_out, per_m.data() + (size_t)b * K, sizeof(pastila_snippet) * K);
-    return PASTILA_OK;
+    return stage_check(h);
 }
 
 }  // extern "C"

@@ -15,11 +15,13 @@
 // g*Rg .. g*Rg+Rg-1; column thread t owns the V columns tV .. tV+V-1.  All
 // groups step through their rows together, one barrier per step.
 // Phases:
+//   0  stage: bulk asynchronous copies (cp.async.bulk, completing on an
+//      mbarrier) of the tile's series values and the segment's row statistics
+//      into shared memory
 //   1  seeds: exact dot products cov(g*Rg, x) for every column at the first row
 //      of every row group, and cov(r, 0) for every row (left edge), in the
-//      working precision, from series values held as hi + lo pairs about a tile
-//      reference and centred locally before they are multiplied (covariance is
-//      shift-invariant)
+//      working precision, from series values held as hi + lo pairs and centred
+//      locally before they are multiplied (covariance is shift-invariant)
 //   2  rows: centred recurrence along diagonals
 //        cov(r, x) = cov(r-1, x-1) + df_i dg_j + df_j dg_i
 //      The covariance is carried as hi + lo: the updates of up to V rows
@@ -46,6 +48,56 @@
 #include "keys.cuh"
 
 namespace pastila {
+
+// Bulk asynchronous copies from global to shared memory, completing on an
+// mbarrier (the async copy engine moves the bytes; no thread issues loads).
+// Both addresses must be 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// makes an initialised mbarrier visible to the async proxy
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of the given parity to complete, for at most `limit`
+// SM clock cycles; false if it did not.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
 
 template <typename real> struct RealLimits;
 template <> struct RealLimits<float> {
@@ -76,6 +128,13 @@ struct ProfileArgs {
     // areas without D
     const real* M;
     double* part;
+    // bounded waits: the staging wait gives up after spin_limit SM cycles and
+    // then stores 1 to *err (host-visible); test_timeout is 0, and 1 only in
+    // the test that makes the wait run out (a second wait, on the barrier's
+    // next phase, which nothing completes)
+    int* err;
+    long long spin_limit;
+    int test_timeout;
 };
 
 // Shared-memory layout and thread layout of one tile; identical on host and device.
@@ -88,6 +147,7 @@ struct TileGeom {
     // other CTAs write the rows they compute into it through distributed shared
     // memory), CBp[c'] the partial column maxima of CTA c'
     int CS, Rh, Wc;
+    int RSt;  // stride of the five row-statistic arrays (room for a 16-byte-aligned copy of R values)
     size_t off_AB, off_CB, off_PRE, off_CM, off_LV, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
         off_Ts, off_Tsl, off_q, off_CBp, bytes;
 };
@@ -129,13 +189,17 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.off_CM = o;   o = align16(o + sizeof(real) * NG * 2 * (size_t)(g.NTc + 1));
     g.off_LV = o;   o = align16(o + sizeof(real) * NG * 2 * 4 * (size_t)g.NTc);
     g.off_XCH = o;  o = align16(o + sizeof(real) * NG * 4 * (size_t)g.NWc);
-    g.off_row = o;  o = align16(o + sizeof(real) * 5 * (size_t)g.R);
+    // staged copies start at a 16-byte boundary at or below the data (up to
+    // 16 / sizeof(real) - 1 elements early) and cover whole 16-byte units
+    const int AE = 16 / (int)sizeof(real);
+    g.RSt = (g.R + 2 * AE + AE - 1) / AE * AE;
+    g.off_row = o;  o = align16(o + sizeof(real) * 5 * (size_t)g.RSt);
     g.off_left = o; o = align16(o + sizeof(real) * (size_t)g.R);
     g.off_top = o;  o = align16(o + sizeof(real) * NG * (size_t)(g.NTc * V));
     g.off_Tc = o;   o = align16(o + sizeof(real) * (size_t)(g.NTc * V + ell + 64));
     g.off_Tcl = o;  o = align16(o + sizeof(real) * (size_t)(g.NTc * V + ell + 64));
-    g.off_Ts = o;   o = align16(o + sizeof(real) * (size_t)m);
-    g.off_Tsl = o;  o = align16(o + sizeof(real) * (size_t)m);
+    g.off_Ts = o;   o = align16(o + sizeof(real) * (size_t)(m + 2 * AE));
+    g.off_Tsl = o;  o = align16(o + sizeof(real) * (size_t)(m + 2 * AE));
     g.off_q = o;    o = align16(o + sizeof(real) * NG * (size_t)(ell + 1));
     g.off_CBp = o;  o = align16(o + (CS > 1 ? sizeof(real) * (size_t)CS * (g.Wb + 32) : 0));
     g.bytes = o;
@@ -602,117 +666,91 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     real* LV = (real*)(sm + G.off_LV) + (size_t)g * 2 * 4 * NTc;     // [parity][k-1][NTc]: max of the 2^k chunk
                                                                       // maxima from a chunk on, within its warp
     real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][hi/lo][warp]
-    real* rdf = (real*)(sm + G.off_row);
-    real* rdg = rdf + R;
-    real* ra = rdg + R;
-    real* rmu = ra + R;   // mu_i as hi + lo
-    real* rmul = rmu + R;
+    // segment data are staged from the 16-byte boundary at or below i0
+    constexpr int AE = 16 / (int)sizeof(real);
+    const int os = (int)(i0 % AE);
+    real* rowb = (real*)(sm + G.off_row);
+    const int RSt = G.RSt;
+    real* rdf = rowb + os;
+    real* rdg = rowb + RSt + os;
+    real* ra = rowb + 2 * RSt + os;
+    real* rmu = rowb + 3 * RSt + os;  // mu_i as hi + lo
+    real* rmul = rowb + 4 * RSt + os;
     real* lseed = (real*)(sm + G.off_left);
     real* top = (real*)(sm + G.off_top);  // [group][NTc * V] seeds, later the groups' column maxima
     real* Tc = (real*)(sm + G.off_Tc);    // the window's T as hi + lo pairs: exact to
     real* Tcl = (real*)(sm + G.off_Tcl);  // about twice the working precision
-    real* Ts = (real*)(sm + G.off_Ts);    // the segment's T, the same way
-    real* Tsl = (real*)(sm + G.off_Tsl);
+    real* Tsb = (real*)(sm + G.off_Ts);   // the segment's T, the same way
+    real* Tslb = (real*)(sm + G.off_Tsl);
+    real* Ts = Tsb + os;
+    real* Tsl = Tslb + os;
     real* q = (real*)(sm + G.off_q);      // [group][ell + 1] centred head of the group's first row
 
     // ---------------------------------------------------------------- stage
-    // One index space over everything staged: the window's and the segment's
-    // series values (hi + lo pairs), the five row statistics and the groups'
-    // centred heads.  In FP32 each thread issues the global loads of SG
-    // elements before any of their shared stores, so a whole chunk's loads are
-    // in flight together (one CTA per SM hides no latency for them).  No FP64
-    // arithmetic: the series and the means arrive as pairs.
+    // Bulk asynchronous copies of the window's and the segment's series pairs
+    // and the segment's five row statistics, completing on one mbarrier.  Each
+    // copy starts at a 16-byte boundary (the window's start p0 is a multiple of
+    // the tile width; the segment's is rounded down by os elements) and covers
+    // whole 16-byte units (the device arrays carry padding past their ends).
+    // No FP64 arithmetic: the series and the means arrive as pairs.  The wait
+    // is bounded: past the limit the tile stores an error flag for the host and
+    // goes on with whatever the shared memory holds, so that every barrier of
+    // the tile (and of its cluster) is still reached.
+    __shared__ uint64_t stage_bar;
     const int nTc = Wb + ell - 1;
-    const real c0h = A.muh[p0], c0l = A.mul[p0];  // mean of column 0, for the left seeds
-    if constexpr (sizeof(real) == 4) {
-        constexpr int SG = 4;
-        const int n1 = NTc * V + ell + 64, n2 = n1 + m, n3 = n2 + 5 * R, n4 = n3 + NG * ell;
-        for (int e0 = tid; e0 < n4; e0 += SG * BD) {
-            real x[SG], y[SG], z[SG], w[SG];
-#pragma unroll
-            for (int u = 0; u < SG; ++u) {
-                const int e = e0 + u * BD;
-                x[u] = y[u] = z[u] = w[u] = (real)0;
-                if (e < n1) {
-                    if (e < nTc) {
-                        x[u] = A.Th[p0 + e];
-                        y[u] = A.Tl[p0 + e];
-                    }
-                } else if (e < n2) {
-                    x[u] = A.Th[i0 + (e - n1)];
-                    y[u] = A.Tl[i0 + (e - n1)];
-                } else if (e < n3) {
-                    const int kind = (e - n2) / R;
-                    const int64_t i = i0 + ((e - n2) - kind * R);
-                    const real* src = kind == 0 ? A.df : kind == 1 ? A.dg : kind == 2 ? A.a : kind == 3 ? A.muh : A.mul;
-                    x[u] = src[i];
-                } else if (e < n4) {
-                    const int gg = (e - n3) / ell, uu = (e - n3) - gg * ell;
-                    const int64_t ig = i0 + rbase + (int64_t)gg * Rg;
-                    x[u] = A.Th[ig + uu];
-                    y[u] = A.Tl[ig + uu];
-                    z[u] = A.muh[ig];
-                    w[u] = A.mul[ig];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < SG; ++u) {
-                const int e = e0 + u * BD;
-                if (e < n1) {
-                    Tc[e] = x[u];
-                    Tcl[e] = y[u];
-                } else if (e < n2) {
-                    Ts[e - n1] = x[u];
-                    Tsl[e - n1] = y[u];
-                } else if (e < n3) {
-                    const int kind = (e - n2) / R, r = (e - n2) - kind * R;
-                    real* dst = kind == 0 ? rdf : kind == 1 ? rdg : kind == 2 ? ra : kind == 3 ? rmu : rmul;
-                    dst[r] = x[u];
-                } else if (e < n4) {
-                    const int gg = (e - n3) / ell, uu = (e - n3) - gg * ell;
-                    q[gg * (ell + 1) + uu] = (x[u] - z[u]) + (y[u] - w[u]);
-                }
-            }
+    {
+        const int64_t is = i0 - os;
+        const uint32_t bw = (uint32_t)(sizeof(real) * ((nTc + AE - 1) / AE * AE));
+        const uint32_t bs = (uint32_t)(sizeof(real) * ((os + m + AE - 1) / AE * AE));
+        const uint32_t br = (uint32_t)(sizeof(real) * ((os + R + AE - 1) / AE * AE));
+        if (tid == 0) {
+            mbar_init(&stage_bar, 1);
+            mbar_init_fence();
+            mbar_arrive_expect_tx(&stage_bar, 2 * bw + 2 * bs + 5 * br);
+            bulk_copy_g2s(Tc, A.Th + p0, bw, &stage_bar);
+            bulk_copy_g2s(Tcl, A.Tl + p0, bw, &stage_bar);
+            bulk_copy_g2s(Tsb, A.Th + is, bs, &stage_bar);
+            bulk_copy_g2s(Tslb, A.Tl + is, bs, &stage_bar);
+            bulk_copy_g2s(rowb, A.df + is, br, &stage_bar);
+            bulk_copy_g2s(rowb + RSt, A.dg + is, br, &stage_bar);
+            bulk_copy_g2s(rowb + 2 * RSt, A.a + is, br, &stage_bar);
+            bulk_copy_g2s(rowb + 3 * RSt, A.muh + is, br, &stage_bar);
+            bulk_copy_g2s(rowb + 4 * RSt, A.mul + is, br, &stage_bar);
         }
-    } else {  // FP64: plain loops (the merged form costs the FP64 kernels a register spill)
-        for (int y = tid; y < NTc * V + ell + 64; y += BD) {
-            const bool in = y < nTc;
-            Tc[y] = in ? A.Th[p0 + y] : (real)0;
-            Tcl[y] = in ? A.Tl[p0 + y] : (real)0;
-        }
-        for (int u = tid; u < m; u += BD) {
-            Ts[u] = A.Th[i0 + u];
-            Tsl[u] = A.Tl[i0 + u];
-        }
-        for (int r = tid; r < R; r += BD) {
-            rdf[r] = A.df[i0 + r];
-            rdg[r] = A.dg[i0 + r];
-            ra[r] = A.a[i0 + r];
-            rmu[r] = A.muh[i0 + r];
-            rmul[r] = A.mul[i0 + r];
-        }
-        for (int e = tid; e < NG * ell; e += BD) {
-            const int gg = e / ell, u = e - gg * ell;
-            const int64_t ig = i0 + rbase + (int64_t)gg * Rg;
-            q[gg * (ell + 1) + u] = (A.Th[ig + u] - A.muh[ig]) + (A.Tl[ig + u] - A.mul[ig]);
+        // meanwhile: zeros past the copied window (columns beyond the tile feed
+        // only discarded seeds)
+        const int wcopied = (int)(bw / sizeof(real));
+        for (int y = wcopied + tid; y < NTc * V + ell + 64; y += BD) {
+            Tc[y] = (real)0;
+            Tcl[y] = (real)0;
         }
     }
-    __syncthreads();
-    if ((tid >> 5) < NG) {  // warp gg: sum of group gg's rounded q, in FP64
-        const int gg = tid >> 5;
-        double acc = 0;
-        for (int u = lane; u < ell; u += 32) acc += (double)q[gg * (ell + 1) + u];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (lane == 0) q[gg * (ell + 1) + ell] = (real)acc;
-    }
-
     // this thread's column statistics for the rows phase, loaded now so that
-    // their latency passes under the seeds (FP32 path; the FP64 path has no
-    // registers to spare and loads them after the seeds)
+    // their latency passes under the staging and the seeds (FP32 path; the FP64
+    // path has no registers to spare and loads them after the seeds)
     const int xb = t * V;
     real cdf[V], cdg[V], ca[V];
     auto load_cols = [&]() {
+        if constexpr (sizeof(real) == 4 && V == 4) {
+            if (xb + V <= Wb) {  // p0 + xb is a multiple of 4 (W is a multiple of 32): one 16-byte load each
+                const float4 f = *reinterpret_cast<const float4*>(A.df + p0 + xb);
+                const float4 gq = *reinterpret_cast<const float4*>(A.dg + p0 + xb);
+                const float4 aq = *reinterpret_cast<const float4*>(A.a + p0 + xb);
+                cdf[0] = f.x;
+                cdf[1] = f.y;
+                cdf[2] = f.z;
+                cdf[3] = f.w;
+                cdg[0] = gq.x;
+                cdg[1] = gq.y;
+                cdg[2] = gq.z;
+                cdg[3] = gq.w;
+                ca[0] = aq.x;
+                ca[1] = aq.y;
+                ca[2] = aq.z;
+                ca[3] = aq.w;
+                return;
+            }
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int x = xb + v;
@@ -724,6 +762,28 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     };
     constexpr bool early_cols = sizeof(real) == 4;
     if (early_cols) load_cols();
+    const real c0h = A.muh[p0], c0l = A.mul[p0];  // mean of column 0, for the left seeds
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    {
+        bool ok = mbar_wait_bounded(&stage_bar, 0, A.spin_limit);
+        if (ok && A.test_timeout) ok = mbar_wait_bounded(&stage_bar, 1, A.spin_limit);
+        if (!ok) *(volatile int*)A.err = 1;
+    }
+    // the groups' centred heads q = T[ig + u] - mu_ig, ig = i0 + rbase + gg Rg
+    for (int e = tid; e < NG * ell; e += BD) {
+        const int gg = e / ell, u = e - gg * ell;
+        const int rb = rbase + gg * Rg;
+        q[gg * (ell + 1) + u] = (Ts[rb + u] - rmu[rb]) + (Tsl[rb + u] - rmul[rb]);
+    }
+    __syncthreads();
+    if ((tid >> 5) < NG) {  // warp gg: sum of group gg's rounded q, in FP64
+        const int gg = tid >> 5;
+        double acc = 0;
+        for (int u = lane; u < ell; u += 32) acc += (double)q[gg * (ell + 1) + u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (lane == 0) q[gg * (ell + 1) + ell] = (real)acc;
+    }
 
     // ---------------------------------------------------------------- seeds
     // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0), both
