@@ -52,11 +52,8 @@ SM_MAX_MHZ = 2032.0
 # exact seed of every diagonal (ell FMA per R cells, about 2 FLOP at ell = m/2)
 FLOP_PER_ED_CELL = 8.0
 # dram__bytes_read.sum + dram__bytes_write.sum of the tile launches of one sweep
-# step (one-CTA tiles of m = 64 .. 256: 45 MB + 2.09 GB; two-CTA cluster tiles of
-# m = 288 .. 512: 45 MB + 0.78 GB), measured with ncu on this kernel version; when
-# the tuner gives m = 64 a two-CTA-per-SM layout (its own launch) the sum was
-# 2.92 GB
-SWEEP_TILE_DRAM_BYTES = 2.96e9
+# step, from an ncu capture of this kernel version (None: not yet measured)
+SWEEP_TILE_DRAM_BYTES = None
 
 
 def workload(m_list=None):
