@@ -33,8 +33,12 @@ def test_four_regime_profiles(lib, prec):
 # (n, m, ell, k): several tiles with a ragged last tile and a tail segment
 # (n % m != 0); R < V (ell close to m); R = 1 (ell = m); k >= 2R (max branch);
 # k = 1 (min branch); odd sizes; R > 288 and R > 384 (the selection keeps 12
-# values of a column per lane in registers and reads the rest from shared memory)
+# values of a column per lane in registers and reads the rest from shared memory);
+# odd m, so that segment starts s m fall at every offset from a 16-byte boundary
+# (the tile stages segment data from the boundary below the start)
 CASES = [
+    (2777, 77, 39, 8),
+    (1999, 33, 17, 4),
     (4000, 640, 320, 64),
     (4500, 600, 150, 60),
     (3000, 400, 200, 40),
