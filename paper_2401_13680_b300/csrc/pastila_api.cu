@@ -658,7 +658,7 @@ pastila_status snippets_on_device(pastila_series* h, const MParams& q, const voi
 //
 // Steps 0 and 1 run one streaming pass over all segments, which gives every
 // segment's area sum_p min(M_p, D_s(p)) up to FP64 rounding (relative error far
-// below 1e-9), whole and over 64 blocks of positions; the segments whose area
+// below 1e-9), whole and over STREAM_NB blocks of positions; the segments whose area
 // lies within that margin of the best are recomputed exactly (their rows, then
 // the same per-row sum as the materialized path), and the exact minimum wins
 // (lowest index on ties).  From step 2 on, M only shrinks, so the area of a
@@ -682,7 +682,7 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     const int ntiles = (int)((P + g.W - 1) / g.W);
     const int chunk = std::max(1, std::min(S, (int)((size_t)(32u << 20) / (size_t)ntiles)));  // <= 256 MiB of partials
     // position blocks for the bounds: NB blocks of TB whole tiles (L positions)
-    const int TB = (ntiles + 63) / 64, NB = (ntiles + TB - 1) / TB;
+    const int TB = (ntiles + STREAM_NB - 1) / STREAM_NB, NB = (ntiles + TB - 1) / TB;
     const int64_t L = (int64_t)TB * g.W;
     void *part, *apx, *blk, *keep, *M, *rows, *segs, *rarea, *rblk, *dk, *mblk;
     void *chosen_d, *aafter_d, *counts, *oi, *orank, *ofrac, *oarea, *lab = nullptr;
@@ -696,7 +696,7 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     TRY(scratch(h, "st_rarea", 8 * BATCH, &rarea));
     TRY(scratch(h, "st_rblk", 8 * (size_t)BATCH * NB, &rblk));
     TRY(scratch(h, "dmax", 8, &dk));
-    TRY(scratch(h, "st_mblk", 8 * 64, &mblk));
+    TRY(scratch(h, "st_mblk", 8 * STREAM_NB, &mblk));
     TRY(scratch(h, "sn_chosen", 4 * 64, &chosen_d));
     TRY(scratch(h, "sn_aafter", 8 * 64, &aafter_d));
     TRY(scratch(h, "sn_counts", 8 * 64, &counts));
@@ -720,7 +720,7 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
         for (int s0 = 0; s0 < S; s0 += chunk) {
             const int ns = std::min(chunk, S - s0);
             stream_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)ns), g.NT, g.bytes, h->stream>>>(B, g, s0);
-            segment_blocks_kernel<<<ns, 64, 0, h->stream>>>((const double*)part, ntiles, TB, NB,
+            segment_blocks_kernel<<<ns, STREAM_NB, 0, h->stream>>>((const double*)part, ntiles, TB, NB,
                                                             (double*)blk + (size_t)s0 * NB, (double*)apx + s0);
             h->launches += 2;
         }

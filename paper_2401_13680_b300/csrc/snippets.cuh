@@ -76,12 +76,21 @@ row_area_kernel(const real* __restrict__ rows, int64_t P, const real* __restrict
     if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
+// Position blocks of the greedy search without the profile set: at most
+// STREAM_NB blocks of whole tiles (finer blocks give bounds that are tighter in
+// principle; 256 and 1024 blocks recomputed the same rows as 64 on the n = 10^6
+// drift series).
+#ifndef STREAM_NB
+#define STREAM_NB 64
+#endif
+
 // Block sums of the tile partials: blocks[s][b] = sum of part[s][tile] over the
 // tiles b*TB .. (b+1)*TB-1, in tile order, and tot[s] = the sum of the blocks in
-// order.  Grid (segments), 64 threads (NB <= 64).
-__global__ void segment_blocks_kernel(const double* __restrict__ part, int ntiles, int TB, int NB,
-                                      double* __restrict__ blocks, double* __restrict__ tot) {
-    __shared__ double bs[64];
+// order.  Grid (segments), STREAM_NB threads (NB <= STREAM_NB).
+__global__ void __launch_bounds__(STREAM_NB) segment_blocks_kernel(const double* __restrict__ part, int ntiles, int TB,
+                                                                   int NB, double* __restrict__ blocks,
+                                                                   double* __restrict__ tot) {
+    __shared__ double bs[STREAM_NB];
     const int s = blockIdx.x, b = threadIdx.x;
     double acc = 0.0;
     if (b < NB) {
