@@ -414,7 +414,9 @@ pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_m
  * the cheapest of every thread count, then by modelled cost, these within
  * 1.5x of the model's best), each also with twice the default selection group
  * width where R <= 288, on the first
- * min(S, 64) segments of h's series, and keeps the fastest in a process-wide
+ * min(S, 64) segments of h's series, and keeps the fastest (a rival must beat
+ * the layout kept so far by more than 1 %, so that layouts within timing noise
+ * of each other do not trade places from run to run) in a process-wide
  * table keyed by (precision, m, ell, k) that every later call uses (handles and
  * engines alike; a captured select_length graph is rebuilt).  Results depend
  * on the layout only through FP32 rounding (the seeds sit at the tile and

@@ -321,6 +321,7 @@ struct TileCand {
     bool pair;    // two CTAs of this layout fit on one SM
 };
 
+constexpr double TUNE_MARGIN = 0.01;
 constexpr int CLUSTER_MIN_R = 65;    // two-CTA cluster tiles are considered from R = 65 up
 constexpr int CLUSTER4_MIN_R = 129;  // four-CTA cluster tiles from R = 129 up
 
@@ -486,10 +487,10 @@ pastila_status launch_profiles(pastila_series* h, const MParams& q, void* D, uns
     return launch_profiles_t<float, V_F32>(h, q, st, (float*)D, dmax);
 }
 
-// Autotuner: times the cost model's layout and its closest rivals (the cheapest
-// of every thread count first, then by modelled cost, within 1.5x of the
-// model's best) on the first min(S, 64) segments of this series, and keeps the
-// fastest for (precision, m, ell, k).
+// Autotuner: times the cost model's layout and its closest rivals (the model's
+// best cluster and two-CTA-per-SM layouts, the cheapest of every thread count,
+// then by modelled cost within 1.5x of the model's best) on the first min(S, 64)
+// segments of this series, and keeps the fastest for (precision, m, ell, k).
 template <typename real, int V>
 pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila_tune_result* res) {
     std::vector<TileCand> c;
@@ -572,7 +573,11 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
         CK(cudaGetLastError());
         h->launches += 3;
         if (i == 0) model_ms = best;
-        if (best < best_ms) {
+        // a rival replaces the layout kept so far only when it is faster by more
+        // than TUNE_MARGIN: layouts within timing noise of each other do not
+        // trade places from one run to the next (and with them the rounding of
+        // the results)
+        if (i == 0 || best < best_ms * (1.0 - TUNE_MARGIN)) {
             best_ms = best;
             bi = i;
         }
