@@ -179,6 +179,25 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def max_over_ranks(seconds: float, dist=None, device="cpu") -> float:
+    """The whole job's time: the slowest rank's (every rank calls this after the
+    same timed region; replicas only, so this is the one collective)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, cells_per_step: float, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas, each doing `steps` steps of
+    `cells_per_step` cells, all done within `seconds` (the slowest rank's time)."""
+    return world * cells_per_step * steps / seconds
+
+
 # ----------------------------------------------------------------------------- serving
 
 def job_ed_cells(job):
@@ -340,11 +359,8 @@ def run_ours(args):
     h.set_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     tot_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([tot_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_s = float(t.item())
-    value = world * prof_cells * args.steps / tot_s
+    tot_s = max_over_ranks(tot_s, dist, dev)
+    value = replica_rate(world, prof_cells, args.steps, tot_s)
     clocks = clk.summary()
 
     # ---- end to end through the C ABI: host series in, host results out
@@ -356,9 +372,9 @@ def run_ours(args):
         h.reload(T_host)
         h.select_length(ms, K_SNIPPETS)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
     d2h = 4 + 8 * len(ms) + len(ms) * K_SNIPPETS * 24
-    e2e = {"value": world * prof_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+    e2e = {"value": replica_rate(world, prof_cells, 1, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
 
     # ---- roofline of the dominant kernel (profile tiles), from its own events:
