@@ -55,6 +55,10 @@ FLOP_PER_ED_CELL = 8.0
 # step (one-CTA tiles of m = 64 .. 256: 47 MB + 2.09 GB; two-CTA cluster tiles of
 # m = 288 .. 512: 46 MB + 0.78 GB), from an ncu capture of this kernel version
 SWEEP_TILE_DRAM_BYTES = 2.97e9
+# smsp__issue_active.avg.pct_of_peak_sustained_active of the tile kernel at two
+# lengths of the sweep (ncu --set full on this kernel version): the share of the
+# SMs' instruction-issue slots the kernel fills, beside the FLOP fraction
+TILE_ISSUE_ACTIVE = {"m128": 0.551, "m512": 0.520}
 
 
 def workload(m_list=None):
@@ -394,7 +398,9 @@ def run_ours(args):
                 "launches": tile_launches, "avg_launch_ms": tile_ms / max(tile_launches, 1),
                 "ed_cells_per_s": ed_cells * args.steps / tile_s,
                 "tile_share_of_step": tile_s / tot_s if world == 1 else None,
-                "halo_factor": tile_cells_halo / (ed_cells * args.steps)}
+                "halo_factor": tile_cells_halo / (ed_cells * args.steps),
+                "issue_active_ncu": dict(TILE_ISSUE_ACTIVE, source="profiles/tile_kernel_six_regime_m128.md, "
+                                                                   "profiles/tile_kernel_six_regime_m512_cluster.md")}
 
     # ---- the plain FP64 one-job GPU path on the same workload (one step)
     fp64 = None
