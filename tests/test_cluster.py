@@ -109,3 +109,43 @@ def test_tune_set_argument_errors(lib):
         pastila.tune_set(0, 128, 64, 13, 256, 2, 4, 1)
     with pytest.raises(pastila.PastilaError, match="no tuned layout"):
         pastila.tune_get(0, 123, 61, 13)
+
+
+def test_two_ctas_per_sm_layouts(table):
+    """Layouts of at most 256 threads and half an SM's shared memory (two CTAs per
+    SM) get a tile launch of their own in a sweep: parity with the oracle, one
+    more tile launch than with the model's layouts, the same criterion as eq. 18
+    on the GPU's own profiles, and the engine's results equal select_length."""
+    pastila = table
+    s = synth.four_regimes(per_regime=750)  # n = 3000
+    ms, K = [64, 96, 128, 160], 3
+    with pastila.Series(s.T, precision=pastila.FP32) as h:
+        h.select_length(ms, K)
+        l0 = h.kernel_launches()
+        h.select_length(ms, K)
+        base_launches = h.kernel_launches() - l0
+    _force(pastila, 0, 64, 32, 7, 480, 2, 4, CS=1)
+    _force(pastila, 0, 128, 64, 13, 320, 2, 8, CS=1)
+    with pastila.Series(s.T, precision=pastila.FP32) as h:
+        for m in (64, 128):
+            lay = h.tile_layout(m)
+            assert lay["NT"] <= 256 and lay["CS"] == 1, lay
+        r = h.select_length(ms, K)
+        l0 = h.kernel_launches()
+        r2 = h.select_length(ms, K)
+        assert h.kernel_launches() - l0 == base_launches + 1  # the two-CTA-per-SM launch
+        assert r2[0] == r[0] and np.array_equal(r2[1], r[1])
+        for i, m in enumerate(ms):
+            D, _ = h.profiles(m)
+            Dd = D.astype(np.float64)
+            c, _ = oracle.greedy(Dd, K)
+            assert r[1][i] == pytest.approx(oracle.criterion(Dd, c), rel=1e-12)
+            ref = oracle.profiles(s.T, m, m // 2, (m + 9) // 10)
+            assert_profiles_close(D, ref, m // 2, 1e-4)
+    with pastila.Engine(wave_ed_cells=3e6) as e:
+        j = e.submit(s.T, ms, K)
+        assert e.wait(j)["state"] == pastila.JOB_DONE
+        got = e.result(j)
+    assert got[0] == r[0]
+    np.testing.assert_array_equal(got[1], r[1])
+    assert got[2] == r[2]

@@ -177,6 +177,30 @@ def test_snippets_fp64_bit_exact(lib, K):
     np.testing.assert_allclose(prof, D[chosen], rtol=1e-9, atol=1e-9)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_snippets_every_segment_chosen(lib, prec):
+    # K = S: every segment becomes a snippet.  FP64: the oracle's greedy order,
+    # areas, shares and labels; FP32: the same on the GPU's own profiles (the
+    # decisions are taken on FP32 values).  The areas never grow.
+    from paper_2401_13680_b300 import pastila
+    s = synth.four_regimes(per_regime=320)  # n = 1280
+    m, ell, k = 128, 64, 13
+    S = s.T.shape[0] // m
+    with pastila.Series(s.T, precision=prec) as h:
+        recs, lab, prof = h.snippets(m, S, want_labels=True, want_profiles=True)
+        D, _ = h.profiles(m)
+    chosen, area, labels, frac, order, _ = oracle.snippets(s.T, m, ell, k, S,
+                                                           D=None if prec == 1 else D.astype(np.float64))
+    assert sorted(r[0] for r in recs) == list(range(S))
+    assert [r[0] for r in recs] == [int(chosen[o]) for o in order]
+    assert [r[1] for r in recs] == [int(o) for o in order]
+    np.testing.assert_allclose([r[2] for r in recs], [frac[o] for o in order], rtol=0, atol=1e-12)
+    np.testing.assert_allclose([r[3] for r in recs], [area[o] for o in order], rtol=1e-9)
+    assert np.array_equal(lab, labels)
+    by_step = sorted(recs, key=lambda r: r[1])
+    assert all(b[3] <= a_[3] for a_, b in zip(by_step, by_step[1:]))
+
+
 @pytest.mark.parametrize("K", [2, 4])
 def test_snippets_fp32(lib, K):
     """FP32: (1) the GPU greedy equals the oracle greedy run on the GPU's own D
