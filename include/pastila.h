@@ -388,12 +388,14 @@ pastila_status pastila_model_predict(pastila_precision prec, int64_t n, const in
  * profile set, for lengths whose D does not fit the budget or the device
  * (pastila_snippets switches to it by itself when allocating D fails with
  * ENOMEM).  Rows of D are recomputed by the profile kernel: one pass over all
- * segments for each of the first two greedy steps, then only the rows whose
- * area bound can still beat the best (M only shrinks, so a segment's area over
- * a block of positions falls by at most the block's drop in M and not below 0:
- * its last known block areas bound its next area).  Memory: K + 9 rows of P
- * values, the FP64 partial sums of at most 256 MiB, and 65 doubles per
- * segment.  Results (records, labels, chosen profiles) are
+ * segments, which also keeps a sketch of every row (per block of whole tiles:
+ * its sum, largest and smallest value), then, at every step, only the rows
+ * whose lower area bound can still beat the best (from the sketch against the
+ * current curve M, and, for a row recomputed earlier, its block areas then
+ * less the block's drop in M since).  Memory: K + 10 rows of P values and P doubles, at
+ * most 256 MiB of per-tile partials and 512 MiB of sketches and block areas
+ * (the blocks are as fine as that allows, down to one tile).  Results
+ * (records, labels, chosen profiles) are
  * identical to pastila_snippets on the materialised D: every area it compares
  * is computed exactly as there.  work_out (may be NULL) receives two values:
  * full passes over the segments and rows recomputed.  No counterpart in the

@@ -661,16 +661,18 @@ pastila_status snippets_on_device(pastila_series* h, const MParams& q, const voi
 // evaluation), for lengths whose D does not fit.  Rows of D are recomputed by
 // the tile kernel; the profiles of the K chosen segments are kept.
 //
-// Steps 0 and 1 run one streaming pass over all segments, which gives every
-// segment's area sum_p min(M_p, D_s(p)) up to FP64 rounding (relative error far
-// below 1e-9), whole and over STREAM_NB blocks of positions; the segments whose area
-// lies within that margin of the best are recomputed exactly (their rows, then
-// the same per-row sum as the materialized path), and the exact minimum wins
-// (lowest index on ties).  From step 2 on, M only shrinks, so the area of a
-// segment over a block can fall by at most that block's drop in M, and not
-// below 0: the block areas last known for a segment bound its area from below;
-// segments are recomputed in order of that bound until the bound passes the
-// best exact area.  Every choice and area is therefore the one the
+// Step 0 runs one streaming pass over all segments: every segment's area
+// sum_p D_s(p) up to FP64 rounding (relative error far below 1e-9), and a
+// sketch of its row over blocks of positions (whole tiles): the block sums and
+// the block's largest and smallest value.  The segments whose area lies within
+// the rounding margin of the best are recomputed exactly (their rows, then the
+// same per-row sum as the materialized path), and the exact minimum wins
+// (lowest index on ties).  From step 1 on, every segment's area is bounded from
+// below, block by block, by what is known of its row: its block minimum and
+// maximum against the current curve M, and, for a row recomputed at an earlier
+// step, its block areas then less the block's drop in M since (M only
+// shrinks).  Segments are recomputed in order of the bound until the bound
+// passes the best exact area.  Every choice and area is therefore the one the
 // materialized search makes.
 // ---------------------------------------------------------------------------
 template <typename real, int V>
@@ -685,23 +687,38 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     Stats* st;
     TRY(ensure_stats(h, q.ell, &st));
     const int ntiles = (int)((P + g.W - 1) / g.W);
-    const int chunk = std::max(1, std::min(S, (int)((size_t)(32u << 20) / (size_t)ntiles)));  // <= 256 MiB of partials
-    // position blocks for the bounds: NB blocks of TB whole tiles (L positions)
-    const int TB = (ntiles + STREAM_NB - 1) / STREAM_NB, NB = (ntiles + TB - 1) / TB;
+    // per-CTA partial sums, maxima and minima of a chunk of segments: <= 256 MiB
+    const int chunk = std::max(1, std::min(S, (int)((size_t)(256u << 20) / ((8 + 2 * rs) * (size_t)ntiles))));
+    // position blocks of TB whole tiles (L positions): as fine as 512 MiB of
+    // sketches and block areas allow (8 + 8 + 2 rs bytes per segment and block)
+    const size_t per_block = (size_t)S * (16 + 2 * rs);
+    const int nb_max = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntiles, ((size_t)512 << 20) / per_block));
+    const int TB = (ntiles + nb_max - 1) / nb_max, NB = (ntiles + TB - 1) / TB;
     const int64_t L = (int64_t)TB * g.W;
-    void *part, *apx, *blk, *keep, *M, *rows, *segs, *rarea, *rblk, *dk, *mblk;
+    void *part, *pmx, *pmn, *apx, *A0, *Ab, *X, *N, *keep, *M, *rows, *segs, *rarea, *rblk, *dk, *mblk;
+    void *Ms, *Mp, *tsd, *tkd, *lbd;
     void *chosen_d, *aafter_d, *counts, *oi, *orank, *ofrac, *oarea, *lab = nullptr;
     TRY(scratch(h, "st_part", 8 * (size_t)chunk * ntiles, &part));
+    TRY(scratch(h, "st_pmx", rs * (size_t)chunk * ntiles, &pmx));
+    TRY(scratch(h, "st_pmn", rs * (size_t)chunk * ntiles, &pmn));
     TRY(scratch(h, "st_apx", 8 * (size_t)S, &apx));
-    TRY(scratch(h, "st_blk", 8 * (size_t)S * NB, &blk));
+    TRY(scratch(h, "st_A0", 8 * (size_t)S * NB, &A0));
+    TRY(scratch(h, "st_Ab", 8 * (size_t)S * NB, &Ab));
+    TRY(scratch(h, "st_X", rs * (size_t)S * NB, &X));
+    TRY(scratch(h, "st_N", rs * (size_t)S * NB, &N));
     TRY(scratch(h, "st_keep", rs * (size_t)K * P, &keep));
     TRY(scratch(h, "st_M", rs * (size_t)P, &M));
+    TRY(scratch(h, "st_Ms", rs * (size_t)P, &Ms));
+    TRY(scratch(h, "st_Mp", 8 * (size_t)P, &Mp));
     TRY(scratch(h, "st_rows", rs * (size_t)BATCH * P, &rows));
     TRY(scratch(h, "st_segs", 4 * BATCH, &segs));
     TRY(scratch(h, "st_rarea", 8 * BATCH, &rarea));
     TRY(scratch(h, "st_rblk", 8 * (size_t)BATCH * NB, &rblk));
+    TRY(scratch(h, "st_ts", 4 * (size_t)S, &tsd));
+    TRY(scratch(h, "st_taken", (size_t)S, &tkd));
+    TRY(scratch(h, "st_lb", 8 * (size_t)S, &lbd));
     TRY(scratch(h, "dmax", 8, &dk));
-    TRY(scratch(h, "st_mblk", 8 * STREAM_NB, &mblk));
+    TRY(scratch(h, "st_mblk", 8 * (size_t)(K + 1) * NB, &mblk));
     TRY(scratch(h, "sn_chosen", 4 * 64, &chosen_d));
     TRY(scratch(h, "sn_aafter", 8 * 64, &aafter_d));
     TRY(scratch(h, "sn_counts", 8 * 64, &counts));
@@ -716,26 +733,28 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     h->launches += 1;
     ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, nullptr, (unsigned long long*)dk);
     int64_t passes = 0, nrows = 0;
-    std::vector<double> hapx(S), hblk((size_t)S * NB), ex(BATCH), exb((size_t)BATCH * NB);
-    // one streaming pass: approximate areas of every segment, whole and per block
-    auto stream_pass = [&](const real* Mc) -> pastila_status {
+    std::vector<double> hapx(S), hlb(S), ex(BATCH);
+    // the one streaming pass (M = +inf): approximate areas and the block sketches
+    {
         ProfileArgs<real> B = A;
-        B.M = Mc;
+        B.M = nullptr;
         B.part = (double*)part;
+        B.pmx = (real*)pmx;
+        B.pmn = (real*)pmn;
         for (int s0 = 0; s0 < S; s0 += chunk) {
             const int ns = std::min(chunk, S - s0);
             stream_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)ns), g.NT, g.bytes, h->stream>>>(B, g, s0);
-            segment_blocks_kernel<<<ns, STREAM_NB, 0, h->stream>>>((const double*)part, ntiles, TB, NB,
-                                                            (double*)blk + (size_t)s0 * NB, (double*)apx + s0);
+            segment_sketch_kernel<real><<<ns, AREA_THREADS, 0, h->stream>>>(
+                (const double*)part, (const real*)pmx, (const real*)pmn, ntiles, TB, NB,
+                (double*)A0 + (size_t)s0 * NB, (real*)X + (size_t)s0 * NB, (real*)N + (size_t)s0 * NB,
+                (double*)apx + s0);
             h->launches += 2;
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(hapx.data(), apx, 8 * (size_t)S, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaMemcpyAsync(hblk.data(), blk, 8 * (size_t)S * NB, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         passes++;
-        return PASTILA_OK;
-    };
+    }
     // exact areas (the materialized path's per-row sums) and block areas of up to BATCH rows
     auto exact = [&](const std::vector<int32_t>& ss, const real* Mc) -> pastila_status {
         const int nb = (int)ss.size();
@@ -749,7 +768,6 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
             (const real*)rows, P, Mc, L, NB, (double*)rblk);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(ex.data(), rarea, 8 * (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
-        CK(cudaMemcpyAsync(exb.data(), rblk, 8 * (size_t)nb * NB, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         h->launches += 3;
         nrows += nb;
@@ -758,61 +776,67 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     const double REL = 1e-9;  // far above the FP64 rounding of these sums
     std::vector<int32_t> chosen;
     std::vector<double> aafter;
-    std::vector<char> taken(S, 0);
-    // per segment: block areas at the step ts[s] they were taken; block sums of M per step
-    std::vector<double> Ab((size_t)S * NB, 0.0), MB((size_t)(K + 1) * NB, 0.0), lb(S);
-    std::vector<int> ts(S, 1);
+    std::vector<unsigned char> taken(S, 0);
+    std::vector<int32_t> ts(S, 0);  // step at which a segment's block areas were last taken (0: only the sketch)
+    std::vector<real> hM;
+    std::vector<double> hMp;
     std::vector<int32_t> order;
     order.reserve(S);
     for (int t = 0; t < K; ++t) {
         const real* Mc = t ? (const real*)M : nullptr;
-        double mtot = 0.0;
-        if (t >= 1) {
-            curve_blocks_kernel<real><<<NB, AREA_THREADS, 0, h->stream>>>((const real*)M, P, L, (double*)mblk);
-            CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(&MB[(size_t)t * NB], mblk, 8 * (size_t)NB, cudaMemcpyDeviceToHost, h->stream));
-            CK(cudaStreamSynchronize(h->stream));
-            h->launches += 1;
-            for (int b = 0; b < NB; ++b) mtot += MB[(size_t)t * NB + b];
-        }
-        if (t <= 1) {
-            TRY(stream_pass(Mc));
-            for (int s = 0; s < S; ++s) lb[s] = hapx[s] - REL * (std::fabs(hapx[s]) + mtot);
-            if (t == 1) Ab = hblk;  // ts = 1 for every segment
+        if (t == 0) {
+            for (int s = 0; s < S; ++s) hlb[s] = hapx[s] - REL * std::fabs(hapx[s]);
         } else {
-            // M only shrinks: a block's area can fall by at most its drop in M, and not below 0
-            for (int s = 0; s < S; ++s) {
-                if (taken[s]) continue;
-                const double* ab = &Ab[(size_t)s * NB];
-                const double* m0 = &MB[(size_t)ts[s] * NB];
-                const double* m1 = &MB[(size_t)t * NB];
-                double v = 0.0, scale = 0.0;
-                for (int b = 0; b < NB; ++b) {
-                    const double x = ab[b] - (m0[b] - m1[b]);
-                    v += x > 0.0 ? x : 0.0;
-                    scale += m0[b];
+            // block sums of M at this step, and M sorted within each block with running sums
+            curve_blocks_kernel<real><<<NB, AREA_THREADS, 0, h->stream>>>((const real*)M, P, L,
+                                                                         (double*)mblk + (size_t)t * NB);
+            CK(cudaGetLastError());
+            h->launches += 1;
+            hM.resize(P);
+            hMp.resize(P);
+            CK(cudaMemcpyAsync(hM.data(), M, rs * (size_t)P, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            for (int b = 0; b < NB; ++b) {
+                const int64_t p0 = (int64_t)b * L, p1 = std::min(P, p0 + L);
+                std::sort(hM.begin() + p0, hM.begin() + p1);
+                double run = 0.0;
+                for (int64_t p = p0; p < p1; ++p) {
+                    run += (double)hM[p];
+                    hMp[p] = run;
                 }
-                lb[s] = v - REL * scale;
             }
+            CK(cudaMemcpyAsync(Ms, hM.data(), rs * (size_t)P, cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(Mp, hMp.data(), 8 * (size_t)P, cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(tsd, ts.data(), 4 * (size_t)S, cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(tkd, taken.data(), (size_t)S, cudaMemcpyHostToDevice, h->stream));
+            stream_bounds_kernel<real><<<S, AREA_THREADS, 0, h->stream>>>(
+                (const double*)A0, (const double*)Ab, (const real*)X, (const real*)N, (const int32_t*)tsd,
+                (const double*)mblk, t, (const real*)Ms, (const double*)Mp, P, L, NB, (const unsigned char*)tkd, REL,
+                (double*)lbd);
+            CK(cudaGetLastError());
+            h->launches += 1;
+            CK(cudaMemcpyAsync(hlb.data(), lbd, 8 * (size_t)S, cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
         }
         order.clear();
         for (int s = 0; s < S; ++s)
             if (!taken[s]) order.push_back(s);
         std::sort(order.begin(), order.end(),
-                  [&](int32_t x, int32_t y) { return lb[x] < lb[y] || (lb[x] == lb[y] && x < y); });
+                  [&](int32_t x, int32_t y) { return hlb[x] < hlb[y] || (hlb[x] == hlb[y] && x < y); });
         double best = std::numeric_limits<double>::infinity();
         int32_t bs = -1;
         size_t i = 0;
         std::vector<int32_t> batch;
-        while (i < order.size() && lb[order[i]] <= best) {
+        while (i < order.size() && hlb[order[i]] <= best) {
             batch.clear();
-            while (i < order.size() && (int)batch.size() < BATCH && lb[order[i]] <= best) batch.push_back(order[i++]);
+            while (i < order.size() && (int)batch.size() < BATCH && hlb[order[i]] <= best) batch.push_back(order[i++]);
             TRY(exact(batch, Mc));
             for (int j = 0; j < (int)batch.size(); ++j) {
                 const int32_t s = batch[j];
                 const double ar = ex[j];
-                if (t >= 1) {
-                    std::copy(exb.begin() + (size_t)j * NB, exb.begin() + (size_t)(j + 1) * NB, Ab.begin() + (size_t)s * NB);
+                if (t >= 1) {  // this row's block areas at step t, for the later bounds
+                    CK(cudaMemcpyAsync((double*)Ab + (size_t)s * NB, (const double*)rblk + (size_t)j * NB,
+                                       8 * (size_t)NB, cudaMemcpyDeviceToDevice, h->stream));
                     ts[s] = t;
                 }
                 if (ar < best || (ar == best && s < bs)) {

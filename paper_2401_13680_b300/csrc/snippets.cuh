@@ -76,35 +76,95 @@ row_area_kernel(const real* __restrict__ rows, int64_t P, const real* __restrict
     if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
-// Position blocks of the greedy search without the profile set: at most
-// STREAM_NB blocks of whole tiles (finer blocks give bounds that are tighter in
-// principle; 256 and 1024 blocks recomputed the same rows as 64 on the n = 10^6
-// drift series).
-#ifndef STREAM_NB
-#define STREAM_NB 64
-#endif
-
-// Block sums of the tile partials: blocks[s][b] = sum of part[s][tile] over the
-// tiles b*TB .. (b+1)*TB-1, in tile order, and tot[s] = the sum of the blocks in
-// order.  Grid (segments), STREAM_NB threads (NB <= STREAM_NB).
-__global__ void __launch_bounds__(STREAM_NB) segment_blocks_kernel(const double* __restrict__ part, int ntiles, int TB,
-                                                                   int NB, double* __restrict__ blocks,
-                                                                   double* __restrict__ tot) {
-    __shared__ double bs[STREAM_NB];
-    const int s = blockIdx.x, b = threadIdx.x;
-    double acc = 0.0;
-    if (b < NB) {
-        const int t1 = (b + 1) * TB < ntiles ? (b + 1) * TB : ntiles;
-        for (int t = b * TB; t < t1; ++t) acc += part[(int64_t)s * ntiles + t];
-        blocks[(int64_t)s * NB + b] = acc;
+// Block sketches of one streaming pass, for the segments of a chunk: over the
+// tiles b TB .. (b+1) TB - 1 of segment s, the sum of the tiles' partial areas
+// (A0, in tile order) and the largest and smallest profile value (X, N), from
+// the per-CTA values of the pass; tot[s] = the block sums added in block order.
+// Grid (segments), AREA_THREADS threads.
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS)
+segment_sketch_kernel(const double* __restrict__ part, const real* __restrict__ pmx, const real* __restrict__ pmn,
+                      int ntiles, int TB, int NB, double* __restrict__ A0, real* __restrict__ X, real* __restrict__ N,
+                      double* __restrict__ tot) {
+    const int s = blockIdx.x;
+    const int64_t rt = (int64_t)s * ntiles, rb = (int64_t)s * NB;
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+        const int t0 = b * TB, t1 = (b + 1) * TB < ntiles ? (b + 1) * TB : ntiles;
+        double acc = 0.0;
+        real mx = pmx[rt + t0], mn = pmn[rt + t0];
+        for (int t = t0; t < t1; ++t) {
+            acc += part[rt + t];
+            mx = pmx[rt + t] > mx ? pmx[rt + t] : mx;
+            mn = pmn[rt + t] < mn ? pmn[rt + t] : mn;
+        }
+        A0[rb + b] = acc;
+        X[rb + b] = mx;
+        N[rb + b] = mn;
     }
-    bs[b] = acc;
     __syncthreads();
-    if (b == 0) {
+    if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int i = 0; i < NB; ++i) t += bs[i];
+        for (int b = 0; b < NB; ++b) t += A0[rb + b];
         tot[s] = t;
     }
+}
+
+// Lower bounds on the greedy areas sum_p min(M_p, D_s(p)) of step t (eq. 17)
+// for segments whose rows are not at hand, block by block (blocks of L
+// positions; Ms: the block's values of M sorted ascending, Mp: their running
+// sums within the block):
+//   D_s >= N_sb on the block:  sum min(M, D_s) >= sum min(M, N_sb)
+//   D_s <= X_sb on the block:  sum min(M, D_s) = sum D_s - sum max(0, D_s - M)
+//                                             >= A0_sb - sum max(0, X_sb - M)
+//   block area Ab_sb known from step ts_s >= 1 (M only shrinks after it):
+//                              sum min(M_t, D_s) >= Ab_sb - (MB_ts,b - MB_t,b)
+// each also >= 0.  lb[s] = the sum over blocks of the largest of these, less
+// rel times the magnitude of the sums involved (their FP64 rounding); taken
+// segments get +inf.  Grid (S), AREA_THREADS threads.
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS)
+stream_bounds_kernel(const double* __restrict__ A0, const double* __restrict__ Ab, const real* __restrict__ X,
+                     const real* __restrict__ N, const int32_t* __restrict__ ts, const double* __restrict__ MB, int t,
+                     const real* __restrict__ Ms, const double* __restrict__ Mp, int64_t P, int64_t L, int NB,
+                     const unsigned char* __restrict__ taken, double rel, double* __restrict__ lb) {
+    __shared__ double red[AREA_THREADS / 32], red2[AREA_THREADS / 32];
+    const int s = blockIdx.x;
+    if (taken[s]) {
+        if (threadIdx.x == 0) lb[s] = __longlong_as_double(0x7ff0000000000000ll);
+        return;
+    }
+    const int tss = ts[s];
+    const int64_t rb = (int64_t)s * NB;
+    double acc = 0.0, scale = 0.0;
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+        const int64_t p0 = (int64_t)b * L;
+        const int64_t Lb = p0 + L < P ? L : P - p0;
+        const real* ms = Ms + p0;
+        const double* mp = Mp + p0;
+        auto below = [&](real v) {  // #{M < v} in the block
+            int64_t lo = 0, hi = Lb;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (ms[mid] < v) lo = mid + 1; else hi = mid;
+            }
+            return lo;
+        };
+        const real n = N[rb + b], x = X[rb + b];
+        const int64_t k1 = below(n), k2 = below(x);
+        const double s1 = k1 ? mp[k1 - 1] : 0.0, s2 = k2 ? mp[k2 - 1] : 0.0;
+        const double lbA = s1 + (double)n * (double)(Lb - k1);
+        const double lbB = A0[rb + b] - ((double)x * (double)k2 - s2);
+        double v = lbA > lbB ? lbA : lbB;
+        if (tss >= 1) {
+            const double lbD = Ab[rb + b] - (MB[(int64_t)tss * NB + b] - MB[(int64_t)t * NB + b]);
+            v = lbD > v ? lbD : v;
+        }
+        acc += v > 0.0 ? v : 0.0;
+        scale += A0[rb + b] + MB[(int64_t)t * NB + b] + (tss >= 1 ? MB[(int64_t)tss * NB + b] : 0.0);
+    }
+    const double tot = block_sum(acc, red);
+    const double sc = block_sum(scale, red2);
+    if (threadIdx.x == 0) lb[s] = tot - rel * sc;
 }
 
 // out[y][b] = sum over positions b*L .. min(P, (b+1)*L) - 1 of min(M_p, rows[y][p])

@@ -102,9 +102,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 template <typename real> struct RealLimits;
 template <> struct RealLimits<float> {
     __host__ __device__ static constexpr float lowest() { return -FLT_MAX; }
+    __host__ __device__ static constexpr float max() { return FLT_MAX; }
 };
 template <> struct RealLimits<double> {
     __host__ __device__ static constexpr double lowest() { return -DBL_MAX; }
+    __host__ __device__ static constexpr double max() { return DBL_MAX; }
 };
 
 template <typename real>
@@ -128,6 +130,11 @@ struct ProfileArgs {
     // areas without D
     const real* M;
     double* part;
+    // with part: when pmx is not null, every CTA also writes the largest and the
+    // smallest D_s(p) over its positions to pmx / pmn at the same index (the
+    // sketch that bounds later greedy areas without recomputing the rows)
+    real* pmx;
+    real* pmn;
     // bounded waits: the staging wait gives up after spin_limit SM cycles and
     // then stores 1 to *err (host-visible); test_timeout is 0, and 1 only in
     // the test that makes the wait run out (a second wait, on the barrier's
@@ -1100,6 +1107,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int kk = 2 * R > A.k ? A.k : 2 * R;
     const real two_ell = (real)(2 * ell);
     real tmax = 0;
+    real tmin = RealLimits<real>::max();
     real* Drow = A.D + (int64_t)(s - row_base) * A.P + p0;  // row s - row_base of the output
     const bool streaming = A.part != nullptr;
     double sacc = 0.0;
@@ -1110,6 +1118,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         if (streaming) {
             const real mm = A.M ? A.M[p0 + p] : d;
             sacc += (double)(d < mm ? d : mm);
+            tmin = d < tmin ? d : tmin;
         } else {
             Drow[p] = d;
         }
@@ -1141,14 +1150,30 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(wmax));
     if (streaming) {  // this tile's area share: warps in order, then one store
         __shared__ double red[16];
+        __shared__ real rmx[16], rmn[16];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(FULL, sacc, o);
-        if (lane == 0) red[tid >> 5] = sacc;
+        const real wmn = warp_min(tmin);
+        if (lane == 0) {
+            red[tid >> 5] = sacc;
+            rmx[tid >> 5] = (real)wmax;
+            rmn[tid >> 5] = wmn;
+        }
         __syncthreads();
         if (tid == 0) {
             double tot = 0.0;
-            for (int w = 0; w < (BD >> 5); ++w) tot += red[w];
-            A.part[((int64_t)(s - row_base) * A.ntiles + tt) * CS + crank] = tot;
+            real mx = rmx[0], mn = rmn[0];
+            for (int w = 0; w < (BD >> 5); ++w) {
+                tot += red[w];
+                mx = rmx[w] > mx ? rmx[w] : mx;
+                mn = rmn[w] < mn ? rmn[w] : mn;
+            }
+            const int64_t idx = ((int64_t)(s - row_base) * A.ntiles + tt) * CS + crank;
+            A.part[idx] = tot;
+            if (A.pmx) {
+                A.pmx[idx] = mx;
+                A.pmn[idx] = mn;
+            }
         }
     }
 }

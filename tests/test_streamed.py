@@ -1,7 +1,7 @@
 """The greedy snippet search without the profile set (pastila_snippets_streamed
 and the automatic switch to it in pastila_snippets): the same records, labels
 and chosen profiles as the search on the materialised D, bit for bit, with
-two full passes over the segments and a few recomputed rows."""
+one full pass over the segments and a few recomputed rows."""
 import numpy as np
 import pytest
 
@@ -35,7 +35,7 @@ def test_streamed_equals_materialised(lib, prec):
         ref, got = _both(pastila, T, m, K, prec)
         _same(ref, got)
         passes, rows = got[3]
-        assert passes == min(K, 2)
+        assert passes == 1
         assert rows >= K
         S = T.shape[0] // m
         assert rows <= K * S  # never more than the materialised search's rows
