@@ -392,7 +392,9 @@ pastila_status pastila_model_predict(pastila_precision prec, int64_t n, const in
  * its sum, largest and smallest value), then, at every step, only the rows
  * whose lower area bound can still beat the best (from the sketch against the
  * current curve M, and, for a row recomputed earlier, its block areas then
- * less the block's drop in M since).  Memory: K + 10 rows of P values and P doubles, at
+ * less the block's drop in M since); a step whose bounds leave more than half
+ * of the segments open makes one more pass instead.  It uses the tile layout
+ * pastila_snippets uses.  Memory: K + 10 rows of P values and P doubles, at
  * most 256 MiB of per-tile partials and 512 MiB of sketches and block areas
  * (the blocks are as fine as that allows, down to one tile).  Results
  * (records, labels, chosen profiles) are

@@ -681,26 +681,29 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     const int S = q.S;
     const int64_t P = q.P;
     const size_t rs = sizeof(real);
-    constexpr int BATCH = 8;
     TileGeom g;
-    TRY(choose_tile<real, V>(h, q, &g, false));  // one-CTA tiles: per-tile partial sums
+    TRY(choose_tile<real, V>(h, q, &g));  // the layout pastila_snippets uses: the same D to the last bit
     Stats* st;
     TRY(ensure_stats(h, q.ell, &st));
     const int ntiles = (int)((P + g.W - 1) / g.W);
+    const int CS = g.CS;
+    const int ne = ntiles * CS;  // CTA entries per segment: CTA c of tile t covers its positions c Wc ..
     // per-CTA partial sums, maxima and minima of a chunk of segments: <= 256 MiB
-    const int chunk = std::max(1, std::min(S, (int)((size_t)(256u << 20) / ((8 + 2 * rs) * (size_t)ntiles))));
+    const int chunk = std::max(1, std::min(S, (int)((size_t)(256u << 20) / ((8 + 2 * rs) * (size_t)ne))));
     // position blocks of TB whole tiles (L positions): as fine as 512 MiB of
     // sketches and block areas allow (8 + 8 + 2 rs bytes per segment and block)
     const size_t per_block = (size_t)S * (16 + 2 * rs);
     const int nb_max = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntiles, ((size_t)512 << 20) / per_block));
     const int TB = (ntiles + nb_max - 1) / nb_max, NB = (ntiles + TB - 1) / TB;
     const int64_t L = (int64_t)TB * g.W;
+    // rows recomputed per batch: 8 at first, doubling up to BMAX (<= 256 MiB of rows)
+    const int BMAX = (int)std::max<int64_t>(8, std::min<int64_t>(32, ((int64_t)256 << 20) / ((int64_t)rs * P)));
     void *part, *pmx, *pmn, *apx, *A0, *Ab, *X, *N, *keep, *M, *rows, *segs, *rarea, *rblk, *dk, *mblk;
     void *Ms, *Mp, *tsd, *tkd, *lbd;
     void *chosen_d, *aafter_d, *counts, *oi, *orank, *ofrac, *oarea, *lab = nullptr;
-    TRY(scratch(h, "st_part", 8 * (size_t)chunk * ntiles, &part));
-    TRY(scratch(h, "st_pmx", rs * (size_t)chunk * ntiles, &pmx));
-    TRY(scratch(h, "st_pmn", rs * (size_t)chunk * ntiles, &pmn));
+    TRY(scratch(h, "st_part", 8 * (size_t)chunk * ne, &part));
+    TRY(scratch(h, "st_pmx", rs * (size_t)chunk * ne, &pmx));
+    TRY(scratch(h, "st_pmn", rs * (size_t)chunk * ne, &pmn));
     TRY(scratch(h, "st_apx", 8 * (size_t)S, &apx));
     TRY(scratch(h, "st_A0", 8 * (size_t)S * NB, &A0));
     TRY(scratch(h, "st_Ab", 8 * (size_t)S * NB, &Ab));
@@ -710,10 +713,10 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     TRY(scratch(h, "st_M", rs * (size_t)P, &M));
     TRY(scratch(h, "st_Ms", rs * (size_t)P, &Ms));
     TRY(scratch(h, "st_Mp", 8 * (size_t)P, &Mp));
-    TRY(scratch(h, "st_rows", rs * (size_t)BATCH * P, &rows));
-    TRY(scratch(h, "st_segs", 4 * BATCH, &segs));
-    TRY(scratch(h, "st_rarea", 8 * BATCH, &rarea));
-    TRY(scratch(h, "st_rblk", 8 * (size_t)BATCH * NB, &rblk));
+    TRY(scratch(h, "st_rows", rs * (size_t)BMAX * P, &rows));
+    TRY(scratch(h, "st_segs", 4 * (size_t)BMAX, &segs));
+    TRY(scratch(h, "st_rarea", 8 * (size_t)BMAX, &rarea));
+    TRY(scratch(h, "st_rblk", 8 * (size_t)BMAX * NB, &rblk));
     TRY(scratch(h, "st_ts", 4 * (size_t)S, &tsd));
     TRY(scratch(h, "st_taken", (size_t)S, &tkd));
     TRY(scratch(h, "st_lb", 8 * (size_t)S, &lbd));
@@ -733,36 +736,40 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     h->launches += 1;
     ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, nullptr, (unsigned long long*)dk);
     int64_t passes = 0, nrows = 0;
-    std::vector<double> hapx(S), hlb(S), ex(BATCH);
-    // the one streaming pass (M = +inf): approximate areas and the block sketches
-    {
+    std::vector<double> hapx(S), hlb(S), ex(BMAX);
+    // a streaming pass over every segment with the curve Mc (nullptr: +inf):
+    // approximate areas (hapx), their block sums into blocks, and the block
+    // sketches X, N (the same at every pass: D does not change)
+    auto pass = [&](const real* Mc, double* blocks) -> pastila_status {
         ProfileArgs<real> B = A;
-        B.M = nullptr;
+        B.M = Mc;
         B.part = (double*)part;
         B.pmx = (real*)pmx;
         B.pmn = (real*)pmn;
         for (int s0 = 0; s0 < S; s0 += chunk) {
             const int ns = std::min(chunk, S - s0);
-            stream_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)ns), g.NT, g.bytes, h->stream>>>(B, g, s0);
+            CK(launch_tiles(stream_tiles_kernel<real, V>, dim3((unsigned)ne, (unsigned)ns), g.NT, g.bytes, h->stream,
+                            CS, B, g, s0));
             segment_sketch_kernel<real><<<ns, AREA_THREADS, 0, h->stream>>>(
-                (const double*)part, (const real*)pmx, (const real*)pmn, ntiles, TB, NB,
-                (double*)A0 + (size_t)s0 * NB, (real*)X + (size_t)s0 * NB, (real*)N + (size_t)s0 * NB,
-                (double*)apx + s0);
+                (const double*)part, (const real*)pmx, (const real*)pmn, ne, TB * CS, NB, blocks + (size_t)s0 * NB,
+                (real*)X + (size_t)s0 * NB, (real*)N + (size_t)s0 * NB, (double*)apx + s0);
             h->launches += 2;
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(hapx.data(), apx, 8 * (size_t)S, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         passes++;
-    }
-    // exact areas (the materialized path's per-row sums) and block areas of up to BATCH rows
+        return PASTILA_OK;
+    };
+    TRY(pass(nullptr, (double*)A0));  // step 0: the row sums and the sketches
+    // exact areas (the materialized path's per-row sums) and block areas of up to BMAX rows
     auto exact = [&](const std::vector<int32_t>& ss, const real* Mc) -> pastila_status {
         const int nb = (int)ss.size();
         CK(cudaMemcpyAsync(segs, ss.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, h->stream));
         ProfileArgs<real> B = A;
         B.D = (real*)rows;
-        rows_tiles_kernel<real, V><<<dim3((unsigned)ntiles, (unsigned)nb), g.NT, g.bytes, h->stream>>>(
-            B, g, (const int32_t*)segs);
+        CK(launch_tiles(rows_tiles_kernel<real, V>, dim3((unsigned)ne, (unsigned)nb), g.NT, g.bytes, h->stream, CS, B,
+                        g, (const int32_t*)segs));
         row_area_kernel<real><<<nb, AREA_THREADS, 0, h->stream>>>((const real*)rows, P, Mc, (double*)rarea);
         row_blocks_kernel<real><<<dim3((unsigned)NB, (unsigned)nb), AREA_THREADS, 0, h->stream>>>(
             (const real*)rows, P, Mc, L, NB, (double*)rblk);
@@ -821,16 +828,19 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
         order.clear();
         for (int s = 0; s < S; ++s)
             if (!taken[s]) order.push_back(s);
-        std::sort(order.begin(), order.end(),
-                  [&](int32_t x, int32_t y) { return hlb[x] < hlb[y] || (hlb[x] == hlb[y] && x < y); });
+        auto by_bound = [&](int32_t x, int32_t y) { return hlb[x] < hlb[y] || (hlb[x] == hlb[y] && x < y); };
+        std::sort(order.begin(), order.end(), by_bound);
         double best = std::numeric_limits<double>::infinity();
         int32_t bs = -1;
         size_t i = 0;
+        int bsz = 8;
+        bool passed = t == 0;  // step 0 had its pass
         std::vector<int32_t> batch;
         while (i < order.size() && hlb[order[i]] <= best) {
             batch.clear();
-            while (i < order.size() && (int)batch.size() < BATCH && hlb[order[i]] <= best) batch.push_back(order[i++]);
+            while (i < order.size() && (int)batch.size() < bsz && hlb[order[i]] <= best) batch.push_back(order[i++]);
             TRY(exact(batch, Mc));
+            bsz = std::min(2 * bsz, BMAX);
             for (int j = 0; j < (int)batch.size(); ++j) {
                 const int32_t s = batch[j];
                 const double ar = ex[j];
@@ -839,11 +849,32 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
                                        8 * (size_t)NB, cudaMemcpyDeviceToDevice, h->stream));
                     ts[s] = t;
                 }
+                hlb[s] = std::numeric_limits<double>::infinity();  // settled at this step
                 if (ar < best || (ar == best && s < bs)) {
                     best = ar;
                     bs = s;
                     CK(cudaMemcpyAsync((char*)keep + rs * (size_t)t * P, (const char*)rows + rs * (size_t)j * P,
                                        rs * (size_t)P, cudaMemcpyDeviceToDevice, h->stream));
+                }
+            }
+            // when the bounds leave more than half of the segments open, one pass
+            // over all of them costs less than recomputing those rows one by one:
+            // it gives every area up to rounding and every block area at step t
+            if (!passed) {
+                size_t open = 0;
+                for (size_t u = i; u < order.size() && hlb[order[u]] <= best; ++u) ++open;
+                if (2 * open > (size_t)S) {
+                    TRY(pass(Mc, (double*)Ab));
+                    passed = true;
+                    for (int s = 0; s < S; ++s) {
+                        if (taken[s]) continue;
+                        ts[s] = t;
+                        if (std::isfinite(hlb[s])) hlb[s] = hapx[s] - REL * std::fabs(hapx[s]);
+                    }
+                    std::vector<int32_t> rest(order.begin() + i, order.end());
+                    std::sort(rest.begin(), rest.end(), by_bound);
+                    order.swap(rest);
+                    i = 0;
                 }
             }
         }

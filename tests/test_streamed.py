@@ -1,7 +1,9 @@
 """The greedy snippet search without the profile set (pastila_snippets_streamed
 and the automatic switch to it in pastila_snippets): the same records, labels
-and chosen profiles as the search on the materialised D, bit for bit, with
-one full pass over the segments and a few recomputed rows."""
+and chosen profiles as the search on the materialised D, bit for bit (the
+same tile layout, cluster tiles included), with one full pass over the
+segments and few recomputed rows where the area bounds prune, and a further
+pass at a step where they leave more than half of the segments open."""
 import numpy as np
 import pytest
 
@@ -35,7 +37,7 @@ def test_streamed_equals_materialised(lib, prec):
         ref, got = _both(pastila, T, m, K, prec)
         _same(ref, got)
         passes, rows = got[3]
-        assert passes == 1
+        assert 1 <= passes <= K
         assert rows >= K
         S = T.shape[0] // m
         assert rows <= K * S  # never more than the materialised search's rows
@@ -50,6 +52,8 @@ def test_streamed_exact_ties(lib):
     ref, got = _both(pastila, T, 128, 3, 0)
     _same(ref, got)
     assert [r[0] for r in sorted(got[0], key=lambda r: r[1])] == [0, 1, 2]
+    # no bound can separate equal areas: steps 1 and 2 fall back to a pass
+    assert got[3][0] == 3
 
 
 def test_snippets_switches_to_streaming_when_d_does_not_fit(lib):
@@ -75,3 +79,21 @@ def test_streamed_on_ecg_like_series(lib):
     s = synth.ecg_like(n=200_000)
     ref, got = _both(pastila, s.T, 256, 8, 0)
     _same(ref, got)
+
+
+def test_streamed_with_cluster_tiles(lib):
+    """With a two-CTA cluster layout in force the streamed search uses it too,
+    and its results stay those of the materialised search."""
+    from paper_2401_13680_b300 import pastila
+    rng = np.random.default_rng(8)
+    T = synth.random_planted(rng, 30_000, 5).T
+    m, K = 256, 5
+    pastila.tune_clear()
+    try:
+        pastila.tune_set(pastila.FP32, m, m // 2, (m + 9) // 10, 256, 2, 16, 2)
+        with pastila.Series(T, precision=pastila.FP32) as h:
+            assert h.tile_layout(m)["CS"] == 2
+        ref, got = _both(pastila, T, m, K, 0)
+        _same(ref, got)
+    finally:
+        pastila.tune_clear()
