@@ -1227,7 +1227,7 @@ pastila_status pastila_engine_poll(pastila_engine* e, int64_t job, int32_t timeo
     g_err.clear();
     if (!e) return fail(PASTILA_EINVAL, "engine is NULL");
     std::unique_lock<std::mutex> lk(e->mu);
-    EJob* j;
+    EJob* j = nullptr;
     TRY(engine_job(e, job, &j));
     if (timeout_ms != 0 && !job_final(*j)) {
         auto pred = [&] { return job_final(*j); };
@@ -1259,7 +1259,7 @@ pastila_status pastila_engine_result(pastila_engine* e, int64_t job, int32_t* m_
     g_err.clear();
     if (!e) return fail(PASTILA_EINVAL, "engine is NULL");
     std::lock_guard<std::mutex> lk(e->mu);
-    EJob* j;
+    EJob* j = nullptr;
     TRY(engine_job(e, job, &j));
     if (!job_final(*j)) return fail(PASTILA_EBUSY, "job %lld has not finished", (long long)job);
     if (j->state == PASTILA_JOB_CANCELLED) return fail(PASTILA_ECANCELLED, "job %lld was cancelled", (long long)job);
@@ -1274,7 +1274,7 @@ pastila_status pastila_engine_cancel(pastila_engine* e, int64_t job) {
     g_err.clear();
     if (!e) return fail(PASTILA_EINVAL, "engine is NULL");
     std::lock_guard<std::mutex> lk(e->mu);
-    EJob* j;
+    EJob* j = nullptr;
     TRY(engine_job(e, job, &j));
     if (job_final(*j) || j->finalizing)
         return fail(PASTILA_EINVAL, "job %lld has finished or is finishing", (long long)job);
@@ -1287,7 +1287,7 @@ pastila_status pastila_engine_release(pastila_engine* e, int64_t job) {
     g_err.clear();
     if (!e) return fail(PASTILA_EINVAL, "engine is NULL");
     std::lock_guard<std::mutex> lk(e->mu);
-    EJob* j;
+    EJob* j = nullptr;
     TRY(engine_job(e, job, &j));
     if (!job_final(*j)) return fail(PASTILA_EBUSY, "job %lld has not finished", (long long)job);
     e->jobs.erase(job);
