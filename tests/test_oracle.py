@@ -1,7 +1,6 @@
 """Pins of the FP64 oracle against things other than itself: library routines
 (numpy / scipy), brute force on tiny inputs, closed forms, special cases and
 invariants the definitions imply.  CPU only."""
-import itertools
 import math
 
 import numpy as np
