@@ -66,7 +66,7 @@ typedef enum {
 } pastila_precision;
 
 /* MPdist parameters of one snippet length m.  ell = 0 selects m / 2 and k = 0
- * selects ceil(0.05 * 2m) = (m + 9) / 10, the paper's "5 % of 2m" (Section 4.1). */
+ * selects ceil(0.05 * 2m) = (m + 9) / 10, five per cent of 2m (Section 4.1). */
 typedef struct {
     int32_t ell;
     int32_t k;
