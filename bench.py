@@ -387,6 +387,7 @@ def run_ours(args):
     tile_s = tile_ms / 1e3
     achieved = FLOP_PER_ED_CELL * ed_cells * args.steps / tile_s / 1e12
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fma32, fma64 = pastila.probe_fma(local)  # measured FMA rates, outside every timed region
     # DRAM bytes of one sweep's tile launches, from an ncu capture of the current
     # kernel (read + write; the algorithmic bytes are the profile set D, 2.97 GB)
     traffic = SWEEP_TILE_DRAM_BYTES if ms == synth.sweep_lengths() else None
@@ -400,7 +401,11 @@ def run_ours(args):
                 "tile_share_of_step": tile_s / tot_s if world == 1 else None,
                 "halo_factor": tile_cells_halo / (ed_cells * args.steps),
                 "issue_active_ncu": dict(TILE_ISSUE_ACTIVE, source="profiles/tile_kernel_six_regime_m128.md, "
-                                                                   "profiles/tile_kernel_six_regime_m512_cluster.md")}
+                                                                   "profiles/tile_kernel_six_regime_m512_cluster.md"),
+                "fma_measured_tflops": {"fp32": fma32, "fp64": fma64,
+                                        "basis": "pastila_probe_fma: 8 independent FMA chains per thread, "
+                                                 "148 x 8 CTAs of 256 threads, events"},
+                "frac_of_measured_fp32_fma": achieved / fma32 if fma32 else None}
 
     # ---- the plain FP64 one-job GPU path on the same workload (one step)
     fp64 = None

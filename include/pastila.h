@@ -485,6 +485,17 @@ pastila_status pastila_set_timing(pastila_series* h, int on);
  * Waits for the handle's stream.  Any output may be NULL. */
 pastila_status pastila_tile_time(pastila_series* h, double* ms, int64_t* launches, double* ed_cells);
 
+/* -------------------------------------------------------------- probe ---- */
+
+/* Measured fused multiply-add rates of `device`, in TFLOP/s (2 FLOP per FMA):
+ * a kernel of eight independent FMA chains per thread over 148 x 8 CTAs of 256
+ * threads, timed with events after a warm-up launch, in FP32 and in FP64.
+ * The roofline of the profile kernel, which is bound by FP32/integer issue
+ * rather than by memory or tensor cores, can be read against these.  No
+ * counterpart in the paper.  Allocates and frees a small output buffer.
+ * Errors: EINVAL, ECUDA. */
+pastila_status pastila_probe_fma(int32_t device, double* fp32_tflops, double* fp64_tflops);
+
 #ifdef __cplusplus
 }
 #endif

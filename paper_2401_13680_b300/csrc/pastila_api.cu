@@ -18,6 +18,7 @@
 #include "../../include/pastila.h"
 #include "batch.cuh"
 #include "keys.cuh"
+#include "probe.cuh"
 #include "snippets.cuh"
 #include "stats.cuh"
 #include "tile.cuh"
@@ -1683,5 +1684,46 @@ extern "C" pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, 
         if (t + 1 < K) update_curve_kernel<float><<<pb, 256, 0, st>>>(D_dev, P, chosen_dev, t, M);
     }
     CK(cudaGetLastError());
+    return PASTILA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Measured FMA rates (the roofline denominators of an ALU-bound kernel).
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+pastila_status fma_rate(int iters, double* tflops) {
+    const int blocks = 148 * 8, threads = 256;
+    T* out = nullptr;
+    CK(cudaMalloc((void**)&out, sizeof(T) * (size_t)blocks * threads));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fma_probe_kernel<T><<<blocks, threads>>>(out, 8, (T)1);  // warm-up
+    cudaEventRecord(e0);
+    fma_probe_kernel<T><<<blocks, threads>>>(out, iters, (T)1);
+    cudaEventRecord(e1);
+    cudaError_t r = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (r != cudaSuccess) return fail(PASTILA_ECUDA, "fma probe: %s", cudaGetErrorString(r));
+    const double fmas = (double)blocks * threads * iters * 16.0 * PROBE_CHAINS;
+    *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
+    return PASTILA_OK;
+}
+}  // namespace
+
+extern "C" pastila_status pastila_probe_fma(int32_t device, double* fp32_tflops, double* fp64_tflops) {
+    g_err.clear();
+    if (!fp32_tflops || !fp64_tflops) return fail(PASTILA_EINVAL, "output pointers must not be NULL");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(PASTILA_EINVAL, "device %d: %d device(s) visible", device, ndev);
+    CK(cudaSetDevice(device));
+    TRY(fma_rate<float>(4096, fp32_tflops));
+    TRY(fma_rate<double>(64, fp64_tflops));
     return PASTILA_OK;
 }

@@ -157,6 +157,9 @@ def load(path: str | None = None):
         lib.pastila_engine_stats.restype = S
         lib.pastila_engine_destroy.argtypes = [_vp]
         lib.pastila_engine_destroy.restype = None
+        lib.pastila_probe_fma.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+        lib.pastila_probe_fma.restype = S
         lib.pastila_model_get.argtypes = [ctypes.c_int, ctypes.POINTER(RuntimeModel)]
         lib.pastila_model_get.restype = S
         lib.pastila_model_set.argtypes = [ctypes.POINTER(RuntimeModel)]
@@ -410,6 +413,13 @@ def plan_layout(precision: int, n: int, m: int, smem_limit: int, ell: int = 0, k
     out = np.zeros(8, dtype=np.int32)
     _check(load().pastila_plan_layout(precision, n, m, MParams(ell, k), smem_limit, _ptr(out)))
     return dict(zip(("W", "NG", "NT", "GS", "CS", "Rg", "Rh", "bytes"), (int(x) for x in out)))
+
+
+def probe_fma(device: int = 0) -> tuple:
+    """``pastila_probe_fma``: measured (FP32, FP64) FMA rates in TFLOP/s."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    _check(load().pastila_probe_fma(device, ctypes.byref(f32), ctypes.byref(f64)))
+    return f32.value, f64.value
 
 
 def model_get(precision: int) -> dict:
