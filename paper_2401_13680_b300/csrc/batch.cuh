@@ -77,18 +77,7 @@ __global__ void __launch_bounds__(AREA_THREADS) batched_area_kernel(const BatchI
         if (threadIdx.x == 0) it.area[s] = __longlong_as_double(0x7ff0000000000000ll);
         return;
     }
-    const real* row = it.A.D + (int64_t)s * P;
-    double acc = 0.0;
-    if (t == 0) {
-        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += (double)row[p];
-    } else {
-        const real* M = it.M;
-        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) {
-            const real d = row[p], mm = M[p];
-            acc += (double)(d < mm ? d : mm);
-        }
-    }
-    const double tot = block_sum(acc, red);
+    const double tot = block_sum(row_min_partial(it.A.D + (int64_t)s * P, t == 0 ? (const real*)nullptr : it.M, P), red);
     if (threadIdx.x == 0) it.area[s] = tot;
 }
 

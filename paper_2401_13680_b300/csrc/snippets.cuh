@@ -26,6 +26,43 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return t;  // valid in thread 0
 }
 
+// This thread's share of sum_p min(M_p, row[p]) (M = nullptr: of row[p]) in a
+// CTA of AREA_THREADS: positions tid, tid + AREA_THREADS, ... into four FP64
+// accumulators in turn (four independent add chains), added pairwise at the
+// end.  The areas stay FP64 sums (the precision plan keeps FP64 for them); on
+// this GPU the FP64 adds and the conversions they need, not the memory, set
+// the kernel's speed.  Every greedy area of the library goes through this one
+// function, so the same row gives the same sum to the last bit in every path.
+template <typename real>
+__device__ __forceinline__ double row_min_partial(const real* __restrict__ row, const real* __restrict__ M,
+                                                  int64_t P) {
+    constexpr int64_t st = AREA_THREADS;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t p = threadIdx.x;
+    if (M == nullptr) {
+        for (; p + 3 * st < P; p += 4 * st) {
+            a0 += (double)row[p];
+            a1 += (double)row[p + st];
+            a2 += (double)row[p + 2 * st];
+            a3 += (double)row[p + 3 * st];
+        }
+        for (; p < P; p += st) a0 += (double)row[p];
+    } else {
+        auto mn = [&](int64_t q) {
+            const real d = row[q], mm = M[q];
+            return (double)(d < mm ? d : mm);
+        };
+        for (; p + 3 * st < P; p += 4 * st) {
+            a0 += mn(p);
+            a1 += mn(p + st);
+            a2 += mn(p + 2 * st);
+            a3 += mn(p + 3 * st);
+        }
+        for (; p < P; p += st) a0 += mn(p);
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
 // area[s] = sum_p min(M_p, D_s(p)) for every segment s (M = +inf on the first
 // step, so the area is the row sum).  One CTA per segment; chosen segments are
 // skipped and get +inf.  Grid: (S).
@@ -41,17 +78,7 @@ area_kernel(const real* __restrict__ D, int S, int64_t P, const real* __restrict
         if (threadIdx.x == 0) area[s] = __longlong_as_double(0x7ff0000000000000ll);
         return;
     }
-    const real* row = D + (int64_t)s * P;
-    double acc = 0.0;
-    if (M == nullptr) {
-        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += (double)row[p];
-    } else {
-        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) {
-            const real d = row[p], mm = M[p];
-            acc += (double)(d < mm ? d : mm);
-        }
-    }
-    const double tot = block_sum(acc, red);
+    const double tot = block_sum(row_min_partial(D + (int64_t)s * P, M, P), red);
     if (threadIdx.x == 0) area[s] = tot;
 }
 
@@ -62,17 +89,7 @@ template <typename real>
 __global__ void __launch_bounds__(AREA_THREADS)
 row_area_kernel(const real* __restrict__ rows, int64_t P, const real* __restrict__ M, double* __restrict__ out) {
     __shared__ double red[AREA_THREADS / 32];
-    const real* row = rows + (int64_t)blockIdx.x * P;
-    double acc = 0.0;
-    if (M == nullptr) {
-        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += (double)row[p];
-    } else {
-        for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) {
-            const real d = row[p], mm = M[p];
-            acc += (double)(d < mm ? d : mm);
-        }
-    }
-    const double tot = block_sum(acc, red);
+    const double tot = block_sum(row_min_partial(rows + (int64_t)blockIdx.x * P, M, P), red);
     if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
