@@ -26,12 +26,34 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return t;  // valid in thread 0
 }
 
+// Exact widening of a binary32 value to binary64 (IEEE 754: every binary32
+// value is a binary64 value) by moving its fields with integer operations:
+// the sign stays, the exponent is rebiased by 1023 - 127 = 896, the 23
+// fraction bits move to the top of the 52.  A subnormal input is first scaled
+// by 2^24 in binary32 (exact, the result is normal) and rebiased by 896 - 24;
+// zeros keep only their sign; infinities and NaNs get the all-ones exponent.
+// The FP32 area sums use it instead of a conversion instruction, which on this
+// GPU issues on the FP64 pipe, as slowly as the FP64 add itself.
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u0 = __float_as_uint(f);
+    const uint32_t e0 = u0 & 0x7F800000u;
+    const bool sub = e0 == 0u;
+    const uint32_t u = sub ? __float_as_uint(f * 16777216.0f) : u0;
+    const uint32_t mag = u & 0x7FFFFFFFu;
+    uint32_t hi = (mag >> 3) + ((sub ? 872u : 896u) << 20);
+    if (e0 == 0x7F800000u) hi = 0x7FF00000u | ((mag & 0x007FFFFFu) >> 3);
+    if (mag == 0u) hi = 0u;
+    hi |= u0 & 0x80000000u;
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // This thread's share of sum_p min(M_p, row[p]) (M = nullptr: of row[p]) in a
 // CTA of AREA_THREADS: positions tid, tid + AREA_THREADS, ... into four FP64
 // accumulators in turn (four independent add chains), added pairwise at the
 // end.  The areas stay FP64 sums (the precision plan keeps FP64 for them); on
-// this GPU the FP64 adds and the conversions they need, not the memory, set
-// the kernel's speed.  Every greedy area of the library goes through this one
+// this GPU the FP64 adds, not the memory, set the kernel's speed, so the
+// binary32 values are widened by integer operations (widen).  Every greedy area of the library goes through this one
 // function, so the same row gives the same sum to the last bit in every path.
 template <typename real>
 __device__ __forceinline__ double row_min_partial(const real* __restrict__ row, const real* __restrict__ M,
@@ -41,16 +63,16 @@ __device__ __forceinline__ double row_min_partial(const real* __restrict__ row, 
     int64_t p = threadIdx.x;
     if (M == nullptr) {
         for (; p + 3 * st < P; p += 4 * st) {
-            a0 += (double)row[p];
-            a1 += (double)row[p + st];
-            a2 += (double)row[p + 2 * st];
-            a3 += (double)row[p + 3 * st];
+            a0 += widen(row[p]);
+            a1 += widen(row[p + st]);
+            a2 += widen(row[p + 2 * st]);
+            a3 += widen(row[p + 3 * st]);
         }
-        for (; p < P; p += st) a0 += (double)row[p];
+        for (; p < P; p += st) a0 += widen(row[p]);
     } else {
         auto mn = [&](int64_t q) {
             const real d = row[q], mm = M[q];
-            return (double)(d < mm ? d : mm);
+            return widen(d < mm ? d : mm);
         };
         for (; p + 3 * st < P; p += 4 * st) {
             a0 += mn(p);
@@ -197,7 +219,7 @@ __global__ void __launch_bounds__(AREA_THREADS) row_blocks_kernel(const real* __
     double acc = 0.0;
     for (int64_t p = p0 + threadIdx.x; p < p1; p += AREA_THREADS) {
         const real d = row[p];
-        acc += (double)(M && M[p] < d ? M[p] : d);
+        acc += widen(M && M[p] < d ? M[p] : d);
     }
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) out[(int64_t)y * NB + b] = tot;
@@ -210,7 +232,7 @@ __global__ void __launch_bounds__(AREA_THREADS) curve_blocks_kernel(const real* 
     __shared__ double red[AREA_THREADS / 32];
     const int64_t p0 = (int64_t)blockIdx.x * L, p1 = p0 + L < P ? p0 + L : P;
     double acc = 0.0;
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += AREA_THREADS) acc += (double)M[p];
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += AREA_THREADS) acc += widen(M[p]);
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
@@ -230,7 +252,7 @@ __global__ void __launch_bounds__(AREA_THREADS) curve_sum_kernel(const real* __r
                                                                   double* __restrict__ out) {
     __shared__ double red[AREA_THREADS / 32];
     double acc = 0.0;
-    for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += (double)M[p];
+    for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += widen(M[p]);
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) *out = tot;
 }
