@@ -52,13 +52,13 @@ SM_MAX_MHZ = 2032.0
 # exact seed of every diagonal (ell FMA per R cells, about 2 FLOP at ell = m/2)
 FLOP_PER_ED_CELL = 8.0
 # dram__bytes_read.sum + dram__bytes_write.sum of the tile launches of one sweep
-# step (one-CTA tiles of m = 64 .. 256: 48 MB + 2.10 GB; two-CTA cluster tiles of
-# m = 288 .. 512: 43 MB + 0.78 GB), from an ncu capture of this kernel version
-SWEEP_TILE_DRAM_BYTES = 2.97e9
+# step (one-CTA tiles of m = 64 .. 256: 43 MB + 2.09 GB; two-CTA cluster tiles of
+# m = 288 .. 512: 39 MB + 0.78 GB), from an ncu capture of this kernel version
+SWEEP_TILE_DRAM_BYTES = 2.95e9
 # smsp__issue_active.avg.pct_of_peak_sustained_active of the tile kernel at two
 # lengths of the sweep (ncu --set full on this kernel version): the share of the
 # SMs' instruction-issue slots the kernel fills, beside the FLOP fraction
-TILE_ISSUE_ACTIVE = {"m128": 0.551, "m512": 0.520}
+TILE_ISSUE_ACTIVE = {"m128": 0.550, "m512": 0.519}
 
 
 def workload(m_list=None):

@@ -271,7 +271,8 @@ constexpr int SEL_CACHE = 9;  // keys of one position held per lane, per half (r
 
 // k-th largest key (kk-th, 1-based) of P_ABBA for a run of consecutive tile
 // positions, one run per group of G lanes; all groups of a warp step through
-// their runs together (npos_warp steps; a group past its own run idles).  Lane
+// their runs together (npos_warp steps; a group past its own run idles on the
+// CTA's first position).  Lane
 // gl of a group holds rows gl, gl+G, ... of AB column p and the window entries
 // CB[p+gl], CB[p+gl+G], ... in registers.  Every position after the first of
 // a run starts from the previous answer tau (consecutive positions share all
@@ -301,7 +302,9 @@ __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int R
     key_t tau = 0;
     for (int it = 0; it < npos_warp; ++it) {
         const bool valid = it < npos;
-        const int p = valid ? p_begin + it : 0;  // an idle group reads position 0
+        // an idle group (past the end of its run) reads this CTA's first
+        // position, pofs, and takes no part in the searches
+        const int p = valid ? p_begin + it : pofs;
         key_t va[SEL_CACHE], vb[SEL_CACHE];
         {
             const key_t* col = AB + ((p - pofs) % V) * LA + (p - pofs) / V + (size_t)gl * RS;
@@ -314,7 +317,7 @@ __device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int R
             }
         }
         key_t lo = 0, hi = KMAX;
-        bool done = false;
+        bool done = !valid;
         if (it > 0) {
             for (int step = 0; step < 3; ++step) {
                 // counts alone settle most positions (the rank of tau did not move)
