@@ -404,7 +404,7 @@ def run_ours(args):
                                                                    "profiles/tile_kernel_six_regime_m512_cluster.md"),
                 "fma_measured_tflops": {"fp32": fma32, "fp64": fma64,
                                         "basis": "pastila_probe_fma: 8 independent FMA chains per thread, "
-                                                 "148 x 8 CTAs of 256 threads, events"},
+                                                 "8 CTAs of 256 threads per SM, events"},
                 "frac_of_measured_fp32_fma": achieved / fma32 if fma32 else None}
 
     # ---- the plain FP64 one-job GPU path on the same workload (one step)

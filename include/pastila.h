@@ -488,8 +488,8 @@ pastila_status pastila_tile_time(pastila_series* h, double* ms, int64_t* launche
 /* -------------------------------------------------------------- probe ---- */
 
 /* Measured fused multiply-add rates of `device`, in TFLOP/s (2 FLOP per FMA):
- * a kernel of eight independent FMA chains per thread over 148 x 8 CTAs of 256
- * threads, timed with events after a warm-up launch, in FP32 and in FP64.
+ * a kernel of eight independent FMA chains per thread over 8 CTAs of 256
+ * threads per SM (148 x 8 on a B300), timed with events after a warm-up launch, in FP32 and in FP64.
  * The roofline of the profile kernel, which is bound by FP32/integer issue
  * rather than by memory or tensor cores, can be read against these.  No
  * counterpart in the paper.  Allocates and frees a small output buffer.

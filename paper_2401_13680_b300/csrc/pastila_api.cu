@@ -1692,8 +1692,8 @@ extern "C" pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, 
 // ---------------------------------------------------------------------------
 namespace {
 template <typename T>
-pastila_status fma_rate(int iters, double* tflops) {
-    const int blocks = 148 * 8, threads = 256;
+pastila_status fma_rate(int sms, int iters, double* tflops) {
+    const int blocks = sms * 8, threads = 256;  // 8 CTAs of 256 threads per SM
     T* out = nullptr;
     CK(cudaMalloc((void**)&out, sizeof(T) * (size_t)blocks * threads));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1723,7 +1723,9 @@ extern "C" pastila_status pastila_probe_fma(int32_t device, double* fp32_tflops,
     CK(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(PASTILA_EINVAL, "device %d: %d device(s) visible", device, ndev);
     CK(cudaSetDevice(device));
-    TRY(fma_rate<float>(4096, fp32_tflops));
-    TRY(fma_rate<double>(64, fp64_tflops));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    TRY(fma_rate<float>(sms, 4096, fp32_tflops));
+    TRY(fma_rate<double>(sms, 64, fp64_tflops));
     return PASTILA_OK;
 }
