@@ -1,0 +1,205 @@
+"""Shared-memory index ranges of the profile tile kernel, checked on the host
+(no device) for every layout the cost model or the tuned table can give.
+
+The tile geometry (array sizes and offsets in shared memory) is restated here
+and pinned to the library's own by the byte count pastila_plan_layout reports.
+The index expressions of the k-th selection (the grouped selector for
+R <= 288 and the warp selector beyond, idle groups included) and the sizes of
+the staging copies are then evaluated for every thread, position, cluster
+rank, partial last tile and block size a launch can have, and every index
+must fall inside its array.  A mistake of the kind this guards against is
+planted in the checker itself (an idle group reading tile position 0 instead
+of its CTA's first position) and must be caught."""
+import numpy as np
+import pytest
+
+from paper_2401_13680_b300 import pastila
+
+SMEM = 232448 - 1024  # B300 opt-in shared memory per block, less the static shared memory
+V = 4                 # columns per thread, both precisions
+SEL_CACHE = 9         # keys of one position per lane and half in the grouped selector
+
+
+def _a16(x):
+    return (x + 15) & ~15
+
+
+def geometry(prec, m, ell, lay):
+    """Array sizes (in elements) and the byte count of one tile's shared memory."""
+    es = 8 if prec == pastila.FP64 else 4  # working precision and key size alike
+    R = m - ell + 1
+    W, CS, Rg, NG = lay["W"], lay["CS"], lay["Rg"], lay["NG"]
+    Wb = W + R - 1
+    NTc = ((Wb + V - 1) // V + 31) // 32 * 32
+    NWc = NTc // 32
+    Wc = W // CS
+    LA = (Wc + V - 1) // V
+    RS = (V * LA) | 1
+    LP = NTc + 1
+    AE = 16 // es
+    RSt = (R + 2 * AE + AE - 1) // AE * AE
+    n = dict(AB=R * RS, CB=Wb + 32, PRE=NG * 2 * V * LP, CM=NG * 2 * (NTc + 1), LV=NG * 2 * 4 * NTc,
+             XCH=NG * 4 * NWc, row=5 * RSt, left=R, top=NG * NTc * V, Tc=NTc * V + ell + 64,
+             Tcl=NTc * V + ell + 64, Ts=m + 2 * AE, Tsl=m + 2 * AE, q=NG * (ell + 1),
+             CBp=CS * (Wb + 32) if CS > 1 else 0)
+    o = 0
+    for k in ("AB", "CB", "PRE", "CM", "LV", "XCH", "row", "left", "top", "Tc", "Tcl", "Ts", "Tsl", "q", "CBp"):
+        o = _a16(o + es * n[k])
+    return dict(n, R=R, W=W, Wb=Wb, NTc=NTc, NWc=NWc, Wc=Wc, LA=LA, RS=RS, LP=LP, RSt=RSt, AE=AE, es=es,
+                CS=CS, Rg=Rg, NG=NG, GS=lay["GS"], NT=lay["NT"], ell=ell, m=m, bytes=o)
+
+
+def _tdiv(a, b):
+    """C integer division (towards zero) and remainder, elementwise."""
+    q = np.trunc(a / b).astype(np.int64)
+    return q, a - q * b
+
+
+def selection_reads(G, BD, crank, Wp, idle_position=None):
+    """(AB index range, CB index range) over every read of the selection phase of
+    CTA crank of a tile with Wp positions, launched with BD threads."""
+    R, Wc, LA, RS = G["R"], G["Wc"], G["LA"], G["RS"]
+    pofs = crank * Wc
+    Wn = max(0, min(Wp - pofs, Wc))
+    ab, cb = [], []
+    if R <= 32 * SEL_CACHE:  # grouped selector
+        GS = G["GS"]
+        ngroups = BD // GS
+        PW = (Wn + ngroups - 1) // ngroups
+        if PW == 0:
+            return None, None
+        tid = np.arange(BD)[:, None, None]
+        grp, gl = tid // GS, tid % GS
+        pb = grp * PW
+        npos = np.where(pb >= Wn, 0, np.where(pb + PW <= Wn, PW, Wn - pb))
+        it = np.arange(PW)[None, :, None]
+        j = np.arange(SEL_CACHE)[None, None, :]
+        valid = it < npos
+        idle = pofs if idle_position is None else idle_position
+        p = np.where(valid, pofs + pb + it, idle)
+        nr = (R - gl + GS - 1) // GS
+        load = j < nr
+        q, r = _tdiv(p - pofs, V)
+        col = r * LA + q + gl * RS
+        ab = (col + j * GS * RS)[np.broadcast_to(load, (BD, PW, SEL_CACHE))]
+        cb = (p + gl + j * GS)[np.broadcast_to(load, (BD, PW, SEL_CACHE))]
+    else:  # one run per warp
+        nwarps = BD >> 5
+        PW = (Wn + nwarps - 1) // nwarps
+        if PW == 0:
+            return None, None
+        ab_l, cb_l = [], []
+        for w in range(nwarps):
+            pb = w * PW
+            npos = 0 if pb >= Wn else min(PW, Wn - pb)
+            if npos == 0:
+                continue
+            p = pofs + pb + np.arange(npos)
+            q, r = _tdiv(p - pofs, V)
+            cp = r * LA + q  # AB column of each position; rows at multiples of RS
+            ab_l += [cp.min(), (R - 1) * RS + cp.max()]
+            cb_l += [p.min(), p.max() + R - 1]
+            if npos > 1:
+                cb_l += [p[1:].min() - 1]
+        ab, cb = np.array(ab_l), np.array(cb_l)
+    return (int(np.min(ab)), int(np.max(ab))), (int(np.min(cb)), int(np.max(cb)))
+
+
+def check_layout(prec, m, ell, lay):
+    G = geometry(prec, m, ell, lay)
+    assert G["bytes"] == lay["bytes"], (m, ell, lay, G["bytes"])  # the restatement is the library's geometry
+    assert G["Wc"] % V == 0  # a thread's V positions share one owner CTA
+    R, AE = G["R"], G["AE"]
+    for BD in sorted({G["NT"], min(512, G["NT"] + 32), 512}):
+        if BD < G["NT"]:
+            continue
+        for crank in range(G["CS"]):
+            for Wp in sorted({G["W"], G["W"] - 1, G["W"] // 2 + 3, G["Wc"] + 1, 1} - {0}):
+                if not 1 <= Wp <= G["W"]:
+                    continue
+                abr, cbr = selection_reads(G, BD, crank, Wp)
+                if abr is None:
+                    continue
+                assert 0 <= abr[0] and abr[1] < G["AB"], (m, ell, lay, BD, crank, Wp, abr, G["AB"])
+                assert 0 <= cbr[0] and cbr[1] < Wp + R - 1 + 32 <= G["CB"], (m, ell, lay, BD, crank, Wp, cbr)
+                # staging copies of this tile: whole 16-byte units from a 16-byte boundary
+                nTc = Wp + R - 1 + ell - 1
+                assert (nTc + AE - 1) // AE * AE <= G["Tc"]
+                for os in range(AE):
+                    assert (os + m + AE - 1) // AE * AE <= G["Ts"]
+                    assert (os + R + AE - 1) // AE * AE <= G["RSt"]
+    # the seeds' sliding reads (9-column blocks) stay inside the staged window
+    J = 9
+    nblk = (G["NTc"] * V + J - 1) // J
+    assert (nblk - 1) * J + ell - 1 + J < G["Tc"]
+    # row-window maxima of owned positions end inside the chunk prefix arrays
+    assert (G["W"] - 1 + R - 1) // V <= G["NTc"] - 1
+
+
+def _cases():
+    ms = [8, 24, 50, 100] + list(range(64, 769, 32))
+    for prec in (pastila.FP32, pastila.FP64):
+        for n in (4096, 100_000, 1_000_000):
+            for m in ms:
+                if m > n:
+                    continue
+                for ell in sorted({m // 2, max(2, m // 8), m}):
+                    yield prec, n, m, ell
+
+
+@pytest.mark.parametrize("prec", [pastila.FP32, pastila.FP64])
+def test_cost_model_layouts_stay_in_bounds(prec):
+    pastila.tune_clear()
+    count = 0
+    for p, n, m, ell in _cases():
+        if p != prec:
+            continue
+        check_layout(prec, m, ell, pastila.plan_layout(prec, n, m, SMEM, ell=ell))
+        count += 1
+    assert count > 100
+
+
+@pytest.mark.parametrize("CS", [1, 2, 4])
+def test_tuned_layouts_stay_in_bounds(CS):
+    """Layouts forced through the tuned table: every width and selection group
+    width the tuner can choose, with one, two and four CTAs per tile."""
+    pastila.tune_clear()
+    checked = 0
+    try:
+        for m in (64, 128, 256, 512, 640):
+            ell = m // 2
+            k = (m + 9) // 10
+            R = m - ell + 1
+            for W in range(32 * CS, 1025, 32 * CS):
+                for NGw in (1, 2, 3, 4):
+                    for GS in (4, 8, 16, 32):
+                        if R <= 32 * SEL_CACHE and R > GS * SEL_CACHE:
+                            continue
+                        pastila.tune_set(pastila.FP32, m, ell, k, W, NGw, GS, CS)
+                        lay = pastila.plan_layout(pastila.FP32, 1_000_000, m, SMEM, ell=ell, k=k)
+                        if (lay["W"], lay["CS"], lay["GS"]) != (W, CS, GS):
+                            continue  # does not fit: the cost model decides instead
+                        check_layout(pastila.FP32, m, ell, lay)
+                        checked += 1
+    finally:
+        pastila.tune_clear()
+    assert checked > 20
+
+
+def test_checker_catches_an_idle_group_reading_tile_position_zero():
+    """An idle group of the second CTA of a cluster that read tile position 0
+    would index its CTA's AB array before its start."""
+    pastila.tune_clear()
+    m, ell = 512, 256
+    try:
+        pastila.tune_set(pastila.FP32, m, ell, 52, 256, 4, 32, 2)
+        lay = pastila.plan_layout(pastila.FP32, 100_000, m, SMEM, ell=ell, k=52)
+    finally:
+        pastila.tune_clear()
+    G = geometry(pastila.FP32, m, ell, lay)
+    assert G["CS"] == 2
+    Wp = G["W"] - 5  # a partial tile: some groups idle for their last steps
+    good, _ = selection_reads(G, G["NT"], 1, Wp)
+    bad, _ = selection_reads(G, G["NT"], 1, Wp, idle_position=0)
+    assert good[0] >= 0
+    assert bad[0] < 0
