@@ -288,6 +288,49 @@ def run_serving_plain(args, pastila, device, rate, precision):
             "basis": "measured: one job at a time in arrival order, select_length on a handle per job"}
 
 
+def run_multivariate(pastila, device, ms, K, d=3, seeds=(1, 5, 9)):
+    """A d-coordinate series (Section 3.1: each coordinate searched on its own,
+    Section 3.2), the coordinates six-regime series like the sweep's, through the
+    engine in one submission (its coordinates share waves) against the same
+    coordinates one after the other through select_length on a handle each.
+    Wall time from submission to the last result; both runs once untimed first."""
+    T = np.stack([synth.six_regime_sweep(seed=sd).T for sd in seeds[:d]])
+    n = T.shape[1]
+    prof = d * cells(n, ms)[0]
+
+    def engine_run():
+        with pastila.Engine(device=device) as e:
+            t0 = time.perf_counter()
+            ids = e.submit_multivariate(T, ms, K)
+            infos = [e.wait(j) for j in ids]
+            res = [e.result(j) for j in ids]
+            dt = time.perf_counter() - t0
+        assert all(i["state"] == pastila.JOB_DONE for i in infos), "a coordinate did not finish"
+        return dt, res, len({i["first_wave"] for i in infos})
+
+    def sequential_run():
+        t0 = time.perf_counter()
+        res = []
+        for c in range(d):
+            with pastila.Series(T[c], device=device, precision=pastila.FP32) as h:
+                res.append(h.select_length(ms, K))
+        return time.perf_counter() - t0, res
+
+    engine_run()
+    sequential_run()
+    te, re_, first_waves = engine_run()
+    ts, rs = sequential_run()
+    same = all(a[0] == b[0] and np.array_equal(np.asarray(a[1]), np.asarray(b[1])) and a[2] == b[2]
+               for a, b in zip(re_, rs))
+    return {"coordinates": d, "n": n, "m_list": ms, "K": K,
+            "workload": "d six-regime series (seeds %s), one engine submission" % (list(seeds[:d]),),
+            "engine_s": te, "engine_profile_cells_per_s": prof / te, "engine_first_waves": first_waves,
+            "sequential_s": ts, "sequential_profile_cells_per_s": prof / ts,
+            "results_identical": bool(same),
+            "basis": "wall time, submission to last result; sequential = select_length on one handle "
+                     "per coordinate, one after the other"}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args):
@@ -441,6 +484,10 @@ def run_ours(args):
                 run_serving_plain(args, pastila, local, serving["arrival_rate_jobs_per_s"], prec)
                 for prec in (pastila.FP32, pastila.FP64)]
 
+    multi = None
+    if not args.no_multi and world == 1:
+        multi = run_multivariate(pastila, local, ms, K_SNIPPETS)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -448,7 +495,7 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps, "roofline": roofline,
             "ed_cells_per_s": world * ed_cells * args.steps / tot_s,
             "m_best": result[0], "criterion": [float(x) for x in result[1]],
-            "step_ms": step_ms, "fp64_path": fp64, "serving": serving, "autotune": tune}
+            "step_ms": step_ms, "fp64_path": fp64, "serving": serving, "multivariate": multi, "autotune": tune}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     h.close()
@@ -478,6 +525,7 @@ def main():
                          "first, or both one after the other (same arrivals)")
     ap.add_argument("--serve-plain", action="store_true",
                     help="also run the serving stream one job at a time on FP32 and FP64 handles (slow)")
+    ap.add_argument("--no-multi", action="store_true", help="skip the multivariate leg")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="offered load of the serving leg, as a fraction of the measured ED-cell rate")
     args = ap.parse_args()
