@@ -237,26 +237,6 @@ __global__ void __launch_bounds__(AREA_THREADS) curve_blocks_kernel(const real* 
     if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
-// out[s] = sum over its tiles of part[s][tile], in tile order.  One thread per segment.
-__global__ void segment_sum_kernel(const double* __restrict__ part, int S, int ntiles, double* __restrict__ out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    double t = 0.0;
-    for (int i = 0; i < ntiles; ++i) t += part[(int64_t)s * ntiles + i];
-    out[s] = t;
-}
-
-// sum of the P values of M, FP64 (one CTA)
-template <typename real>
-__global__ void __launch_bounds__(AREA_THREADS) curve_sum_kernel(const real* __restrict__ M, int64_t P,
-                                                                  double* __restrict__ out) {
-    __shared__ double red[AREA_THREADS / 32];
-    double acc = 0.0;
-    for (int64_t p = threadIdx.x; p < P; p += AREA_THREADS) acc += widen(M[p]);
-    const double tot = block_sum(acc, red);
-    if (threadIdx.x == 0) *out = tot;
-}
-
 // M <- row (first step) or min(M, row)
 template <typename real>
 __global__ void min_curve_kernel(const real* __restrict__ row, int64_t P, int first, real* __restrict__ M) {
