@@ -73,3 +73,18 @@ def test_engine_host_side_validation():
     assert lib.pastila_engine_release(None, 1) == pastila.EINVAL
     assert lib.pastila_engine_stats(None, None) == pastila.EINVAL
     lib.pastila_engine_destroy(None)  # no-op
+
+
+def test_no_device_means_an_error_not_a_fallback():
+    """There is no CPU path: where no GPU is visible, every entry point that
+    needs one reports ECUDA instead of computing anything."""
+    import pytest
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    T = np.random.default_rng(0).normal(size=1000)
+    for make in (lambda: pastila.Series(T), lambda: pastila.Series(T, precision=pastila.FP64),
+                 lambda: pastila.Engine(), lambda: pastila.probe_fma(0)):
+        with pytest.raises(pastila.PastilaError, match="ECUDA"):
+            make()
