@@ -3,9 +3,11 @@
 
 The tile geometry (array sizes and offsets in shared memory) is restated here
 and pinned to the library's own by the byte count pastila_plan_layout reports.
-The index expressions of the k-th selection (the grouped selector for
-R <= 288 and the warp selector beyond, idle groups included) and the sizes of
-the staging copies are then evaluated for every thread, position, cluster
+The index expressions of the rows phase (prefix, chunk and sparse-table
+maxima, the exchange between warps, the row-window maxima written into the
+owning CTA), of the k-th selection (the grouped selector for R <= 288 and the
+warp selector beyond, idle groups included) and the sizes of the staging
+copies are then evaluated for every thread, position, cluster
 rank, partial last tile and block size a launch can have, and every index
 must fall inside its array.  A mistake of the kind this guards against is
 planted in the checker itself (an idle group reading tile position 0 instead
@@ -105,11 +107,93 @@ def selection_reads(G, BD, crank, Wp, idle_position=None):
     return (int(np.min(ab)), int(np.max(ab))), (int(np.min(cb)), int(np.max(cb)))
 
 
+def _assert_union(pieces, lo, hi):
+    """The column (or chunk) ranges cover lo .. hi exactly: nothing outside, no
+    gap (overlaps are harmless for a maximum)."""
+    pieces = sorted(pieces)
+    assert all(lo <= a_ <= b_ <= hi for a_, b_ in pieces), (pieces, lo, hi)
+    assert pieces[0][0] == lo, (pieces, lo)
+    reach = pieces[0][1]
+    for a_, b_ in pieces[1:]:
+        assert a_ <= reach + 1, (pieces, lo, hi)
+        reach = max(reach, b_)
+    assert reach == hi, (pieces, hi)
+
+
+def rows_phase_check(G, Wp):
+    """Every shared-memory index of the rows phase of a tile with Wp positions (per row group: the chunk prefix maxima PRE [parity][V][LP], the
+    chunk maxima CM [parity][NTc + 1], the sparse tables LV [parity][4][NTc], the
+    warp exchange XCH [parity][2][NWc]; the row-window maxima written into the
+    owning CTA's AB) lies inside its array, each sparse-table read spans chunks
+    of one warp, and the pieces of every owned position's window (own suffix,
+    whole chunks in between, the far chunk's prefix) cover exactly its R columns."""
+    R, V_, NTc, NWc, LP = G["R"], V, G["NTc"], G["NWc"], G["LP"]
+    RS, LA, Wc, CS = G["RS"], G["LA"], G["Wc"], G["CS"]
+    q0 = (R - 1) // V_
+    small_R = R - 1 < V_
+    t = np.arange(NTc)
+    xb = t * V_
+    # writes of every active thread (all column threads take part in every row step)
+    assert (V_ - 1) * LP + t.max() < V_ * LP            # PRE
+    assert t.max() < NTc + 1 and NTc < NTc + 1           # CM, and its sentinel
+    assert 3 * NTc + t.max() < 4 * NTc                   # LV
+    assert 1 * NWc + (NWc - 1) < 2 * NWc                 # XCH within its parity
+    owners = xb < Wp
+    for tt in (int(x) for x in t[owners]):
+        x0 = tt * V_
+        # window pieces, as column ranges relative to the tile
+        for i in range(V_):
+            if x0 + i >= Wp:
+                continue
+            e = i + R - 1
+            oi, si = e // V_, e % V_
+            assert (si * LP + tt + oi) < V_ * LP and tt + oi <= NTc - 1
+            lo, hi = x0 + i, x0 + i + R - 1
+            if small_R and e < V_:
+                cover = [(lo, hi)]                       # inside this chunk
+            else:
+                cover = [(x0 + i, x0 + V_ - 1)]          # own suffix
+                if not small_R and q0 >= 2:
+                    cover.append(((tt + 1) * V_, (tt + q0) * V_ - 1))  # whole chunks t+1 .. t+q0-1
+                if not small_R and oi > q0:
+                    cover.append(((tt + q0) * V_, (tt + q0 + 1) * V_ - 1))  # chunk t+q0
+                cover.append(((tt + oi) * V_, (tt + oi) * V_ + si))  # far chunk's prefix
+            _assert_union(cover, lo, hi)
+        if not small_R:
+            assert tt + q0 <= NTc                        # CM[t + q0] (the sentinel at NTc)
+        if not small_R and q0 >= 2:
+            a_, z_ = tt + 1, tt + q0 - 1
+            wa, wz = a_ >> 5, z_ >> 5
+            spans = [(a_, z_)] if wa == wz else [(a_, wa * 32 + 31), (wz * 32, z_)]
+            pieces = []
+            for x, y in spans:
+                k = int(y - x + 1).bit_length() - 1
+                w = 16 if k > 4 else 1 << k
+                for s0 in (x, y - w + 1):
+                    assert s0 >> 5 == (s0 + w - 1) >> 5 and 0 <= s0 and s0 + w - 1 < NTc
+                    pieces.append((s0, s0 + w - 1))
+            for wv in range(wa + 1, wz):
+                assert 3 * NTc + wv * 32 + 16 < 4 * NTc
+                pieces += [(wv * 32, wv * 32 + 15), (wv * 32 + 16, wv * 32 + 31)]
+            _assert_union(pieces, a_, z_)
+        # the row-window maxima of this thread's positions, into the owner's AB
+        owner = x0 // Wc if CS > 1 else 0
+        tofs = owner * (Wc // V_) if CS > 1 else 0
+        for i in range(V_):
+            if x0 + i < Wp:
+                assert owner == (x0 + i) // Wc or CS == 1
+                idx = (R - 1) * RS + (tt - tofs) + i * LA
+                assert 0 <= tt - tofs and idx < R * RS
+
+
 def check_layout(prec, m, ell, lay):
     G = geometry(prec, m, ell, lay)
     assert G["bytes"] == lay["bytes"], (m, ell, lay, G["bytes"])  # the restatement is the library's geometry
     assert G["Wc"] % V == 0  # a thread's V positions share one owner CTA
     R, AE = G["R"], G["AE"]
+    # the rows phase's indices do not depend on the CTA's rank, and a partial
+    # tile owns a subset of a full tile's positions
+    rows_phase_check(G, G["W"])
     for BD in sorted({G["NT"], min(512, G["NT"] + 32), 512}):
         if BD < G["NT"]:
             continue
