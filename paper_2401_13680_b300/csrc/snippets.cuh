@@ -33,7 +33,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // by 2^24 in binary32 (exact, the result is normal) and rebiased by 896 - 24;
 // zeros keep only their sign; infinities and NaNs get the all-ones exponent.
 // The FP32 area sums use it instead of a conversion instruction, which on this
-// GPU issues on the FP64 pipe, as slowly as the FP64 add itself.
+// GPU issues on the FP64 pipe, as slowly as the FP64 add itself.  The library is
+// built without flush-to-zero, so the binary32 scaling keeps subnormal inputs
+// (the exact-sum tests include them).
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double widen(float f) {
     const uint32_t u0 = __float_as_uint(f);
