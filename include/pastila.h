@@ -34,7 +34,13 @@
  *    on the handle that synchronises its stream (profiles, snippets,
  *    select_length, snippets_streamed, tune) returns PASTILA_ETIMEOUT with
  *    its outputs unspecified; an engine fails its unfinished jobs with
- *    PASTILA_ETIMEOUT and stops.  The device context stays usable.
+ *    PASTILA_ETIMEOUT and stops.  Callers of the enqueue-only entry points
+ *    (pastila_profiles_device) read the flag with pastila_stage_status after
+ *    synchronising.  The device context stays usable.  Before it ends, a tile
+ *    whose wait ran out waits once more (bounded) for its copies, so that none
+ *    lands after its shared memory is released; only if that second wait runs
+ *    out as well can a copy still arrive late, into shared memory that another
+ *    block of the same or a later kernel may own by then.
  *    (PASTILA_TEST_STAGE_WAIT=timeout in the environment when a handle or an
  *    engine is created makes every such wait run out, for tests.)
  */
@@ -126,9 +132,19 @@ pastila_status pastila_profiles(pastila_series* h, int32_t m, pastila_mparams mp
 
 /* As pastila_profiles with a device output buffer (same layout and element
  * type), written on the handle's stream; returns once the work is enqueued.
- * D_max_dev: NULL or a device double written on the same stream. */
+ * D_max_dev: NULL or a device double written on the same stream.
+ * The call does not wait, so it cannot report a staging wait that ran out:
+ * after synchronising the stream, call pastila_stage_status before using D. */
 pastila_status pastila_profiles_device(pastila_series* h, int32_t m, pastila_mparams mp,
                                        void* D_dev, double* D_max_dev);
+
+/* Status of the handle's tile work enqueued so far, for callers of the
+ * enqueue-only entry points: call it after the handle's stream has been
+ * synchronised.  Returns PASTILA_ETIMEOUT (and clears the flag) if a tile's
+ * bounded staging wait ran out since the last check, in which case the outputs
+ * of that work are unspecified; PASTILA_OK otherwise.  Reads one host-mapped
+ * word; launches nothing.  Errors: EINVAL (NULL handle). */
+pastila_status pastila_stage_status(pastila_series* h);
 
 /* --------------------------------------------- snippets (eqs. 5-8, 16-17) ---- */
 
@@ -184,7 +200,10 @@ pastila_status pastila_select_length(pastila_series* h, const int32_t* m_list, i
  * with that device current, looks up the array's device address; make that
  * first call before any stream capture.  All calls share the one array, so
  * calls whose work overlaps on the GPU (other streams, other host threads)
- * race; order them on one stream or synchronise between them.
+ * race; order them on one stream or synchronise between them.  The looked-up
+ * address is kept per device ordinal for the life of the process: after a
+ * cudaDeviceReset on a device the entry point must not be called on it again
+ * in that process (it would launch on the stale address).
  * Errors: EINVAL (NULL pointer, S, P or K out of range), ECUDA. */
 pastila_status pastila_greedy_noalloc(const float* D_dev, int32_t S, int64_t P, int32_t K,
                                       int32_t* chosen_dev, double* area_after_dev, void* stream);
@@ -410,15 +429,14 @@ pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_m
 /* ----------------------------------------------------------- autotuner ---- */
 
 /* The tile layout of a length (positions per CTA W, row groups NG, threads NT,
- * lanes per selection group GS) comes from a cost model unless the autotuner
+ * lanes per selection run GS, always 32: one warp per run of positions) comes
+ * from a cost model unless the autotuner
  * has chosen one.  pastila_tune times, for every m of m_list with the ell/k
  * rule, the model's layout and up to max_candidates - 1 rivals (the model's
  * best two- and four-CTA cluster layouts and its best layout of at most 256
  * threads and half an SM's shared memory, so that two CTAs share an SM; then
  * the cheapest of every thread count, then by modelled cost, these within
- * 1.5x of the model's best), each also with twice the default selection group
- * width where R <= 288, on the first
- * min(S, 64) segments of h's series, and keeps the fastest (a rival must beat
+ * 1.5x of the model's best), on the first min(S, 64) segments of h's series, and keeps the fastest (a rival must beat
  * the layout kept so far by more than 1 %, so that layouts within timing noise
  * of each other do not trade places from run to run) in a process-wide
  * table keyed by (precision, m, ell, k) that every later call uses (handles and
@@ -430,7 +448,7 @@ pastila_status pastila_snippets_streamed(pastila_series* h, int32_t m, pastila_m
 typedef struct {
     int32_t m;
     int32_t W, NG, NT;     /* the chosen layout */
-    int32_t GS;            /* lanes per k-th selection group */
+    int32_t GS;            /* lanes per k-th selection run (32) */
     int32_t CS;            /* CTAs per tile: 1, 2 or 4 (a thread-block cluster splitting the rows) */
     int32_t candidates;    /* layouts timed */
     double ms_model;       /* device time of the cost model's layout on the sample */
@@ -445,8 +463,8 @@ void pastila_tune_clear(void);
 
 /* Writes (pastila_tune_set) or reads (pastila_tune_get) one entry of the tuned
  * table: for (prec, m, ell, k), tile width W (a multiple of 32), NG row groups
- * asked per CTA, GS lanes per selection group (4, 8, 16 or 32, and at least
- * R / 9 when R <= 288), CS CTAs per tile (1 or 2).  A table saved with
+ * asked per CTA, GS lanes per selection run (must be 32: the selection runs one
+ * warp per run of positions), CS CTAs per tile (1, 2 or 4).  A table saved with
  * pastila_tune_get and restored with pastila_tune_set reproduces the tuned
  * runs' results bit for bit.  A layout that does not fit the device's shared
  * memory is ignored when it is looked up (the cost model decides instead).

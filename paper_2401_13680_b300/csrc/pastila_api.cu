@@ -543,17 +543,6 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     cudaEvent_t e0, e1;
     TRY(get_event(h, &e0));
     TRY(get_event(h, &e1));
-    // every picked layout with the default selection group width, and with twice
-    // that width where the grouped selector runs (longer runs per group)
-    {
-        const size_t np = pick.size();
-        for (size_t i = 0; i < np; ++i)
-            if (pick[i].g.R <= 32 * SEL_CACHE && pick[i].g.GS < 32) {
-                TileCand t = pick[i];
-                t.g.GS *= 2;
-                pick.push_back(t);
-            }
-    }
     double best_ms = 1e300, model_ms = 0.0;
     size_t bi = 0;
     for (size_t i = 0; i < pick.size(); ++i) {
@@ -1284,11 +1273,8 @@ pastila_status pastila_tune_set(pastila_precision prec, int32_t m, int32_t ell, 
     if (m < 4 || ell < 2 || ell > m || k < 1) return fail(PASTILA_EINVAL, "m = %d, ell = %d, k = %d out of range", m, ell, k);
     if (W < 32 || W % 32) return fail(PASTILA_EINVAL, "W = %d: a positive multiple of 32", W);
     if (NG < 1 || NG > 64) return fail(PASTILA_EINVAL, "NG = %d: 1 .. 64 row groups", NG);
-    if (GS != 4 && GS != 8 && GS != 16 && GS != 32) return fail(PASTILA_EINVAL, "GS = %d: 4, 8, 16 or 32", GS);
+    if (GS != 32) return fail(PASTILA_EINVAL, "GS = %d: the selection runs one warp (32 lanes) per run", GS);
     if (CS != 1 && CS != 2 && CS != 4) return fail(PASTILA_EINVAL, "CS = %d: 1, 2 or 4", CS);
-    const int R = m - ell + 1;
-    if (R <= 32 * SEL_CACHE && R > GS * SEL_CACHE)
-        return fail(PASTILA_EINVAL, "GS = %d holds at most %d values per half; R = %d", GS, GS * SEL_CACHE, R);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[std::make_tuple(prec == PASTILA_FP64 ? 8 : 4, m, ell, k)] = std::make_tuple(W, NG, GS, CS);
     g_tune_gen++;
@@ -1476,6 +1462,12 @@ pastila_status pastila_profiles_device(pastila_series* h, int32_t m, pastila_mpa
         h->launches += 1;
     }
     return PASTILA_OK;
+}
+
+pastila_status pastila_stage_status(pastila_series* h) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    return stage_check(h);
 }
 
 pastila_status pastila_profiles(pastila_series* h, int32_t m, pastila_mparams mp, void* D_out,

@@ -36,9 +36,8 @@
 //      prefix/suffix maxima over V-column chunks plus the maxima of the whole
 //      chunks in between.
 //   3  per position, the k-th largest of the 2R values of P_ABBA (eqs. 12-13),
-//      tracked from position to position: by groups of lanes on order-preserving
-//      integer keys for R <= 288 (select_track), by one warp per run of positions
-//      on values with incrementally updated counts beyond that (select_runs);
+//      tracked from position to position by one warp per run of positions, with
+//      counts updated from the values that changed (select_warp);
 //      D = sqrt(2 ell max(0, 1-rho*))
 #pragma once
 #include <cooperative_groups.h>
@@ -88,6 +87,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// Retires an mbarrier (its shared memory may then be used for anything else).
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Waits for the phase of the given parity to complete, for at most `limit`
@@ -147,7 +151,7 @@ struct ProfileArgs {
 // Shared-memory layout and thread layout of one tile; identical on host and device.
 struct TileGeom {
     int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, LP, ell, m;
-    int GS;  // lanes per selection group (R <= 288: 4, 8, 16 or 32 with R <= 9 GS)
+    int GS;  // lanes per selection run (32: one warp per run of positions)
     // tiles of a thread-block cluster of CS CTAs (1, 2 or 4): CTA c computes rows
     // c Rh .. c Rh + Rh - 1 over every column of the tile and selects positions
     // c Wc .. c Wc + Wc - 1; AB holds all R rows of its own Wc positions (the
@@ -187,7 +191,7 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     g.LA = (g.Wc + V - 1) / V;
     g.RS = (V * g.LA) | 1;
     g.LP = g.NTc + 1;  // chunk prefix maxima: [V][LP], thread t at t (+ chunk offset)
-    g.GS = g.R <= 36 ? 4 : (g.R <= 72 ? 8 : (g.R <= 144 ? 16 : 32));  // the narrowest that fits 9 values per half
+    g.GS = 32;  // lanes per selection run: one warp
     const size_t NG = (size_t)g.NG;
     size_t o = 0;
     g.off_AB = o;   o = align16(o + sizeof(key_t) * (size_t)g.R * g.RS);
@@ -262,187 +266,8 @@ __device__ __forceinline__ T grp_max(T v, int G) {
     return v;
 }
 
-// The working-precision type whose order-preserving key type is key_t.
-template <typename key_t> struct KeyReal;
-template <> struct KeyReal<uint32_t> { typedef float type; };
-template <> struct KeyReal<unsigned long long> { typedef double type; };
-
-constexpr int SEL_CACHE = 9;  // keys of one position held per lane, per half (rows, window)
-
-// k-th largest key (kk-th, 1-based) of P_ABBA for a run of consecutive tile
-// positions, one run per group of G lanes; all groups of a warp step through
-// their runs together (npos_warp steps; a group past its own run idles on the
-// CTA's first position).  Lane
-// gl of a group holds rows gl, gl+G, ... of AB column p and the window entries
-// CB[p+gl], CB[p+gl+G], ... in registers.  Every position after the first of
-// a run starts from the previous answer tau (consecutive positions share all
-// but a few of their 2R values, so the rank of tau moves little): a pass counts
-// the keys >= tau and > tau, which settles most positions; otherwise a second
-// pass finds the nearest key on the side the answer lies, which settles the
-// answer when its rank moved by one, and tau steps to that key and the
-// counting repeats.  The first position of a run,
-// and a position still open after three steps, is searched inside its bracket
-// of keys: the pivot interpolates between the values of two bounds with known
-// counts (#{>= L} >= kk > #{>= H}) at the rank kk, and once a bound's count is
-// exactly kk (or kk - 1 at H) one min (max) pass gives the answer; a bisection
-// over the keys finishes anything still open after six pivots.  Control flow
-// is uniform across the warp: decisions are per-group selects, loops run while
-// any group of the warp still works.
-template <typename key_t, typename Out>
-__device__ __forceinline__ void select_track(const key_t* __restrict__ AB, int RS, int LA, int V,
-                                             const key_t* __restrict__ CB, int R, int kk, int p_begin,
-                                             int npos, int npos_warp, int G, int gl, int pofs, Out out) {
-    // AB column of tile position p: p - pofs in this CTA's AB
-    // requires R <= G * SEL_CACHE: every value of a position sits in the registers of its group
-    typedef KeyOf<typename KeyReal<key_t>::type> K;
-    typedef typename KeyReal<key_t>::type real;
-    const unsigned FULL = 0xffffffffu;
-    const key_t KMAX = ~(key_t)0;
-    const int nr = (R - gl + G - 1) / G;  // values per half held by this lane
-    key_t tau = 0;
-    for (int it = 0; it < npos_warp; ++it) {
-        const bool valid = it < npos;
-        // an idle group (past the end of its run) reads this CTA's first
-        // position, pofs, and takes no part in the searches
-        const int p = valid ? p_begin + it : pofs;
-        key_t va[SEL_CACHE], vb[SEL_CACHE];
-        {
-            const key_t* col = AB + ((p - pofs) % V) * LA + (p - pofs) / V + (size_t)gl * RS;
-            const key_t* win = CB + p + gl;
-#pragma unroll
-            for (int j = 0; j < SEL_CACHE; ++j) {
-                const bool in = j < nr;
-                va[j] = in ? col[(size_t)j * G * RS] : (key_t)0;
-                vb[j] = in ? win[j * G] : (key_t)0;
-            }
-        }
-        key_t lo = 0, hi = KMAX;
-        bool done = !valid;
-        if (it > 0) {
-            for (int step = 0; step < 3; ++step) {
-                // counts alone settle most positions (the rank of tau did not move)
-                uint32_t c = 0;
-#pragma unroll
-                for (int j = 0; j < SEL_CACHE; ++j) {
-                    if (j < nr) {
-                        const key_t a = va[j], b = vb[j];
-                        c += (a >= tau ? 1u : 0u) + (a > tau ? 65536u : 0u);
-                        c += (b >= tau ? 1u : 0u) + (b > tau ? 65536u : 0u);
-                    }
-                }
-                c = grp_sum(c, G);
-                const int cge = (int)(c & 0xffffu), cgt = (int)(c >> 16);
-                if (!done) done = cgt < kk && kk <= cge;
-                if (__all_sync(FULL, done)) break;
-                // otherwise the nearest key on the side the answer lies: below tau when
-                // fewer than kk keys are >= tau, above it when kk or more are > tau;
-                // distance d = tau - 1 - a (below) or a - tau - 1 (above), both as
-                // (a ^ s) + base, and keys on the wrong side wrap to large values
-                const bool down = cge < kk;
-                const key_t s = down ? ~(key_t)0 : (key_t)0, base = down ? tau : ~tau;
-                key_t x = KMAX;
-#pragma unroll
-                for (int j = 0; j < SEL_CACHE; ++j) {
-                    if (j < nr) {
-                        const key_t da = (va[j] ^ s) + base, db = (vb[j] ^ s) + base;
-                        x = da < x ? da : x;
-                        x = db < x ? db : x;
-                    }
-                }
-                x = grp_min(x, G);
-                if (!done) {
-                    if (down) {
-                        tau = tau - (key_t)1 - x;
-                        hi = tau;
-                        done = cge == kk - 1;  // exactly one key short: the next key down is the answer
-                    } else {
-                        tau = tau + (key_t)1 + x;
-                        lo = tau;
-                        done = cgt == kk;      // exactly kk keys above: the smallest of them
-                    }
-                }
-                if (__all_sync(FULL, done)) break;
-            }
-        }
-        // search inside [lo, hi] (the whole key range at a run's first position):
-        // interpolation on the values between two counted bounds, then the exact
-        // answer by one min/max pass once a bound's count is exactly kk (or kk - 1
-        // just above it); a bisection over the keys finishes whatever is left
-        const bool need = !done;
-        if (__any_sync(FULL, need)) {
-            key_t mn = KMAX, mx = 0;
-            uint32_t cb = 0;  // #{>= lo} + 65536 * #{> hi}
-#pragma unroll
-            for (int j = 0; j < SEL_CACHE; ++j) {
-                if (j < nr) {
-                    const key_t a = va[j], b = vb[j];
-                    if (a >= lo && a <= hi) { mn = a < mn ? a : mn; mx = a > mx ? a : mx; }
-                    if (b >= lo && b <= hi) { mn = b < mn ? b : mn; mx = b > mx ? b : mx; }
-                    cb += (a >= lo ? 1u : 0u) + (a > hi ? 65536u : 0u) + (b >= lo ? 1u : 0u) + (b > hi ? 65536u : 0u);
-                }
-            }
-            mn = grp_min(mn, G);
-            mx = grp_max(mx, G);
-            cb = grp_sum(cb, G);
-            // bracket [L, H): #{>= L} = cL >= kk > cH = #{>= H}
-            key_t L = mn, H = mx + (key_t)1;
-            int cL = (int)(cb & 0xffffu), cH = (int)(cb >> 16);
-            auto open = [&]() { return need && cL != kk && cH != kk - 1 && H - L > (key_t)1; };
-            for (int itr = 0; itr < 6 && __any_sync(FULL, open()); ++itr) {
-                const bool act = open();
-                const real fL = K::dec(L), fH = K::dec(H);
-                const real f = ((real)(cL - kk) + (real)0.5) / (real)(cL - cH);
-                key_t pv = K::enc(fL + (fH - fL) * f);
-                if (!(pv > L && pv < H)) pv = L + (key_t)((H - L) >> 1);
-                uint32_t c = 0;
-#pragma unroll
-                for (int j = 0; j < SEL_CACHE; ++j)
-                    if (j < nr) c += (va[j] >= pv ? 1u : 0u) + (vb[j] >= pv ? 1u : 0u);
-                c = grp_sum(c, G);
-                if (act) {
-                    if ((int)c >= kk) { L = pv; cL = (int)c; } else { H = pv; cH = (int)c; }
-                }
-            }
-            // exactly kk keys >= L: the answer is the smallest of them; exactly
-            // kk - 1 keys >= H: the largest key below H
-            const bool by_min = need && cL == kk, by_max = need && !by_min && cH == kk - 1;
-            if (__any_sync(FULL, by_min || by_max)) {
-                key_t lo_ge = KMAX, hi_lt = 0;
-#pragma unroll
-                for (int j = 0; j < SEL_CACHE; ++j) {
-                    if (j < nr) {
-                        const key_t a = va[j], b = vb[j];
-                        if (a >= L) lo_ge = a < lo_ge ? a : lo_ge;
-                        if (b >= L) lo_ge = b < lo_ge ? b : lo_ge;
-                        if (a < H) hi_lt = a > hi_lt ? a : hi_lt;
-                        if (b < H) hi_lt = b > hi_lt ? b : hi_lt;
-                    }
-                }
-                lo_ge = grp_min(lo_ge, G);
-                hi_lt = grp_max(hi_lt, G);
-                if (by_min) { L = lo_ge; H = lo_ge + (key_t)1; }
-                if (by_max) { L = hi_lt; H = hi_lt + (key_t)1; }
-            }
-            key_t blo = need ? L : tau, bhi = need ? H - (key_t)1 : tau;
-            while (__any_sync(FULL, blo < bhi)) {
-                const key_t mid = blo + (key_t)((bhi - blo) >> 1) + 1;
-                uint32_t c = 0;
-#pragma unroll
-                for (int j = 0; j < SEL_CACHE; ++j)
-                    if (j < nr) c += (va[j] >= mid ? 1u : 0u) + (vb[j] >= mid ? 1u : 0u);
-                c = grp_sum(c, G);
-                if (blo < bhi) {
-                    if ((int)c >= kk) blo = mid; else bhi = mid - 1;
-                }
-            }
-            tau = blo;
-        }
-        if (valid && gl == 0) out(p, tau);
-    }
-}
-
-// The bits of a value in a key-typed shared-memory slot (the warp selector reads
-// the slots back as values).
+// The bits of a value in a key-typed shared-memory slot (AB and CB hold values;
+// the selector reads them back as values).
 template <typename real>
 __device__ __forceinline__ typename KeyOf<real>::type as_key(real v);
 template <>
@@ -462,28 +287,38 @@ __device__ __forceinline__ float warp_min(float v) {
 __device__ __forceinline__ double warp_max(double v) { return grp_max(v, 32); }
 __device__ __forceinline__ double warp_min(double v) { return grp_min(v, 32); }
 
-constexpr int SEL_CAP = 12;  // AB values of a column held per lane in registers (R <= 384)
+constexpr int SEL_CAP = 12;  // most AB values of a column held per lane in registers (R <= 384)
+constexpr int SEL_STEPS = 4;  // nearest-value steps before a position falls back to the bracketed search
 
 // kk-th largest (1-based) of the 2R values of P_ABBA (eqs. 12-13) for a run of
 // consecutive tile positions p_begin .. p_begin + npos - 1, one run per warp.
 // Position p's values are AB column p (the R row-window maxima, eq. 11) and the
-// window CB[p .. p+R-1] (column maxima, eq. 10); lane l holds rows l, l+32, ...
+// window CB[p .. p+R-1] (column maxima, eq. 10); lane l holds rows l, l + 32, ...
+// of the AB column in registers (the first SEL_CAP of them; rows beyond are read
+// from shared memory) and reads its window entries CB[p + l + 32 j] where needed.
 //
-// The answer tau is tracked along the run together with the counts
-// cge = #{x >= tau} and cgt = #{x > tau}.  From one position to the next only a
-// few row-window maxima change (a window maximum changes only when it leaves the
-// window or a larger value enters) and the column window slides by one, so the
-// counts are updated from the changed values alone; tau stays the answer while
-// cgt < kk <= cge.  Otherwise a pass over all 2R values finds the counts and the
-// nearest values below and above tau and moves tau to the neighbour, up to three
-// times, then a bisection inside the bracket found so far finishes; the first
-// position of a run is found by bisection over the range of its values.  The
-// bisections run over the order-preserving integer keys of the values (their
-// midpoints are keys) but compare values, so equal values (+0 and -0 included)
-// always count together.  Control flow is uniform across the warp.
+// The answer tau is carried along the run with the counts cge = #{x >= tau} and
+// cgt = #{x > tau}; tau is the answer exactly when cgt < kk <= cge.  From one
+// position to the next only a few row-window maxima change (a window maximum
+// changes only when it leaves the window or a larger value enters) and the column
+// window exchanges two values, so the counts are updated from the changed values
+// alone.  When the rank test fails, the answer lies on one side of tau: one pass
+// finds the nearest value on that side together with its multiplicity, which moves
+// tau there with exact counts (for a move down, the values > new tau are those
+// >= old tau); this repeats up to SEL_STEPS times.  The first position of a run,
+// and a position still open after those steps, is found by a bracketed search:
+// bounds L < H with known counts #{x >= L} >= kk > #{x >= H}, a pivot that
+// interpolates their values at rank kk (bisection of the keys after eight pivots),
+// and, once a bound's count is exactly kk (or kk - 1 at H), one nearest-value pass
+// that gives the answer and its counts.  Every comparison is on values, so equal
+// values (+0 and -0 included) count together; the order-preserving keys serve only
+// the warp reductions and the midpoints.  Control flow is uniform across the warp.
 // out(p, tau) is called by one lane per position, for 32 positions at a time.
-template <typename real, typename Out>
-__device__ __forceinline__ void select_runs(const real* __restrict__ AB, int RS, int LA, int V,
+// NJ: AB rows held per lane in registers (rows lane + 32 j, j < NJ); the caller
+// picks the smallest NJ with 32 NJ >= R, or SEL_CAP (rows beyond are then read
+// from shared memory).  V: positions per AB row chunk (a power of two).
+template <int NJ, int V, typename real, typename Out>
+__device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS, int LA,
                                             const real* __restrict__ CB, int R, int kk, int p_begin,
                                             int npos, int pofs, Out out) {
     typedef KeyOf<real> K;
@@ -493,142 +328,163 @@ __device__ __forceinline__ void select_runs(const real* __restrict__ AB, int RS,
     const int nrw = (R + 31) >> 5;  // entries per lane and half (the last may be partly empty)
     const real NEG = RealLimits<real>::lowest();
     const real POS = -NEG;
-    real cur[SEL_CAP];              // AB column of the current position, rows lane + 32 j
+    // this lane's rows lane + 32 j: offsets into AB and whether the row exists
+    int roff[NJ];
+    bool rin[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int r = lane + 32 * j;
+        rin[j] = r < R;
+        roff[j] = (rin[j] ? r : 0) * RS;
+    }
+    const real* CBl = CB + lane;    // window entry j of position p: CBl[p + 32 j]
+    real cur[NJ];                   // AB column of the current position (NEG where no row)
     real tau = 0, mine = 0;
     int cge = 0, cgt = 0;
     int p = 0, cp = 0, cprev = 0;   // position; AB offsets of its column and of the previous one
 
-    // f(x) for every value of position p held by this lane: rows, then window
+    // f(x, valid) for every value of position p held by this lane: rows, then window
     auto each = [&](auto&& f) {
 #pragma unroll
-        for (int j = 0; j < SEL_CAP; ++j) {
+        for (int j = 0; j < NJ; ++j) {
+            f(cur[j], rin[j]);
+            f(rin[j] ? CBl[p + 32 * j] : NEG, rin[j]);
+        }
+        for (int j = NJ; j < nrw; ++j) {
             const int r = lane + 32 * j;
-            if (j < nrw && r < R) {
-                f(cur[j]);
-                f(CB[p + r]);
-            }
-        }
-        for (int j = SEL_CAP; j < nrw; ++j) {
-            const int r = lane + 32 * j;
-            if (r < R) {
-                f(AB[(size_t)r * RS + cp]);
-                f(CB[p + r]);
-            }
+            const bool in = r < R;
+            f(in ? AB[r * RS + cp] : NEG, in);
+            f(in ? CBl[p + 32 * j] : NEG, in);
         }
     };
-    auto count = [&]() {
-        uint32_t c = 0;
-        each([&](real x) { c += (x >= tau ? 1u : 0u) + (x > tau ? 65536u : 0u); });
-        c = __reduce_add_sync(FULL, c);
-        cge = (int)(c & 0xffffu);
-        cgt = (int)(c >> 16);
+    auto count_ge = [&](real t) {  // t > NEG: absent entries never count
+        int c = 0;
+        each([&](real x, bool) { c += x >= t ? 1 : 0; });
+        return (int)__reduce_add_sync(FULL, (unsigned)c);
     };
-    // largest key v in [lo, hi] with #{x >= value(v)} >= kk
-    auto bisect = [&](key_t lo, key_t hi) {
-        while (lo < hi) {
-            const key_t mid = lo + (key_t)((hi - lo) >> 1) + (key_t)1;
-            const real mv = K::dec(mid);
-            uint32_t c = 0;
-            each([&](real x) { c += x >= mv ? 1u : 0u; });
-            c = __reduce_add_sync(FULL, c);
-            if ((int)c >= kk) lo = mid; else hi = mid - (key_t)1;
-        }
-        return K::dec(lo);
+    // nearest value below t (max{x < t}) with its multiplicity over the position
+    auto nearest_below = [&](real t, int* mult) {
+        real best = NEG;
+        int cnt = 0;
+        each([&](real x, bool in) {
+            const bool side = in && x < t;
+            const bool better = side && x > best;
+            cnt = better ? 1 : cnt + (side && x == best ? 1 : 0);
+            best = better ? x : best;
+        });
+        const real w = warp_max(best);
+        *mult = (int)__reduce_add_sync(FULL, (unsigned)(best == w ? cnt : 0));
+        return w;
     };
-    auto range = [&](key_t* lo, key_t* hi) {
+    // nearest value above t (min{x > t}, or min{x >= t} with incl) with its multiplicity
+    auto nearest_above = [&](real t, bool incl, int* mult) {
+        real best = POS;
+        int cnt = 0;
+        each([&](real x, bool in) {
+            const bool side = in && (x > t || (incl && x == t));
+            const bool better = side && x < best;
+            cnt = better ? 1 : cnt + (side && x == best ? 1 : 0);
+            best = better ? x : best;
+        });
+        const real w = warp_min(best);
+        *mult = (int)__reduce_add_sync(FULL, (unsigned)(best == w ? cnt : 0));
+        return w;
+    };
+    // exact answer of position p by the bracketed search; sets tau, cge, cgt
+    auto search = [&]() {
         real mn = POS, mx = NEG;
-        each([&](real x) {
-            mn = x < mn ? x : mn;
+        each([&](real x, bool in) {
+            mn = in && x < mn ? x : mn;
             mx = x > mx ? x : mx;
         });
-        *lo = K::enc(warp_min(mn));
-        *hi = K::enc(warp_max(mx));
-    };
-    // tau from its previous value (the rank test has failed); leaves exact counts
-    auto retrack = [&]() {
-        key_t lo, hi;
-        bool lo_set = false, hi_set = false;
-        for (int step = 0; step < 3; ++step) {
-            uint32_t c = 0;
-            real below = NEG, above = POS;
-            each([&](real x) {
-                c += (x >= tau ? 1u : 0u) + (x > tau ? 65536u : 0u);
-                below = (x < tau && x > below) ? x : below;
-                above = (x > tau && x < above) ? x : above;
-            });
-            c = __reduce_add_sync(FULL, c);
-            cge = (int)(c & 0xffffu);
-            cgt = (int)(c >> 16);
-            if (cgt < kk && kk <= cge) return;
-            if (cge < kk) {  // the answer lies below tau
-                tau = warp_max(below);
-                hi = K::enc(tau);
-                hi_set = true;
-                if (cge == kk - 1) {
-                    count();
-                    return;
-                }
-            } else {         // above tau
-                tau = warp_min(above);
-                lo = K::enc(tau);
-                lo_set = true;
-                if (cgt == kk) {
-                    count();
-                    return;
-                }
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        key_t kL = K::enc(mn), kH = K::enc(mx) + (key_t)1;
+        int cL = 2 * R, cH = 0;  // #{x >= mn}, #{x >= the value after mx}
+        for (int it = 0; it < 64; ++it) {
+            int mult;
+            if (cL == kk) {  // the answer is the smallest value >= L
+                tau = nearest_above(K::dec(kL), true, &mult);
+                cge = cL;
+                cgt = cL - mult;
+                return;
+            }
+            if (cH == kk - 1) {  // the answer is the largest value < H
+                tau = nearest_below(K::dec(kH), &mult);
+                cgt = cH;
+                cge = cH + mult;
+                return;
+            }
+            if (kH - kL <= (key_t)1) {  // only L itself lies in [L, H)
+                tau = K::dec(kL);
+                cge = cL;
+                cgt = cH;
+                return;
+            }
+            key_t kp = kL + (key_t)((kH - kL) >> 1);
+            if (it < 8) {
+                const real vL = K::dec(kL), vH = K::dec(kH);
+                const real f = ((real)(cL - kk) + (real)0.5) / (real)(cL - cH);
+                const key_t ki = K::enc(vL + (vH - vL) * f);
+                if (ki > kL && ki < kH) kp = ki;
+            }
+            const int c = count_ge(K::dec(kp));
+            if (c >= kk) {
+                kL = kp;
+                cL = c;
+            } else {
+                kH = kp;
+                cH = c;
             }
         }
-        key_t rlo, rhi;
-        range(&rlo, &rhi);
-        tau = bisect(lo_set ? lo : rlo, hi_set ? hi : rhi);
-        count();
+        // not reached: past the eighth pivot the bracket halves every iteration
+        tau = K::dec(kL);
+        cge = cL;
+        cgt = cH;
     };
+    // contribution of one value to the packed counts (#{>= tau} + 65536 #{> tau})
+    auto cnt2 = [&](real x) { return (x >= tau ? 1 : 0) + (x > tau ? 65536 : 0); };
 
     for (int it = 0; it < npos; ++it) {
         p = p_begin + it;
         cprev = cp;
-        cp = ((p - pofs) % V) * LA + (p - pofs) / V;
+        const int q = p - pofs;
+        cp = (q & (V - 1)) * LA + q / V;
         if (it == 0) {
 #pragma unroll
-            for (int j = 0; j < SEL_CAP; ++j) {
-                const int r = lane + 32 * j;
-                cur[j] = (j < nrw && r < R) ? AB[(size_t)r * RS + cp] : NEG;
-            }
-            key_t lo, hi;
-            range(&lo, &hi);
-            tau = bisect(lo, hi);
-            count();
+            for (int j = 0; j < NJ; ++j) cur[j] = rin[j] ? AB[roff[j] + cp] : NEG;
+            search();
         } else {
             // count changes of the values that changed: rows, then the window slide
             int d = 0;
 #pragma unroll
-            for (int j = 0; j < SEL_CAP; ++j) {
+            for (int j = 0; j < NJ; ++j) {
+                const real nv = rin[j] ? AB[roff[j] + cp] : NEG;
+                d += cnt2(nv) - cnt2(cur[j]);
+                cur[j] = nv;
+            }
+            for (int j = NJ; j < nrw; ++j) {
                 const int r = lane + 32 * j;
-                if (j < nrw && r < R) {
-                    const real nv = AB[(size_t)r * RS + cp], ov = cur[j];
-                    d += ((nv >= tau) - (ov >= tau)) + 65536 * ((nv > tau) - (ov > tau));
-                    cur[j] = nv;
-                }
+                if (r < R) d += cnt2(AB[r * RS + cp]) - cnt2(AB[r * RS + cprev]);
             }
-            for (int j = SEL_CAP; j < nrw; ++j) {
-                const int r = lane + 32 * j;
-                if (r < R) {
-                    const real nv = AB[(size_t)r * RS + cp], ov = AB[(size_t)r * RS + cprev];
-                    d += ((nv >= tau) - (ov >= tau)) + 65536 * ((nv > tau) - (ov > tau));
-                }
-            }
-            if (lane == 0) {
-                const real ov = CB[p - 1];
-                d -= (ov >= tau) + 65536 * (ov > tau);
-            } else if (lane == 1) {
-                const real nv = CB[p + R - 1];
-                d += (nv >= tau) + 65536 * (nv > tau);
-            }
-            d = __reduce_add_sync(FULL, d);
+            d = (int)__reduce_add_sync(FULL, (unsigned)d) + cnt2(CB[p + R - 1]) - cnt2(CB[p - 1]);
             const int dge = (int)(int16_t)(d & 0xffff);
             cge += dge;
             cgt += (d - dge) >> 16;
-            if (!(cgt < kk && kk <= cge)) retrack();
+            // the answer moved: step to the nearest value on its side, with exact counts
+            for (int step = 0; step < SEL_STEPS && !(cgt < kk && kk <= cge); ++step) {
+                int mult;
+                if (cge < kk) {
+                    tau = nearest_below(tau, &mult);
+                    cgt = cge;
+                    cge += mult;
+                } else {
+                    tau = nearest_above(tau, false, &mult);
+                    cge = cgt;
+                    cgt -= mult;
+                }
+            }
+            if (!(cgt < kk && kk <= cge)) search();
         }
         // lane (it mod 32) keeps this position's answer; 32 positions are written at once
         if (lane == (it & 31)) mine = tau;
@@ -668,7 +524,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // row-window maxima (eq. 11), [row][position], and column maxima (eq. 10): as
     // order-preserving keys for the grouped selector (R <= 288), as values for the
     // warp selector
-    const bool keyed = R <= 32 * SEL_CACHE;
+    const bool keyed = false;  // AB and CB hold values (select_warp compares values)
     key_t* AB = (key_t*)(sm + G.off_AB);
     key_t* CB = (key_t*)(sm + G.off_CB);
     real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * LP;  // this group's [parity][V][LP]
@@ -774,8 +630,11 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     if (early_cols) load_cols();
     const real c0h = A.muh[p0], c0l = A.mul[p0];  // mean of column 0, for the left seeds
     __syncthreads();  // the barrier is initialised before anyone waits on it
+    // staged: the copies of this thread's wait completed (if not, they may still
+    // be in flight; the tile drains them before it ends)
+    const bool staged = mbar_wait_bounded(&stage_bar, 0, A.spin_limit);
     {
-        bool ok = mbar_wait_bounded(&stage_bar, 0, A.spin_limit);
+        bool ok = staged;
         if (ok && A.test_timeout) ok = mbar_wait_bounded(&stage_bar, 1, A.spin_limit);
         if (!ok) *(volatile int*)A.err = 1;
     }
@@ -1130,24 +989,19 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // this CTA's positions: pofs .. pofs + Wn - 1 of the tile
     const int pofs = crank * Wc;
     const int Wn = Wp - pofs < 0 ? 0 : (Wp - pofs < Wc ? Wp - pofs : Wc);
-    if (keyed) {
-        // groups of GS lanes, each with a run of positions; a lane caches at most
-        // SEL_CACHE values of each half
-        const int GS = G.GS;
-        const int ngroups = BD / GS;
-        const int grp = tid / GS, gl = tid % GS;
-        const int PW = (Wn + ngroups - 1) / ngroups;
-        const int pb = grp * PW;
-        const int npos = pb >= Wn ? 0 : (pb + PW <= Wn ? PW : Wn - pb);
-        select_track<key_t>(AB, RS, LA, V, CB, R, kk, pofs + pb, npos, PW, GS, gl, pofs,
-                            [&](int p, key_t kb) { emit(p, K::dec(kb)); });
-    } else {
+    {
         // one run per warp; values beyond the register cache are read from shared memory
         const int nwarps = BD >> 5;
         const int PW = (Wn + nwarps - 1) / nwarps;
         const int pb = (tid >> 5) * PW;
         const int npos = pb >= Wn ? 0 : (pb + PW <= Wn ? PW : Wn - pb);
-        select_runs<real>((const real*)AB, RS, LA, V, (const real*)CB, R, kk, pofs + pb, npos, pofs, emit);
+        const real* ABv = (const real*)AB;
+        const real* CBv = (const real*)CB;
+        if (R <= 64) select_warp<2, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 96) select_warp<3, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 160) select_warp<5, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 288) select_warp<9, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else select_warp<SEL_CAP, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
     }
     const double wmax = warp_max(tmax);
     if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(wmax));
@@ -1179,6 +1033,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             }
         }
     }
+    // A staging wait that ran out may leave bulk copies (and their transaction
+    // counts) in flight into this CTA's shared memory; they must not land after
+    // the CTA has ended, in shared memory that another CTA may own by then.  Wait
+    // for them again (bounded), then retire the barrier.  If that wait runs out
+    // too, the barrier is left as it is (the error flag is already set).
+    const bool drained = __syncthreads_and(staged) || mbar_wait_bounded(&stage_bar, 0, A.spin_limit);
+    if (__syncthreads_and(drained) && tid == 0) mbar_inval(&stage_bar);
 }
 
 // Streaming form over segments s_begin .. s_begin + gridDim.y - 1: grid (ntiles CS, segments).

@@ -98,6 +98,8 @@ def load(path: str | None = None):
         lib.pastila_profiles.restype = S
         lib.pastila_profiles_device.argtypes = [_vp, ctypes.c_int32, MParams, _vp, _vp]
         lib.pastila_profiles_device.restype = S
+        lib.pastila_stage_status.argtypes = [_vp]
+        lib.pastila_stage_status.restype = S
         lib.pastila_snippets.argtypes = [_vp, ctypes.c_int32, MParams, ctypes.c_int32,
                                          ctypes.POINTER(Snippet), _vp, _vp]
         lib.pastila_snippets.restype = S
@@ -267,6 +269,11 @@ class Series:
         """Enqueue D into a device buffer (``pastila_profiles_device``)."""
         _check(load().pastila_profiles_device(self._h, m, MParams(ell, k), _vp(D_ptr),
                                               _vp(dmax_ptr) if dmax_ptr else None))
+
+    def stage_status(self):
+        """``pastila_stage_status``: raise if a staging wait of enqueued tile work ran
+        out (call after synchronising the handle's stream)."""
+        _check(load().pastila_stage_status(self._h))
 
     def snippets(self, m: int, K: int, ell: int = 0, k: int = 0, want_labels: bool = False,
                  want_profiles: bool = False):

@@ -28,14 +28,14 @@ def _force(pastila, prec, m, ell, k, W, NG, GS, CS=2):
     assert pastila.tune_get(prec, m, ell, k) == (W, NG, GS, CS)
 
 
-# (n, m, ell, k, W, NG, GS, CS): R = 65, 101, 129 (grouped selector), 321 (warp
-# selector) with a ragged last tile and a tail segment
+# (n, m, ell, k, W, NG, GS, CS): R = 65, 101, 129 (rows held in 3-5 registers per
+# lane) and 321 (beyond the register cache), with a ragged last tile and a tail segment
 CLUSTER_CASES = [
-    (4096, 128, 64, 13, 256, 2, 8, 2),
-    (3001, 200, 100, 20, 192, 2, 16, 2),
-    (5003, 256, 128, 26, 192, 3, 16, 2),
+    (4096, 128, 64, 13, 256, 2, 32, 2),
+    (3001, 200, 100, 20, 192, 2, 32, 2),
+    (5003, 256, 128, 26, 192, 3, 32, 2),
     (4000, 640, 320, 64, 64, 2, 32, 2),
-    (5003, 256, 128, 26, 256, 2, 16, 4),
+    (5003, 256, 128, 26, 256, 2, 32, 4),
     (4000, 640, 320, 64, 128, 2, 32, 4),
 ]
 
@@ -62,10 +62,10 @@ def test_sweep_mixing_one_and_two_cta_tiles(table):
     pastila = table
     s = synth.four_regimes(per_regime=750)  # n = 3000
     ms, K = [96, 128, 160, 192, 256], 3
-    _force(pastila, 0, 96, 48, 10, 608, 1, 8, CS=1)
-    _force(pastila, 0, 128, 64, 13, 192, 2, 8)
-    _force(pastila, 0, 192, 96, 20, 160, 2, 16)
-    _force(pastila, 0, 256, 128, 26, 256, 2, 16, CS=4)
+    _force(pastila, 0, 96, 48, 10, 608, 1, 32, CS=1)
+    _force(pastila, 0, 128, 64, 13, 192, 2, 32)
+    _force(pastila, 0, 192, 96, 20, 160, 2, 32)
+    _force(pastila, 0, 256, 128, 26, 256, 2, 32, CS=4)
     with pastila.Series(s.T, precision=pastila.FP32) as h:
         assert [h.tile_layout(m)["CS"] for m in ms] == [1, 2, 1, 2, 4]
         runs = [h.select_length(ms, K) for _ in range(3)]  # direct, captured, replayed
@@ -85,8 +85,8 @@ def test_engine_with_cluster_tiles(table):
     rng = np.random.default_rng(77)
     T = synth.random_planted(rng, 30_000, 4).T
     ms, K = [128, 160, 256, 384], 4
-    _force(pastila, 0, 128, 64, 13, 256, 2, 8)
-    _force(pastila, 0, 256, 128, 26, 192, 3, 16)
+    _force(pastila, 0, 128, 64, 13, 256, 2, 32)
+    _force(pastila, 0, 256, 128, 26, 192, 3, 32)
     _force(pastila, 0, 384, 192, 39, 384, 2, 32, CS=4)
     with pastila.Series(T, precision=pastila.FP32) as h:
         ref = h.select_length(ms, K)
@@ -102,10 +102,10 @@ def test_engine_with_cluster_tiles(table):
 def test_tune_set_argument_errors(lib):
     from paper_2401_13680_b300 import pastila
     with pytest.raises(pastila.PastilaError, match="CS = 3"):
-        pastila.tune_set(0, 128, 64, 13, 256, 2, 8, 3)
+        pastila.tune_set(0, 128, 64, 13, 256, 2, 32, 3)
     with pytest.raises(pastila.PastilaError, match="multiple of 32"):
-        pastila.tune_set(0, 128, 64, 13, 250, 2, 8, 1)
-    with pytest.raises(pastila.PastilaError, match="GS = 4 holds"):
+        pastila.tune_set(0, 128, 64, 13, 250, 2, 32, 1)
+    with pytest.raises(pastila.PastilaError, match="GS = 4: the selection runs one warp"):
         pastila.tune_set(0, 128, 64, 13, 256, 2, 4, 1)
     with pytest.raises(pastila.PastilaError, match="no tuned layout"):
         pastila.tune_get(0, 123, 61, 13)
@@ -124,8 +124,8 @@ def test_two_ctas_per_sm_layouts(table):
         l0 = h.kernel_launches()
         h.select_length(ms, K)
         base_launches = h.kernel_launches() - l0
-    _force(pastila, 0, 64, 32, 7, 480, 2, 4, CS=1)
-    _force(pastila, 0, 128, 64, 13, 320, 2, 8, CS=1)
+    _force(pastila, 0, 64, 32, 7, 480, 2, 32, CS=1)
+    _force(pastila, 0, 128, 64, 13, 320, 2, 32, CS=1)
     with pastila.Series(s.T, precision=pastila.FP32) as h:
         for m in (64, 128):
             lay = h.tile_layout(m)

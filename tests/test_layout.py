@@ -25,17 +25,16 @@ def test_cost_model_layouts_obey_the_kernel_constraints(prec, n):
             assert lay["Rh"] == -(-R // lay["CS"])
             assert lay["NG"] * lay["Rg"] >= lay["Rh"] and (lay["NG"] - 1) * lay["Rg"] < lay["Rh"]
             assert lay["NG"] == 1 or lay["Rg"] >= 4
-            if R <= 288:  # the grouped selector keeps a column's values in its lanes' registers
-                assert lay["GS"] in (4, 8, 16, 32) and lay["GS"] * 9 >= R
+            assert lay["GS"] == 32  # one warp per run of positions
 
 
 def test_tuned_entries_are_used_when_they_fit():
     pastila.tune_clear()
     try:
         model = pastila.plan_layout(pastila.FP32, 100_000, 256, SMEM)
-        pastila.tune_set(pastila.FP32, 256, 128, 26, 320, 2, 16, 2)
+        pastila.tune_set(pastila.FP32, 256, 128, 26, 320, 2, 32, 2)
         lay = pastila.plan_layout(pastila.FP32, 100_000, 256, SMEM)
-        assert (lay["W"], lay["CS"], lay["GS"]) == (320, 2, 16)
+        assert (lay["W"], lay["CS"], lay["GS"]) == (320, 2, 32)
         # the same entry does not fit a small budget: the cost model decides
         small = pastila.plan_layout(pastila.FP32, 100_000, 256, 64 * 1024)
         assert small["bytes"] <= 64 * 1024 and (small["W"], small["CS"]) != (320, 2)

@@ -5,13 +5,13 @@ The tile geometry (array sizes and offsets in shared memory) is restated here
 and pinned to the library's own by the byte count pastila_plan_layout reports.
 The index expressions of the rows phase (prefix, chunk and sparse-table
 maxima, the exchange between warps, the row-window maxima written into the
-owning CTA), of the k-th selection (the grouped selector for R <= 288 and the
-warp selector beyond, idle groups included) and the sizes of the staging
-copies are then evaluated for every thread, position, cluster
-rank, partial last tile and block size a launch can have, and every index
-must fall inside its array.  A mistake of the kind this guards against is
-planted in the checker itself (an idle group reading tile position 0 instead
-of its CTA's first position) and must be caught."""
+owning CTA), of the k-th selection (one run of positions per warp) and the
+sizes of the staging copies are then evaluated for every thread, position,
+cluster rank, partial last tile and block size a launch can have, and every
+index must fall inside its array.  A mistake of the kind this guards against is
+planted in the checker itself (a run that applied the column window's slide
+at its first position, reading the window entry before it) and must be
+caught."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,6 @@ from paper_2401_13680_b300 import pastila
 
 SMEM = 232448 - 1024  # B300 opt-in shared memory per block, less the static shared memory
 V = 4                 # columns per thread, both precisions
-SEL_CACHE = 9         # keys of one position per lane and half in the grouped selector
 
 
 def _a16(x):
@@ -57,53 +56,36 @@ def _tdiv(a, b):
     return q, a - q * b
 
 
-def selection_reads(G, BD, crank, Wp, idle_position=None):
+def selection_reads(G, BD, crank, Wp, slide_at_start=False):
     """(AB index range, CB index range) over every read of the selection phase of
-    CTA crank of a tile with Wp positions, launched with BD threads."""
+    CTA crank of a tile with Wp positions, launched with BD threads: one run of
+    consecutive positions per warp; lane l reads rows l + 32 j of each position's
+    AB column and its window entries p + l + 32 j, and every position after a
+    run's first also reads the window entries that leave (p - 1) and enter
+    (p + R - 1).  slide_at_start plants the mistake of sliding the window at a
+    run's first position as well."""
     R, Wc, LA, RS = G["R"], G["Wc"], G["LA"], G["RS"]
     pofs = crank * Wc
     Wn = max(0, min(Wp - pofs, Wc))
-    ab, cb = [], []
-    if R <= 32 * SEL_CACHE:  # grouped selector
-        GS = G["GS"]
-        ngroups = BD // GS
-        PW = (Wn + ngroups - 1) // ngroups
-        if PW == 0:
-            return None, None
-        tid = np.arange(BD)[:, None, None]
-        grp, gl = tid // GS, tid % GS
-        pb = grp * PW
-        npos = np.where(pb >= Wn, 0, np.where(pb + PW <= Wn, PW, Wn - pb))
-        it = np.arange(PW)[None, :, None]
-        j = np.arange(SEL_CACHE)[None, None, :]
-        valid = it < npos
-        idle = pofs if idle_position is None else idle_position
-        p = np.where(valid, pofs + pb + it, idle)
-        nr = (R - gl + GS - 1) // GS
-        load = j < nr
+    nwarps = BD >> 5
+    PW = (Wn + nwarps - 1) // nwarps
+    if PW == 0:
+        return None, None
+    ab_l, cb_l = [], []
+    for w in range(nwarps):
+        pb = w * PW
+        npos = 0 if pb >= Wn else min(PW, Wn - pb)
+        if npos == 0:
+            continue
+        p = pofs + pb + np.arange(npos)
         q, r = _tdiv(p - pofs, V)
-        col = r * LA + q + gl * RS
-        ab = (col + j * GS * RS)[np.broadcast_to(load, (BD, PW, SEL_CACHE))]
-        cb = (p + gl + j * GS)[np.broadcast_to(load, (BD, PW, SEL_CACHE))]
-    else:  # one run per warp
-        nwarps = BD >> 5
-        PW = (Wn + nwarps - 1) // nwarps
-        if PW == 0:
-            return None, None
-        ab_l, cb_l = [], []
-        for w in range(nwarps):
-            pb = w * PW
-            npos = 0 if pb >= Wn else min(PW, Wn - pb)
-            if npos == 0:
-                continue
-            p = pofs + pb + np.arange(npos)
-            q, r = _tdiv(p - pofs, V)
-            cp = r * LA + q  # AB column of each position; rows at multiples of RS
-            ab_l += [cp.min(), (R - 1) * RS + cp.max()]
-            cb_l += [p.min(), p.max() + R - 1]
-            if npos > 1:
-                cb_l += [p[1:].min() - 1]
-        ab, cb = np.array(ab_l), np.array(cb_l)
+        cp = r * LA + q  # AB column of each position; rows at multiples of RS
+        ab_l += [cp.min(), (R - 1) * RS + cp.max()]
+        cb_l += [p.min(), p.max() + R - 1]
+        slid = p if slide_at_start else p[1:]
+        if slid.size:
+            cb_l += [slid.min() - 1]
+    ab, cb = np.array(ab_l), np.array(cb_l)
     return (int(np.min(ab)), int(np.max(ab))), (int(np.min(cb)), int(np.max(cb)))
 
 
@@ -245,8 +227,8 @@ def test_cost_model_layouts_stay_in_bounds(prec):
 
 @pytest.mark.parametrize("CS", [1, 2, 4])
 def test_tuned_layouts_stay_in_bounds(CS):
-    """Layouts forced through the tuned table: every width and selection group
-    width the tuner can choose, with one, two and four CTAs per tile."""
+    """Layouts forced through the tuned table: every width and row-group count
+    the tuner can choose, with one, two and four CTAs per tile."""
     pastila.tune_clear()
     checked = 0
     try:
@@ -256,23 +238,20 @@ def test_tuned_layouts_stay_in_bounds(CS):
             R = m - ell + 1
             for W in range(32 * CS, 1025, 32 * CS):
                 for NGw in (1, 2, 3, 4):
-                    for GS in (4, 8, 16, 32):
-                        if R <= 32 * SEL_CACHE and R > GS * SEL_CACHE:
-                            continue
-                        pastila.tune_set(pastila.FP32, m, ell, k, W, NGw, GS, CS)
-                        lay = pastila.plan_layout(pastila.FP32, 1_000_000, m, SMEM, ell=ell, k=k)
-                        if (lay["W"], lay["CS"], lay["GS"]) != (W, CS, GS):
-                            continue  # does not fit: the cost model decides instead
-                        check_layout(pastila.FP32, m, ell, lay)
-                        checked += 1
+                    pastila.tune_set(pastila.FP32, m, ell, k, W, NGw, 32, CS)
+                    lay = pastila.plan_layout(pastila.FP32, 1_000_000, m, SMEM, ell=ell, k=k)
+                    if (lay["W"], lay["CS"]) != (W, CS):
+                        continue  # does not fit: the cost model decides instead
+                    check_layout(pastila.FP32, m, ell, lay)
+                    checked += 1
     finally:
         pastila.tune_clear()
     assert checked > 20
 
 
-def test_checker_catches_an_idle_group_reading_tile_position_zero():
-    """An idle group of the second CTA of a cluster that read tile position 0
-    would index its CTA's AB array before its start."""
+def test_checker_catches_a_window_slide_at_a_run_start():
+    """A run that slid the column window at its first position would read the
+    window entry before the first position of the tile (index -1 of CB)."""
     pastila.tune_clear()
     m, ell = 512, 256
     try:
@@ -282,8 +261,8 @@ def test_checker_catches_an_idle_group_reading_tile_position_zero():
         pastila.tune_clear()
     G = geometry(pastila.FP32, m, ell, lay)
     assert G["CS"] == 2
-    Wp = G["W"] - 5  # a partial tile: some groups idle for their last steps
-    good, _ = selection_reads(G, G["NT"], 1, Wp)
-    bad, _ = selection_reads(G, G["NT"], 1, Wp, idle_position=0)
+    Wp = G["W"] - 5  # a partial tile
+    _, good = selection_reads(G, G["NT"], 0, Wp)
+    _, bad = selection_reads(G, G["NT"], 0, Wp, slide_at_start=True)
     assert good[0] >= 0
     assert bad[0] < 0

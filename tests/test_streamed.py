@@ -90,7 +90,7 @@ def test_streamed_with_cluster_tiles(lib):
     m, K = 256, 5
     pastila.tune_clear()
     try:
-        pastila.tune_set(pastila.FP32, m, m // 2, (m + 9) // 10, 256, 2, 16, 2)
+        pastila.tune_set(pastila.FP32, m, m // 2, (m + 9) // 10, 256, 2, 32, 2)
         with pastila.Series(T, precision=pastila.FP32) as h:
             assert h.tile_layout(m)["CS"] == 2
         ref, got = _both(pastila, T, m, K, 0)

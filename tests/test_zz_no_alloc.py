@@ -30,6 +30,7 @@ def test_greedy_noalloc_matches_snippets(lib):
             D = torch.empty((S, P), dtype=torch.float32, device=dev)
             h.profiles_device(m, D.data_ptr())
             torch.cuda.synchronize()
+            h.stage_status()  # the enqueue-only call's staging waits completed
             chosen = torch.full((K,), -1, dtype=torch.int32, device=dev)
             area = torch.zeros(K, dtype=torch.float64, device=dev)
             pastila.greedy_noalloc(D.data_ptr(), S, P, K, chosen.data_ptr(), area.data_ptr(),
