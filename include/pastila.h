@@ -162,6 +162,19 @@ pastila_status pastila_snippets(pastila_series* h, int32_t m, pastila_mparams mp
                                 pastila_snippet* out, int32_t* labels_out,
                                 void* snippet_profiles_out);
 
+/* Greedy decisions of FP32 handles (snippets, select_length).  The FP32
+ * profiles are accurate to |rho - rho64| <= 2e-6 cell by cell, i.e.
+ * |d^2 - d64^2| <= 4e-6 ell (the FP32 tiles recompute ill-conditioned cells
+ * exactly to keep it), so each FP32 area of a greedy step has a bound on its
+ * distance from the FP64 area of the paper's definitions.  With on = 1 (the default), a step that leaves
+ * more than one segment within those bounds of the smallest FP32 area is
+ * decided on FP64 areas of FP64 profile rows (of up to 16 contenders, those with
+ * the smallest FP32 areas, and of the segments chosen before), lowest index on
+ * ties, so that the chosen segments are those of an FP64 search; area_after of
+ * such a step is its FP64 area.  With on = 0 every step is decided on the FP32
+ * areas alone.  No effect on FP64 handles.  Errors: EINVAL (NULL handle). */
+pastila_status pastila_set_fp64_ties(pastila_series* h, int on);
+
 /* --------------------------------------------- length selection (eq. 18) ---- */
 
 /* PaSTiLa's length criterion over a sweep (Section 4.2, eq. 18): for every m in
@@ -256,6 +269,10 @@ typedef struct {
                                     proportion to 1 + (time since submission) / age_weight_s, which moves
                                     the engine from processor sharing toward arrival order */
     int32_t policy;              /* pastila_policy; 0: PASTILA_POLICY_SHARE */
+    int32_t fp32_greedy;         /* FP32 engines: 0 (default) decides near-tied greedy steps on FP64 areas,
+                                    as select_length does (pastila_set_fp64_ties); 1 decides every step on
+                                    the FP32 areas alone (no FP64 rows: wave times then depend only on the
+                                    wave's work, not on how many steps are near-ties) */
 } pastila_engine_config;
 
 typedef enum {

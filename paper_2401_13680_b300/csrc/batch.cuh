@@ -19,10 +19,45 @@
 
 namespace pastila {
 
+// FP64 re-evaluation of near-tied greedy steps (FP32 items).  The FP32 profiles
+// are accurate to |d rho| <= 2e-6 cell by cell (the tolerance rule's bound
+// below d_floor, which the FP32 tiles meet at every cell: they recompute the
+// ill-conditioned ones exactly), hence every FP32 area of a step is within
+// E_s = sum_p b(min(M_p, D_s(p))) of the FP64 area the oracle computes, b the
+// per-value bound of row_bound_partial.
+// When more segments than the FP32 minimum lie within the bounds of it, the
+// step is decided on FP64 areas: FP64 rows of those contenders (at most
+// REF_NCAND, those with the smallest FP32 areas) and of every earlier chosen
+// segment come from the FP64 tile kernel, and the curve M of FP64 rows gives
+// the FP64 areas (lowest segment index on ties).
+constexpr int REF_NCAND = 16;
+constexpr int REF_TODO_GRID = 4;   // grid rows of the FP64 row launch (each loops over the to-do list)
+// layout of an item's refinement state (int32):
+constexpr int REF_TODO_N = 0;      // rows the next FP64 row launch computes
+constexpr int REF_NC = 1;          // contenders of the current step (0: decided in FP32)
+constexpr int REF_HAS = 4;         // [64]: 1 when rows64 slot t holds chosen segment t's FP64 row
+constexpr int REF_TODO_SEG = 68;   // [64 + REF_NCAND]: segments of the to-do rows
+constexpr int REF_TODO_SLOT = REF_TODO_SEG + 64 + REF_NCAND;  // and their rows64 slots
+constexpr int REF_CAND = REF_TODO_SLOT + 64 + REF_NCAND;       // [REF_NCAND] contenders, ascending index
+constexpr int REF_STATE_INTS = REF_CAND + REF_NCAND;
+
 template <typename real>
 struct BatchItem {
     ProfileArgs<real> A;   // profile arguments (series, statistics, D, D max key)
     TileGeom G;            // tile layout of this item
+    // FP64 re-evaluation (rows64 == nullptr: off): FP64 profile arguments of
+    // the same length (their D is rows64; their D max key a scratch word), the
+    // FP64 tile layout, (K + REF_NCAND) x P FP64 rows (slot t < K: chosen
+    // segment t; slot K + c: contender c), the S FP32 area bounds of the step,
+    // the contenders' FP64 areas, the state above and the constant c of
+    // row_bound_partial (2.2 ell times 2e-6)
+    ProfileArgs<double> A64;
+    TileGeom G64;
+    double* rows64;
+    float* bound;
+    double* cand_area;
+    int32_t* rst;
+    float bc;
     long long cta_begin;   // first CTA of this item in the flattened tile grid (even for cluster tiles)
     long long ctas;        // its CTA count (CTAs past it, alignment padding, do nothing)
     int s_begin;           // first segment of this launch's share of the item (the
@@ -77,8 +112,239 @@ __global__ void __launch_bounds__(AREA_THREADS) batched_area_kernel(const BatchI
         if (threadIdx.x == 0) it.area[s] = __longlong_as_double(0x7ff0000000000000ll);
         return;
     }
-    const double tot = block_sum(row_min_partial(it.A.D + (int64_t)s * P, t == 0 ? (const real*)nullptr : it.M, P), red);
+    const real* row = it.A.D + (int64_t)s * P;
+    const real* M = t == 0 ? (const real*)nullptr : it.M;
+    const double tot = block_sum(row_min_partial(row, M, P), red);
     if (threadIdx.x == 0) it.area[s] = tot;
+    if (it.rows64) {  // the error bound of this area (FP32 items with refinement), 2 % margin
+        const double e = block_sum((double)row_bound_partial(row, M, P, it.bc), red);
+        if (threadIdx.x == 0) it.bound[s] = (float)(1.02 * e);
+    }
+}
+
+// The greedy choice of step t for every item (one CTA of 1024 per item): the
+// FP32 argmin (lowest index on ties), exactly as batched_argmin_kernel.  Items
+// with refinement then count the contenders, the unchosen segments whose FP32
+// area is within the two error bounds (and a 1e-9 relative margin for the
+// rounding of the FP64 sums) of the minimum; one contender decides the step
+// here; otherwise up to REF_NCAND contenders with the smallest FP32 areas
+// (lowest index on ties) and every earlier chosen segment without an FP64 row go
+// on the to-do list of the FP64 row launch, and batched_choose_update_kernel
+// decides.
+template <typename real>
+__global__ void batched_select_kernel(const BatchItem<real>* __restrict__ items, int t) {
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    __shared__ int picked[REF_NCAND];
+    const BatchItem<real>& it = items[blockIdx.x];
+    if (t >= it.K) return;
+    const int S = it.A.S;
+    const int tid = threadIdx.x;
+    auto chosen_before = [&](int s) {
+        bool c = false;
+        for (int u = 0; u < t; ++u) c |= it.chosen[u] == s;
+        return c;
+    };
+    // block argmin of key(s) over the segments admit(s) accepts (lowest index on ties)
+    auto block_argmin = [&](auto&& key, auto&& admit, double* bestv) {
+        double best = __longlong_as_double(0x7ff0000000000000ll);
+        int bidx = 0x7fffffff;
+        for (int s = tid; s < S; s += blockDim.x) {
+            if (!admit(s)) continue;
+            const double a = key(s);
+            if (a < best || (a == best && s < bidx)) {
+                best = a;
+                bidx = s;
+            }
+        }
+        bv[tid] = best;
+        bi[tid] = bidx;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (tid < w) {
+                const double ov = bv[tid + w];
+                const int oi = bi[tid + w];
+                if (ov < bv[tid] || (ov == bv[tid] && oi < bi[tid])) {
+                    bv[tid] = ov;
+                    bi[tid] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        const int r = bi[0];
+        *bestv = bv[0];
+        __syncthreads();
+        return r;
+    };
+    double Ab;
+    const int b = block_argmin([&](int s) { return it.area[s]; }, [&](int s) { return !chosen_before(s); }, &Ab);
+    if (!it.rows64) {
+        if (tid == 0) {
+            it.chosen[t] = b;
+            it.area_after[t] = Ab;
+        }
+        return;
+    }
+    int32_t* rst = it.rst;
+    if (t == 0) {  // a new search: no chosen segment has an FP64 row yet
+        for (int u = tid; u < 64; u += blockDim.x) rst[REF_HAS + u] = 0;
+        __syncthreads();
+    }
+    const double Eb = (double)it.bound[b];
+    auto contender = [&](int s) {
+        return !chosen_before(s) && it.area[s] - Ab <= Eb + (double)it.bound[s] + 1e-9 * Ab;
+    };
+    int cnt = 0;
+    for (int s = tid; s < S; s += blockDim.x) cnt += contender(s) ? 1 : 0;
+    bi[tid] = cnt;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (tid < w) bi[tid] += bi[tid + w];
+        __syncthreads();
+    }
+    cnt = bi[0];
+    __syncthreads();
+    if (cnt <= 1) {
+        if (tid == 0) {
+            it.chosen[t] = b;
+            it.area_after[t] = Ab;
+            rst[REF_TODO_N] = 0;
+            rst[REF_NC] = 0;
+            rst[REF_HAS + t] = 0;
+        }
+        return;
+    }
+    const int nc = cnt < REF_NCAND ? cnt : REF_NCAND;
+    for (int c = 0; c < nc; ++c) {
+        double v;
+        const int s = block_argmin([&](int q) { return it.area[q]; },
+                                   [&](int q) {
+                                       if (!contender(q)) return false;
+                                       for (int u = 0; u < c; ++u)
+                                           if (picked[u] == q) return false;
+                                       return true;
+                                   },
+                                   &v);
+        if (tid == 0) picked[c] = s;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        for (int i = 1; i < nc; ++i) {  // ascending segment index
+            const int x = picked[i];
+            int j = i - 1;
+            while (j >= 0 && picked[j] > x) {
+                picked[j + 1] = picked[j];
+                --j;
+            }
+            picked[j + 1] = x;
+        }
+        int n = 0;
+        for (int u = 0; u < t; ++u) {
+            if (!rst[REF_HAS + u]) {
+                rst[REF_TODO_SEG + n] = it.chosen[u];
+                rst[REF_TODO_SLOT + n] = u;
+                rst[REF_HAS + u] = 1;  // filled by the row launch that follows
+                ++n;
+            }
+        }
+        for (int c = 0; c < nc; ++c) {
+            rst[REF_CAND + c] = picked[c];
+            rst[REF_TODO_SEG + n] = picked[c];
+            rst[REF_TODO_SLOT + n] = it.K + c;
+            ++n;
+        }
+        rst[REF_TODO_N] = n;
+        rst[REF_NC] = nc;
+        rst[REF_HAS + t] = 0;
+    }
+}
+
+// FP64 rows of an item's to-do list (one item per launch): grid (ntiles64 CS64,
+// REF_TODO_GRID); each CTA computes tile blockIdx.x / CS64 of to-do rows
+// blockIdx.y, blockIdx.y + REF_TODO_GRID, ...  Row y goes to rows64 slot
+// todo_slot[y] (the profile tile writes row s - row_base of its D).
+template <int V>
+__global__ void __launch_bounds__(512) refine_rows_kernel(const BatchItem<float>* __restrict__ item, int t) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (t >= item->K || !item->rows64) return;
+    const int32_t* rst = item->rst;
+    const int n = rst[REF_TODO_N];
+    for (int y = blockIdx.y; y < n; y += gridDim.y) {
+        const int seg = rst[REF_TODO_SEG + y], slot = rst[REF_TODO_SLOT + y];
+        profile_tile<double, V>(item->A64, item->G64, seg, (int)blockIdx.x / item->G64.CS, smem, seg - slot);
+        __syncthreads();
+    }
+}
+
+// FP64 areas of the contenders of step t: cand_area[c] = sum_p min(M64_p,
+// row64_c(p)), M64 = the minimum of the FP64 rows of the chosen segments 0 .. t-1
+// (+inf at step 0).  Grid (REF_NCAND, n items), AREA_THREADS threads.
+template <typename real>
+__global__ void __launch_bounds__(AREA_THREADS) batched_refine_area_kernel(const BatchItem<real>* __restrict__ items,
+                                                                           int t) {
+    __shared__ double red[AREA_THREADS / 32];
+    const BatchItem<real>& it = items[blockIdx.y];
+    const int c = blockIdx.x;
+    if (t >= it.K || !it.rows64 || c >= it.rst[REF_NC]) return;
+    const int64_t P = it.A.P;
+    const double* R64 = it.rows64;
+    const double* row = R64 + (int64_t)(it.K + c) * P;
+    double a0 = 0.0, a1 = 0.0;
+    int64_t p = threadIdx.x;
+    auto term = [&](int64_t q) {
+        double v = row[q];
+        for (int u = 0; u < t; ++u) {
+            const double w = R64[(int64_t)u * P + q];
+            v = w < v ? w : v;
+        }
+        return v;
+    };
+    for (; p + AREA_THREADS < P; p += 2 * AREA_THREADS) {
+        a0 += term(p);
+        a1 += term(p + AREA_THREADS);
+    }
+    for (; p < P; p += AREA_THREADS) a0 += term(p);
+    const double tot = block_sum(a0 + a1, red);
+    if (threadIdx.x == 0) it.cand_area[c] = tot;
+}
+
+// Decides a step that went to FP64 (the smallest FP64 area, lowest segment index
+// on ties: the contenders are in ascending index order), keeps the chosen
+// segment's FP64 row in slot t, and updates the FP32 curve M <- min(M, D_chosen)
+// (not after the last step).  Every CTA takes the decision itself.  Grid
+// (ceil(max P / 256), n items).
+template <typename real>
+__global__ void batched_choose_update_kernel(const BatchItem<real>* __restrict__ items, int t) {
+    const BatchItem<real>& it = items[blockIdx.y];
+    if (t >= it.K) return;
+    const int64_t P = it.A.P;
+    const bool refined = it.rows64 && it.rst[REF_NC] > 0;
+    int seg, best = 0;
+    if (refined) {
+        const int nc = it.rst[REF_NC];
+        for (int c = 1; c < nc; ++c)
+            if (it.cand_area[c] < it.cand_area[best]) best = c;
+        seg = it.rst[REF_CAND + best];
+    } else {
+        seg = it.chosen[t];
+    }
+    if (refined && blockIdx.x == 0 && threadIdx.x == 0) {
+        it.chosen[t] = seg;
+        it.area_after[t] = it.cand_area[best];
+        it.rst[REF_HAS + t] = 1;
+    }
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    if (refined) it.rows64[(int64_t)t * P + p] = it.rows64[(int64_t)(it.K + best) * P + p];
+    if (t + 1 < it.K) {
+        const real d = it.A.D[(int64_t)seg * P + p];
+        if (t == 0) {
+            it.M[p] = d;
+        } else {
+            const real mm = it.M[p];
+            it.M[p] = d < mm ? d : mm;
+        }
+    }
 }
 
 // argmin of step t for every item: one CTA of 1024 per item

@@ -174,6 +174,12 @@ struct EStats {
     void* dg = nullptr;
     void* muh = nullptr;  // mu as hi + lo pairs
     void* mul = nullptr;
+    // FP64 terms of an FP32 engine's jobs (the greedy re-evaluation's FP64 rows)
+    void* a64 = nullptr;
+    void* df64 = nullptr;
+    void* dg64 = nullptr;
+    void* muh64 = nullptr;
+    void* mul64 = nullptr;
 };
 
 struct EItem {
@@ -184,8 +190,12 @@ struct EItem {
     int state = 0;        // 0 waiting, 1 tiles in progress, 2 tiles all issued, 3 greedy issued
     int next_seg = 0;
     double cells_per_seg = 0.0;  // ED cells (halo included) of one segment's tiles
-    void* dblock = nullptr;      // D, M, area
+    void* dblock = nullptr;      // D, M, area (and, in FP32 engines, the greedy re-evaluation's buffers)
     size_t dbytes = 0;
+    TileGeom g64{};              // FP64 tile layout of the re-evaluation's rows (FP32 engines)
+    float* kappa = nullptr;      // FP32 engines: the windows' conditioning ratios for this length's R
+    void* refine = nullptr;      // refine_bytes of the re-evaluation, then its state words
+    int32_t* rst = nullptr;
     void* D = nullptr;
     void* M = nullptr;
     double* area = nullptr;
@@ -214,6 +224,8 @@ struct EJob {
     double* T_dev = nullptr;
     void* Th = nullptr;  // T as hi + lo pairs (written with every length's statistics)
     void* Tl = nullptr;
+    void* Th64 = nullptr;  // T as FP64 pairs (value, 0), FP32 engines
+    void* Tl64 = nullptr;
     double* inv = nullptr;
     int32_t* flat = nullptr;
     int32_t* ms_dev = nullptr;
@@ -273,6 +285,7 @@ struct pastila_engine {
     double wave_cells = 0.0;
     double age_weight = 0.0;
     int policy = PASTILA_POLICY_SHARE;
+    bool refine = true;  // FP32: near-tied greedy steps decided on FP64 areas
     int fail_at = 0;
     int* err = nullptr;  // host-mapped flag the tile kernels set when a bounded wait runs out
     long long spin_limit = 1ll << 31;
@@ -387,6 +400,10 @@ pastila_status plan_job(pastila_engine* e, EJob& j, pastila_mparams rule) {
         it.stats = si;
         it.dbytes = up256e(rs * (size_t)it.q.S * (size_t)it.q.P) + up256e(rs * (size_t)it.q.P) +
                     up256e(8 * (size_t)it.q.S);
+        if (std::is_same<real, float>::value && e->refine) {  // the greedy re-evaluation's FP64 rows and state
+            TRY(choose_tile_s<double, V_F64>((size_t)e->smem_optin, it.q, &it.g64));
+            it.dbytes += refine_bytes(it.q, j.K) + up256e(4 * REF_STATE_INTS);
+        }
         j.max_dbytes = std::max(j.max_dbytes, it.dbytes);
         j.ed_cells += it.cells_per_seg * it.q.S;
         j.profile_cells += (double)it.q.S * (double)it.q.P;
@@ -396,14 +413,19 @@ pastila_status plan_job(pastila_engine* e, EJob& j, pastila_mparams rule) {
         return fail(PASTILA_EINVAL, "K = %d: must satisfy 2 <= K <= min(n / max m, 64) = %d", K, std::min(min_S, 64));
     j.Cmax = 0;
     // the tile kernels' bulk copies may read up to 16 bytes past an array's end
+    const bool refine = std::is_same<real, float>::value && e->refine;  // FP64 statistics for the greedy re-evaluation
     size_t b = up256e(8 * (size_t)j.n) + 2 * up256e(rs * (size_t)(j.n + ARRAY_PAD));
+    if (refine) b += 2 * up256e(8 * (size_t)(j.n + ARRAY_PAD));
     for (auto& st : j.stats) {
         j.Cmax = std::max(j.Cmax, st.C);
         b += up256e(8 * (size_t)st.C) + 5 * up256e(rs * (size_t)(st.C + ARRAY_PAD));
+        if (refine) b += 5 * up256e(8 * (size_t)(st.C + ARRAY_PAD));
     }
     b += up256e(8 * (size_t)j.Cmax) + up256e(4 * (size_t)j.Cmax);
     b += up256e(8 * (size_t)n_m) * 3;  // meta: ms (padded), P, keep_off
     for (auto& it : j.items) b += up256e(rs * (size_t)K * (size_t)it.q.P);
+    if (std::is_same<real, float>::value)
+        for (auto& it : j.items) b += up256e(4 * (size_t)(it.q.C + ARRAY_PAD));  // conditioning ratios
     b += up256e(4 * (size_t)n_m * K) + up256e(8 * (size_t)n_m * K) + up256e(8 * (size_t)n_m * CRIT_BLOCKS) +
          up256e(8 * (size_t)n_m) + up256e(8 * (size_t)K);
     j.result_bytes = 8 + 8 * (size_t)n_m + 24 * (size_t)K;
@@ -423,9 +445,14 @@ pastila_status admit_job(pastila_engine* e, EJob& j) {
         p += up256e(bytes);
         return (void*)r;
     };
+    const bool refine = std::is_same<real, float>::value && e->refine;
     j.T_dev = (double*)take(8 * (size_t)j.n);
     j.Th = take(rs * (size_t)(j.n + ARRAY_PAD));
     j.Tl = take(rs * (size_t)(j.n + ARRAY_PAD));
+    if (refine) {
+        j.Th64 = take(8 * (size_t)(j.n + ARRAY_PAD));
+        j.Tl64 = take(8 * (size_t)(j.n + ARRAY_PAD));
+    }
     for (auto& st : j.stats) {
         st.mu = (double*)take(8 * (size_t)st.C);
         st.a = take(rs * (size_t)(st.C + ARRAY_PAD));
@@ -433,6 +460,13 @@ pastila_status admit_job(pastila_engine* e, EJob& j) {
         st.dg = take(rs * (size_t)(st.C + ARRAY_PAD));
         st.muh = take(rs * (size_t)(st.C + ARRAY_PAD));
         st.mul = take(rs * (size_t)(st.C + ARRAY_PAD));
+        if (refine) {
+            st.a64 = take(8 * (size_t)(st.C + ARRAY_PAD));
+            st.df64 = take(8 * (size_t)(st.C + ARRAY_PAD));
+            st.dg64 = take(8 * (size_t)(st.C + ARRAY_PAD));
+            st.muh64 = take(8 * (size_t)(st.C + ARRAY_PAD));
+            st.mul64 = take(8 * (size_t)(st.C + ARRAY_PAD));
+        }
     }
     j.inv = (double*)take(8 * (size_t)j.Cmax);
     j.flat = (int32_t*)take(4 * (size_t)j.Cmax);
@@ -447,6 +481,8 @@ pastila_status admit_job(pastila_engine* e, EJob& j) {
         keep_off[u] = (int64_t)((p - (char*)j.keep_base) / rs);
         j.items[u].keep = take(rs * (size_t)K * (size_t)j.items[u].q.P);
     }
+    if (std::is_same<real, float>::value)
+        for (int u = 0; u < n_m; ++u) j.items[u].kappa = (float*)take(4 * (size_t)(j.items[u].q.C + ARRAY_PAD));
     int32_t* chosen = (int32_t*)take(4 * (size_t)n_m * K);
     double* aafter = (double*)take(8 * (size_t)n_m * K);
     double* cpart = (double*)take(8 * (size_t)n_m * CRIT_BLOCKS);
@@ -505,6 +541,7 @@ BatchItem<real> item_desc(const pastila_engine* e, const EJob& j, const EItem& i
     A.ntiles = it.ntiles;
     A.D = (real*)it.D;
     A.dmax_key = it.dmax;
+    A.kappa = it.kappa;
     A.err = e->err;
     A.spin_limit = e->spin_limit;
     A.test_timeout = e->test_timeout;
@@ -516,6 +553,42 @@ BatchItem<real> item_desc(const pastila_engine* e, const EJob& j, const EItem& i
     bi.crit_part = it.crit_part;
     bi.crit = it.crit;
     bi.K = j.K;
+    if (it.refine) {  // FP32 engine: the greedy re-evaluation's FP64 rows (cf. refine_attach)
+        ProfileArgs<double> A64{};
+        A64.Th = (const double*)j.Th64;
+        A64.Tl = (const double*)j.Tl64;
+        A64.muh = (const double*)st.muh64;
+        A64.mul = (const double*)st.mul64;
+        A64.a = (const double*)st.a64;
+        A64.df = (const double*)st.df64;
+        A64.dg = (const double*)st.dg64;
+        A64.n = j.n;
+        A64.C = it.q.C;
+        A64.P = it.q.P;
+        A64.m = it.q.m;
+        A64.ell = it.q.ell;
+        A64.k = it.q.k;
+        A64.R = it.q.R;
+        A64.S = it.q.S;
+        A64.W = it.g64.W;
+        A64.ntiles = (int)((it.q.P + it.g64.W - 1) / it.g64.W);
+        A64.err = e->err;
+        A64.spin_limit = e->spin_limit;
+        A64.test_timeout = e->test_timeout;
+        char* r = (char*)it.refine;
+        bi.rows64 = (double*)r;
+        r += up256e(8 * (size_t)(j.K + REF_NCAND) * (size_t)it.q.P);
+        bi.bound = (float*)r;
+        r += up256e(4 * (size_t)it.q.S);
+        bi.cand_area = (double*)r;
+        r += up256e(8 * REF_NCAND);
+        A64.dmax_key = (unsigned long long*)r;
+        A64.D = bi.rows64;
+        bi.A64 = A64;
+        bi.G64 = it.g64;
+        bi.rst = it.rst;
+        bi.bc = (float)(2.2 * it.q.ell * REF_DRHO);
+    }
     return bi;
 }
 
@@ -623,6 +696,12 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
                 it.M = p;
                 p += up256e(sizeof(real) * (size_t)it.q.P);
                 it.area = (double*)p;
+                p += up256e(8 * (size_t)it.q.S);
+                if (std::is_same<real, float>::value && e->refine) {
+                    it.refine = p;
+                    p += refine_bytes(it.q, j.K);
+                    it.rst = (int32_t*)p;
+                }
                 it.state = 1;
                 it.next_seg = 0;
             }
@@ -842,6 +921,19 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
                 j.T_dev, j.n, st.C, st.ell, st.mu, j.inv, (real*)st.a, (real*)st.df, (real*)st.dg,
                 (real*)st.muh, (real*)st.mul, (real*)j.Th, (real*)j.Tl);
             launches += 2;
+            if (st.a64) {  // FP64 terms for the greedy re-evaluation (same mu and inverse norms)
+                stats_terms_kernel<double><<<(unsigned)((j.n + 255) / 256), 256, 0, s>>>(
+                    j.T_dev, j.n, st.C, st.ell, st.mu, j.inv, (double*)st.a64, (double*)st.df64, (double*)st.dg64,
+                    (double*)st.muh64, (double*)st.mul64, (double*)j.Th64, (double*)j.Tl64);
+                launches += 1;
+            }
+        }
+        for (auto& it : j.items) {  // FP32 tiles' conditioning ratios for each length's R
+            if (!it.kappa) continue;
+            const EStats& st = j.stats[it.stats];
+            kappa_kernel<float><<<(unsigned)((it.q.C + 255) / 256), 256, 0, s>>>((const float*)st.a, it.q.C,
+                                                                                it.q.R, it.kappa);
+            launches += 1;
         }
         engine_init_keys_kernel<<<1, 64, 0, s>>>(j.items[0].dmax, (int)j.items.size());
         launches += 1;
@@ -854,15 +946,16 @@ pastila_status form_wave_t(pastila_engine* e, bool* did) {
     if (!greedy.empty()) {
         const int ng = (int)greedy.size();
         const unsigned pb = (unsigned)((gmaxP + 255) / 256);
-        for (int t = 0; t < Kmax; ++t) {
-            batched_area_kernel<real><<<dim3((unsigned)gmaxS, ng), AREA_THREADS, 0, s>>>(d_greedy, t);
-            batched_argmin_kernel<real><<<ng, 1024, 0, s>>>(d_greedy, t);
-            if (t + 1 < Kmax) batched_update_kernel<real><<<dim3(pb, ng), 256, 0, s>>>(d_greedy, t);
-        }
+        // the same greedy launches as select_length (with its FP64 re-evaluation of
+        // near-tied steps on FP32 engines)
+        const std::vector<BatchItem<real>> hg(h_greedy, h_greedy + ng);
+        pastila_status gst;
+        launches += (uint64_t)enqueue_greedy<real>(s, d_greedy, hg, Kmax, gmaxS, gmaxP, e->smem_optin, &gst);
+        if (gst != PASTILA_OK) return gst;
         batched_criterion_kernel<real><<<dim3(CRIT_BLOCKS, ng), AREA_THREADS, 0, s>>>(d_greedy);
         batched_finish_kernel<real><<<1, 256, 0, s>>>(d_greedy, ng, nullptr);
         gather_chosen_kernel<real><<<dim3(pb, ng), 256, 0, s>>>(d_greedy, d_keep);
-        launches += 3 * (uint64_t)Kmax - 1 + 3;
+        launches += 3;
         for (auto& gi : greedy) {
             EItem& it = gi.first->items[gi.second];
             eng_free(e, it.dblock, it.dbytes);
@@ -1069,6 +1162,7 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
     e->fail_at = c.fail_alloc_at;
     e->age_weight = c.age_weight_s;
     e->policy = c.policy;
+    e->refine = c.prec == PASTILA_FP32 && c.fp32_greedy == 0;
     int smem = 0;
     CK(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
     e->smem_optin = smem - 1024;

@@ -12,6 +12,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -140,6 +141,13 @@ struct pastila_series {
     int64_t tile_launches = 0;
     double tile_cells = 0.0;
     std::map<int, Stats> stats;
+    // FP64 statistics of an FP32 handle (the FP64 re-evaluation of near-tied
+    // greedy steps), with T as FP64 pairs (value, 0)
+    std::map<int, Stats> stats64;
+    void* Th64 = nullptr;
+    void* Tl64 = nullptr;
+    int phase2_launches = 0;  // kernels of the last enqueued greedy phase of a sweep
+    bool fp64_ties = true;    // FP32 handles: near-tied greedy steps decided on FP64 areas
     std::map<std::string, Buf> bufs;
     uint64_t alloc_gen = 0;  // bumped whenever a device buffer is (re)allocated
     // captured select_length sequence, replayed while the configuration and the
@@ -213,6 +221,7 @@ pastila_status stage_check(pastila_series* h) {
 
 void invalidate_stats(pastila_series* h) {
     for (auto& kv : h->stats) kv.second.stale = true;
+    for (auto& kv : h->stats64) kv.second.stale = true;
 }
 
 pastila_status ensure_stats(pastila_series* h, int ell, Stats** out) {
@@ -273,10 +282,79 @@ pastila_status ensure_stats(pastila_series* h, int ell, Stats** out) {
     return PASTILA_OK;
 }
 
+// FP64 window statistics of an FP32 handle, for the FP64 rows of the greedy
+// re-evaluation (the same kernels as an FP64 handle's statistics).
+pastila_status ensure_stats64(pastila_series* h, int ell, Stats** out) {
+    auto it = h->stats64.find(ell);
+    if (it != h->stats64.end() && !it->second.stale) {
+        *out = &it->second;
+        return PASTILA_OK;
+    }
+    Stats st;
+    st.C = h->n - ell + 1;
+    void *mu, *inv, *flat, *a, *df, *dg, *muh, *mul;
+    if (it != h->stats64.end()) {
+        mu = it->second.mu;
+        a = it->second.a;
+        df = it->second.df;
+        dg = it->second.dg;
+        muh = it->second.muh;
+        mul = it->second.mul;
+    } else {
+        TRY(dev_alloc(h, &mu, 8 * st.C));
+        TRY(dev_alloc(h, &a, 8 * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &df, 8 * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &dg, 8 * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &muh, 8 * (st.C + ARRAY_PAD)));
+        TRY(dev_alloc(h, &mul, 8 * (st.C + ARRAY_PAD)));
+    }
+    if (!h->Th64) {
+        TRY(dev_alloc(h, &h->Th64, 8 * (h->n + ARRAY_PAD)));
+        TRY(dev_alloc(h, &h->Tl64, 8 * (h->n + ARRAY_PAD)));
+    }
+    TRY(scratch(h, "stats_inv", 8 * st.C, &inv));
+    TRY(scratch(h, "stats_flat", 4 * st.C, &flat));
+    const int64_t nthr = (st.C + STATS_RUN - 1) / STATS_RUN;
+    stats_mu_a_kernel<<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
+        h->T, st.C, ell, (double*)mu, (double*)inv, (int32_t*)flat);
+    stats_terms_kernel<double><<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(
+        h->T, h->n, st.C, ell, (double*)mu, (double*)inv, (double*)a, (double*)df, (double*)dg, (double*)muh,
+        (double*)mul, (double*)h->Th64, (double*)h->Tl64);
+    CK(cudaGetLastError());
+    h->launches += 2;
+    st.mu = (double*)mu;
+    st.a = a;
+    st.df = df;
+    st.dg = dg;
+    st.muh = muh;
+    st.mul = mul;
+    h->stats64[ell] = st;
+    *out = &h->stats64[ell];
+    return PASTILA_OK;
+}
+
 struct MParams {
     int m, ell, k, R, S;
     int64_t P, C;
 };
+
+// Conditioning ratios of the windows for the FP32 tiles of q (kappa_kernel),
+// recomputed from the statistics st on every call (a small launch); nullptr
+// for FP64 handles, whose tiles need no check.
+pastila_status ensure_kappa(pastila_series* h, const MParams& q, const Stats* st, const float** out) {
+    *out = nullptr;
+    if (h->prec == PASTILA_FP64) return PASTILA_OK;
+    char name[48];
+    snprintf(name, sizeof(name), "kappa_%d_%d", q.ell, q.R);
+    void* k;
+    TRY(scratch(h, name, 4 * (size_t)(q.C + ARRAY_PAD), &k));
+    kappa_kernel<float><<<(unsigned)((q.C + 255) / 256), 256, 0, h->stream>>>((const float*)st->a, q.C, q.R,
+                                                                            (float*)k);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    *out = (const float*)k;
+    return PASTILA_OK;
+}
 
 pastila_status resolve_n(int64_t n, int32_t m, pastila_mparams mp, MParams* o) {
     if (m < 4) return fail(PASTILA_EINVAL, "m = %d: must be at least 4", m);
@@ -459,7 +537,8 @@ pastila_status launch_profiles_t(pastila_series* h, const MParams& q, Stats* st,
                                  unsigned long long* dmax) {
     TileGeom g;
     TRY(choose_tile<real, V>(h, q, &g));
-    const ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, D, dmax);
+    ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, D, dmax);
+    TRY(ensure_kappa(h, q, st, &A.kappa));
     CK(tile_attrs(profile_tiles_kernel<real, V>, h->smem_optin));
     init_dmax_kernel<<<1, 1, 0, h->stream>>>(dmax);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -486,6 +565,120 @@ pastila_status launch_profiles(pastila_series* h, const MParams& q, void* D, uns
     TRY(ensure_stats(h, q.ell, &st));
     if (h->prec == PASTILA_FP64) return launch_profiles_t<double, V_F64>(h, q, st, (double*)D, dmax);
     return launch_profiles_t<float, V_F32>(h, q, st, (float*)D, dmax);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-evaluation of near-tied greedy steps on FP32 handles (batch.cuh,
+// batched_select_kernel): per length, (K + REF_NCAND) FP64 rows, S area bounds,
+// the contenders' FP64 areas and a D-max word for the FP64 tiles; the state
+// words live apart (one array for all lengths, cleared once per search).
+constexpr double REF_DRHO = 2e-6;  // the FP32 profiles' accuracy in rho at every cell
+
+inline size_t refine_bytes(const MParams& q, int K) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return up(8 * (size_t)(K + REF_NCAND) * (size_t)q.P) + up(4 * (size_t)q.S) + up(8 * REF_NCAND) + up(8);
+}
+
+// Fills it's refinement fields from region (refine_bytes) and rst (REF_STATE_INTS
+// ints); FP64 statistics and the FP64 tile layout of q.
+pastila_status refine_attach(pastila_series* h, const MParams& q, int K, BatchItem<float>* it, char* region,
+                             int32_t* rst) {
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    if (!h->fp64_ties) return PASTILA_OK;  // greedy steps decided on FP32 areas alone
+    Stats* st;
+    TRY(ensure_stats64(h, q.ell, &st));
+    TileGeom g;
+    TRY(choose_tile<double, V_F64>(h, q, &g));
+    ProfileArgs<double> A{};
+    A.Th = (const double*)h->Th64;
+    A.Tl = (const double*)h->Tl64;
+    A.muh = (const double*)st->muh;
+    A.mul = (const double*)st->mul;
+    A.a = (const double*)st->a;
+    A.df = (const double*)st->df;
+    A.dg = (const double*)st->dg;
+    A.n = h->n;
+    A.C = q.C;
+    A.P = q.P;
+    A.m = q.m;
+    A.ell = q.ell;
+    A.k = q.k;
+    A.R = q.R;
+    A.S = q.S;
+    A.W = g.W;
+    A.ntiles = (int)((q.P + g.W - 1) / g.W);
+    A.err = h->err;
+    A.spin_limit = h->spin_limit;
+    A.test_timeout = h->test_timeout;
+    char* r = region;
+    it->rows64 = (double*)r;
+    r += up(8 * (size_t)(K + REF_NCAND) * (size_t)q.P);
+    it->bound = (float*)r;
+    r += up(4 * (size_t)q.S);
+    it->cand_area = (double*)r;
+    r += up(8 * REF_NCAND);
+    A.dmax_key = (unsigned long long*)r;  // the FP64 rows' D max (unused)
+    A.D = it->rows64;
+    it->A64 = A;
+    it->G64 = g;
+    it->rst = rst;
+    it->bc = (float)(2.2 * q.ell * REF_DRHO);
+    return PASTILA_OK;
+}
+
+// The K greedy steps of n items (device array d_items, host copies hi) on one
+// stream: FP32 areas with their bounds, the choice (FP32, or FP64 for a
+// near-tied step), the FP64 rows that needs (one launch per refining item), the
+// contenders' FP64 areas, the decision and the curve update.  Returns the
+// launch count.
+template <typename real>
+int enqueue_greedy(cudaStream_t s, const BatchItem<real>* d_items, const std::vector<BatchItem<real>>& hi, int K,
+                   int64_t maxS, int64_t maxP, int smem_optin, pastila_status* err) {
+    const int n = (int)hi.size();
+    const unsigned pb = (unsigned)((maxP + 255) / 256);
+    bool any = false;
+    for (const auto& it : hi) any |= it.rows64 != nullptr;
+    int launches = 0;
+    *err = PASTILA_OK;
+    if (any) {
+        const cudaError_t e = tile_attrs(refine_rows_kernel<V_F64>, smem_optin);
+        if (e != cudaSuccess) {
+            *err = fail(PASTILA_ECUDA, "greedy refinement set-up: %s", cudaGetErrorString(e));
+            return 0;
+        }
+    }
+    for (int t = 0; t < K; ++t) {
+        batched_area_kernel<real><<<dim3((unsigned)maxS, n), AREA_THREADS, 0, s>>>(d_items, t);
+        if (!any) {
+            batched_argmin_kernel<real><<<n, 1024, 0, s>>>(d_items, t);
+            if (t + 1 < K) batched_update_kernel<real><<<dim3(pb, n), 256, 0, s>>>(d_items, t);
+            launches += t + 1 < K ? 3 : 2;
+            continue;
+        }
+        batched_select_kernel<real><<<n, 1024, 0, s>>>(d_items, t);
+        launches += 2;
+        if constexpr (std::is_same<real, float>::value) {
+            for (int i = 0; i < n; ++i) {
+                const BatchItem<real>& it = hi[i];
+                if (!it.rows64 || t >= it.K) continue;
+                const TileGeom& g = it.G64;
+                const cudaError_t e = launch_tiles(refine_rows_kernel<V_F64>,
+                                                   dim3((unsigned)(it.A64.ntiles * g.CS), REF_TODO_GRID), g.NT,
+                                                   g.bytes, s, g.CS, d_items + i, t);
+                if (e != cudaSuccess) {
+                    *err = fail(PASTILA_ECUDA, "FP64 rows launch: %s", cudaGetErrorString(e));
+                    return launches;
+                }
+                ++launches;
+            }
+        }
+        batched_refine_area_kernel<real><<<dim3(REF_NCAND, n), AREA_THREADS, 0, s>>>(d_items, t);
+        batched_choose_update_kernel<real><<<dim3(pb, n), 256, 0, s>>>(d_items, t);
+        launches += 2;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) *err = fail(PASTILA_ECUDA, "greedy launches: %s", cudaGetErrorString(e));
+    return launches;
 }
 
 // Autotuner: times the cost model's layout and its closest rivals (the model's
@@ -547,7 +740,8 @@ pastila_status tune_t(pastila_series* h, const MParams& q, int max_cand, pastila
     size_t bi = 0;
     for (size_t i = 0; i < pick.size(); ++i) {
         const TileGeom& g = pick[i].g;
-        const ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, (real*)D, (unsigned long long*)dk);
+        ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, (real*)D, (unsigned long long*)dk);
+        TRY(ensure_kappa(h, q, st, &A.kappa));
         const dim3 grid((unsigned)(A.ntiles * g.CS), (unsigned)S_sub);
         CK(launch_tiles(profile_tiles_kernel<real, V>, grid, g.NT, g.bytes, h->stream, g.CS, A, g));  // warm-up
         float best = 1e30f;
@@ -610,13 +804,40 @@ pastila_status snippets_on_device_t(pastila_series* h, const MParams& q, const r
     TRY(scratch(h, "sn_ofrac", 8 * 64, &ofrac));
     TRY(scratch(h, "sn_oarea", 8 * 64, &oarea));
     const unsigned pb = (unsigned)((q.P + 255) / 256);
-    for (int t = 0; t < K; ++t) {
-        area_kernel<real><<<q.S, AREA_THREADS, 0, h->stream>>>(D, q.S, q.P, t ? (const real*)M : nullptr,
-                                                               (const int32_t*)chosen, t, (double*)area);
-        argmin_area_kernel<<<1, 1024, 0, h->stream>>>((const double*)area, q.S, (int32_t*)chosen,
-                                                      (double*)aafter, t);
-        if (t + 1 < K)
-            update_curve_kernel<real><<<pb, 256, 0, h->stream>>>(D, q.P, (const int32_t*)chosen, t, (real*)M);
+    if constexpr (std::is_same<real, float>::value) {
+        // the greedy steps as a one-item batch, with the FP64 re-evaluation of
+        // near-tied steps (the same kernels as a select_length sweep)
+        void *dit, *rreg, *rst;
+        TRY(scratch(h, "sn_item", sizeof(BatchItem<real>), &dit));
+        TRY(scratch(h, "sn_refine", refine_bytes(q, K), &rreg));
+        TRY(scratch(h, "sn_rst", 4 * REF_STATE_INTS, &rst));
+        std::vector<BatchItem<real>> hi(1, BatchItem<real>{});
+        BatchItem<real>& it = hi[0];
+        it.A.D = const_cast<real*>(D);
+        it.A.S = q.S;
+        it.A.P = q.P;
+        it.A.m = q.m;
+        it.M = (real*)M;
+        it.area = (double*)area;
+        it.chosen = (int32_t*)chosen;
+        it.area_after = (double*)aafter;
+        it.K = K;
+        TRY(refine_attach(h, q, K, &it, (char*)rreg, (int32_t*)rst));
+        CK(cudaMemcpyAsync(dit, &it, sizeof(BatchItem<real>), cudaMemcpyHostToDevice, h->stream));
+        pastila_status gst;
+        h->launches += enqueue_greedy<real>(h->stream, (const BatchItem<real>*)dit, hi, K, q.S, q.P, h->smem_optin,
+                                            &gst);
+        if (gst != PASTILA_OK) return gst;
+        h->launches -= 3 * K - 1;  // counted below with the plain steps
+    } else {
+        for (int t = 0; t < K; ++t) {
+            area_kernel<real><<<q.S, AREA_THREADS, 0, h->stream>>>(D, q.S, q.P, t ? (const real*)M : nullptr,
+                                                                   (const int32_t*)chosen, t, (double*)area);
+            argmin_area_kernel<<<1, 1024, 0, h->stream>>>((const double*)area, q.S, (int32_t*)chosen,
+                                                          (double*)aafter, t);
+            if (t + 1 < K)
+                update_curve_kernel<real><<<pb, 256, 0, h->stream>>>(D, q.P, (const int32_t*)chosen, t, (real*)M);
+        }
     }
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(counts, 0, 8 * 64, h->stream));
@@ -725,6 +946,7 @@ pastila_status snippets_streamed_t(pastila_series* h, const MParams& q, int K, i
     init_dmax_kernel<<<1, 1, 0, h->stream>>>((unsigned long long*)dk);
     h->launches += 1;
     ProfileArgs<real> A = profile_args<real, V>(h, q, st, g, nullptr, (unsigned long long*)dk);
+    TRY(ensure_kappa(h, q, st, &A.kappa));
     int64_t passes = 0, nrows = 0;
     std::vector<double> hapx(S), hlb(S), ex(BMAX);
     // a streaming pass over every segment with the curve Mc (nullptr: +inf):
@@ -946,6 +1168,7 @@ struct SweepBufs {
     void* rec_frac = nullptr;
     void* rec_area = nullptr;
     void* crit = nullptr;
+    void* rst = nullptr;  // refinement state words, REF_STATE_INTS per item
 };
 
 inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -975,6 +1198,15 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
     TRY(scratch(h, "sweep_rec_rank", 4 * 64, &sb->rec_rank));
     TRY(scratch(h, "sweep_rec_frac", 8 * 64, &sb->rec_frac));
     TRY(scratch(h, "sweep_rec_area", 8 * 64, &sb->rec_area));
+    // FP64 re-evaluation of near-tied greedy steps (FP32 handles)
+    constexpr bool refine = std::is_same<real, float>::value;
+    void* rreg = nullptr;
+    if (refine) {
+        size_t rbytes = 0;
+        for (int i = 0; i < n; ++i) rbytes += refine_bytes(qs[i], K);
+        TRY(scratch(h, "sweep_refine", rbytes, &rreg));
+        TRY(scratch(h, "sweep_rst", 4 * (size_t)n * REF_STATE_INTS, &sb->rst));
+    }
     std::vector<Stats*> st(n);
     for (int i = 0; i < n; ++i) TRY(ensure_stats(h, qs[i].ell, &st[i]));
     std::vector<BatchItem<real>>& items = *items_out;
@@ -986,6 +1218,7 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
         const MParams& q = qs[i];
         BatchItem<real>& it = items[i];
         it.A = profile_args<real, V>(h, q, st[i], geo[i], (real*)dp, nullptr);  // D max key below
+        TRY(ensure_kappa(h, q, st[i], &it.A.kappa));
         ProfileArgs<real>& A = it.A;
         dp += up256(sizeof(real) * (size_t)q.S * (size_t)q.P);
         it.G = geo[i];
@@ -1005,6 +1238,10 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
         A.dmax_key = (unsigned long long*)sp;
         sp += up256(8);
         it.K = K;
+        if constexpr (refine) {
+            TRY(refine_attach(h, q, K, &it, (char*)rreg, (int32_t*)sb->rst + (size_t)i * REF_STATE_INTS));
+            rreg = (char*)rreg + refine_bytes(q, K);
+        }
         maxS = q.S > maxS ? q.S : maxS;
         maxP = q.P > maxP ? q.P : maxP;
     }
@@ -1043,7 +1280,7 @@ pastila_status sweep_prepare_t(pastila_series* h, const std::vector<MParams>& qs
 // greedy steps, the criterion, m_best and its eq. 8 records
 template <typename real, int V>
 pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs, int K, const SweepBufs& sb,
-                               int64_t maxS, int64_t maxP, int phase) {
+                               const std::vector<BatchItem<real>>& hitems, int64_t maxS, int64_t maxP, int phase) {
     const int n = (int)qs.size();
     const BatchItem<real>* items = (const BatchItem<real>*)sb.items;
     if (phase == 1) {
@@ -1060,11 +1297,9 @@ pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs
     }
     if (phase == 2) {
         const unsigned pb = (unsigned)((maxP + 255) / 256);
-        for (int t = 0; t < K; ++t) {
-            batched_area_kernel<real><<<dim3((unsigned)maxS, n), AREA_THREADS, 0, h->stream>>>(items, t);
-            batched_argmin_kernel<real><<<n, 1024, 0, h->stream>>>(items, t);
-            if (t + 1 < K) batched_update_kernel<real><<<dim3(pb, n), 256, 0, h->stream>>>(items, t);
-        }
+        pastila_status gst;
+        const int gl = enqueue_greedy<real>(h->stream, items, hitems, K, maxS, maxP, h->smem_optin, &gst);
+        if (gst != PASTILA_OK) return gst;
         batched_criterion_kernel<real><<<dim3(CRIT_BLOCKS, n), AREA_THREADS, 0, h->stream>>>(items);
         batched_finish_kernel<real><<<1, 256, 0, h->stream>>>(items, n, (int32_t*)sb.best);
         CK(cudaMemsetAsync(sb.counts, 0, 8 * 64, h->stream));
@@ -1075,7 +1310,8 @@ pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs
                                                              (int32_t*)sb.rec_index, (int32_t*)sb.rec_rank,
                                                              (double*)sb.rec_frac, (double*)sb.rec_area);
         CK(cudaGetLastError());
-        h->launches += 3 * K - 1 + 4;
+        h->launches += gl + 4;
+        h->phase2_launches = gl + 4;
         return PASTILA_OK;
     }
     std::vector<int> done_ell;
@@ -1084,9 +1320,21 @@ pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs
         for (int e : done_ell) seen |= e == qs[i].ell;
         if (seen) continue;
         done_ell.push_back(qs[i].ell);
-        h->stats[qs[i].ell].stale = true;
+        // recompute every statistic in place (find, not operator[]: an entry the
+        // map does not hold yet would be created with null buffers)
+        auto f = h->stats.find(qs[i].ell);
+        if (f != h->stats.end()) f->second.stale = true;
         Stats* st;
         TRY(ensure_stats(h, qs[i].ell, &st));
+        if (std::is_same<real, float>::value && h->fp64_ties) {  // the greedy re-evaluation's FP64 statistics
+            auto f64 = h->stats64.find(qs[i].ell);
+            if (f64 != h->stats64.end()) f64->second.stale = true;
+            TRY(ensure_stats64(h, qs[i].ell, &st));
+        }
+    }
+    for (int i = 0; i < n; ++i) {  // the FP32 tiles' conditioning ratios, from the new statistics
+        const float* kp;
+        TRY(ensure_kappa(h, qs[i], &h->stats[qs[i].ell], &kp));
     }
     batched_init_dmax_kernel<real><<<1, 64, 0, h->stream>>>(items, n);
     CK(cudaGetLastError());
@@ -1138,7 +1386,7 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
         for (int ph = 0; ph < 3; ++ph) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            pastila_status st = sweep_enqueue_t<real, V>(h, qs, K, sb, maxS, maxP, ph);
+            pastila_status st = sweep_enqueue_t<real, V>(h, qs, K, sb, items, maxS, maxP, ph);
             cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
             if (st != PASTILA_OK) return st;
             if (ec != cudaSuccess) return fail(PASTILA_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
@@ -1155,11 +1403,19 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
         if (gr.exec[ph]) {
             CK(cudaGraphLaunch(gr.exec[ph], h->stream));
         } else {
-            TRY(sweep_enqueue_t<real, V>(h, qs, K, sb, maxS, maxP, ph));
+            TRY(sweep_enqueue_t<real, V>(h, qs, K, sb, items, maxS, maxP, ph));
         }
         if (ph == 1 && h->timing) CK(cudaEventRecord(gr.ev1, h->stream));
     }
-    if (gr.exec[0]) h->launches = l_before + 2 * (uint64_t)n_m + 1 + sb.groups.size() + 3 * K - 1 + 4;
+    if (gr.exec[0]) {  // graph replays: the launches the three captured phases hold
+        uint64_t nst = 0;
+        std::vector<int> seen;
+        for (const MParams& q : qs)
+            if (std::find(seen.begin(), seen.end(), q.ell) == seen.end()) seen.push_back(q.ell);
+        nst = (std::is_same<real, float>::value && h->fp64_ties ? 4 : 2) * (uint64_t)seen.size();
+        if (std::is_same<real, float>::value) nst += (uint64_t)n_m;  // conditioning ratios
+        h->launches = l_before + nst + 1 + sb.groups.size() + (uint64_t)h->phase2_launches;
+    }
     gr.gen = h->alloc_gen;
     int32_t b = 0;
     std::vector<double> cv(n_m);
@@ -1411,10 +1667,20 @@ void pastila_destroy(pastila_series* h) {
         cudaFree(kv.second.muh);
         cudaFree(kv.second.mul);
     }
+    for (auto& kv : h->stats64) {
+        cudaFree(kv.second.mu);
+        cudaFree(kv.second.a);
+        cudaFree(kv.second.df);
+        cudaFree(kv.second.dg);
+        cudaFree(kv.second.muh);
+        cudaFree(kv.second.mul);
+    }
     for (auto& kv : h->bufs) cudaFree(kv.second.p);
     cudaFree(h->T);
     cudaFree(h->Th);
     cudaFree(h->Tl);
+    cudaFree(h->Th64);
+    cudaFree(h->Tl64);
     if (h->err) cudaFreeHost(h->err);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -1461,6 +1727,18 @@ pastila_status pastila_profiles_device(pastila_series* h, int32_t m, pastila_mpa
         CK(cudaGetLastError());
         h->launches += 1;
     }
+    return PASTILA_OK;
+}
+
+pastila_status pastila_set_fp64_ties(pastila_series* h, int on) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    h->fp64_ties = on != 0;
+    auto& gr = h->graph;  // a captured sweep holds the previous choice
+    for (auto& e : gr.exec)
+        if (e) cudaGraphExecDestroy(e);
+    gr.exec[0] = gr.exec[1] = gr.exec[2] = nullptr;
+    gr.ms.clear();
     return PASTILA_OK;
 }
 

@@ -87,6 +87,40 @@ __device__ __forceinline__ double row_min_partial(const real* __restrict__ row, 
     return (a0 + a1) + (a2 + a3);
 }
 
+// This thread's share of the error bound sum_p b(min(M_p, row[p])) (M = nullptr:
+// +inf) of an FP32 area.  Every FP32 profile value x meets |x^2 - d64^2| <= c
+// for the FP64 value d64 of the same cell (c = 2 ell |d rho| with the FP32
+// path's accuracy |d rho| <= 2e-6, times 1.1 for the second-order terms), and
+// min is 1-Lipschitz in each argument, so |min(M, x) - min(M64, d64)| <= b(x),
+// b(x) = x - sqrt(x^2 - c) = c / (x + sqrt(x^2 - c)) for x^2 > c (the larger of
+// the two sides), max(x, sqrt(x^2 + c) - x) otherwise.  In FP32: a bound, not
+// an area; its own rounding, below 1 % for the sizes here, is covered by the
+// caller's margin.
+template <typename real>
+__device__ __forceinline__ float row_bound_partial(const real* __restrict__ row, const real* __restrict__ M,
+                                                   int64_t P, float c) {
+    constexpr int64_t st = AREA_THREADS;
+    float a0 = 0.f, a1 = 0.f;
+    int64_t p = threadIdx.x;
+    auto term = [&](int64_t q) {
+        float x = (float)row[q];
+        if (M) {
+            const float mm = (float)M[q];
+            x = x < mm ? x : mm;
+        }
+        const float x2 = x * x;
+        if (x2 > c) return c / (x + sqrtf(x2 - c));
+        const float up = c / (sqrtf(x2 + c) + x);
+        return x > up ? x : up;
+    };
+    for (; p + st < P; p += 2 * st) {
+        a0 += term(p);
+        a1 += term(p + st);
+    }
+    for (; p < P; p += st) a0 += term(p);
+    return a0 + a1;
+}
+
 // area[s] = sum_p min(M_p, D_s(p)) for every segment s (M = +inf on the first
 // step, so the area is the row sum).  One CTA per segment; chosen segments are
 // skipped and get +inf.  Grid: (S).

@@ -96,4 +96,34 @@ __global__ void stats_terms_kernel(const double* __restrict__ T, int64_t n, int6
     }
 }
 
+// Conditioning of the FP32 covariance recurrence (FP32 tiles).  Along a
+// diagonal the recurrence accumulates rounding errors at the scale of the
+// windows it passed through, while rho divides by the norms of the current
+// ones: a cell (i, j) whose windows are much smaller than those of the last R
+// steps of its diagonal can lose the FP32 accuracy the tolerance rule asks
+// (|d rho| <= 2e-6).  kappa[j] = a[j] / min{a[u] > 0 : max(0, j-R+1) <= u <= j}
+// (the largest norm among the R windows up to j over the norm of window j;
+// 0 for a flat window, whose rho the flat rule sets) bounds that ratio for
+// the row and the column side alike; the tile recomputes a cell exactly when
+// kappa[i] * kappa[j] exceeds KAPPA_FLAG (the recurrence's error in rho grows
+// about in proportion to that product).  One thread per
+// window; R loads each (a few hundred), once per length.
+template <typename real>
+__global__ void kappa_kernel(const real* __restrict__ a, int64_t C, int R, float* __restrict__ kappa) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= C) return;
+    const real aj = a[j];
+    if (!(aj > (real)0)) {
+        kappa[j] = 0.0f;
+        return;
+    }
+    real mn = aj;
+    const int64_t u0 = j - R + 1 > 0 ? j - R + 1 : 0;
+    for (int64_t u = u0; u < j; ++u) {
+        const real au = a[u];
+        if (au > (real)0 && au < mn) mn = au;
+    }
+    kappa[j] = (float)(aj / mn);
+}
+
 }  // namespace pastila

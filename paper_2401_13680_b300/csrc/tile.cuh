@@ -43,6 +43,7 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 #include <cfloat>
+#include <type_traits>
 
 #include "keys.cuh"
 
@@ -103,6 +104,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// A cell of an FP32 tile whose row and column conditioning ratios (kappa,
+// stats.cuh) multiply past this is recomputed by an exact dot product.  With
+// the carry folded into hi every row, a float emulation of the recurrence on
+// planted regimes and random walks (m = 64, 77; one group or groups of 10
+// rows; seeds summed in blocks of 9 terms as below) keeps |d rho| below about
+// 1.4e-7 kappa_i kappa_j -- most of it the rounding of the centred values
+// themselves -- so 8 leaves about 1.1e-6, half of the 2e-6 the FP32 cells are
+// held to.
+constexpr float KAPPA_FLAG = 8.0f;
+
 template <typename real> struct RealLimits;
 template <> struct RealLimits<float> {
     __host__ __device__ static constexpr float lowest() { return -FLT_MAX; }
@@ -139,6 +150,10 @@ struct ProfileArgs {
     // sketch that bounds later greedy areas without recomputing the rows)
     real* pmx;
     real* pmn;
+    // FP32 tiles: C conditioning ratios of the windows (kappa_kernel); a cell
+    // whose row and column ratios multiply past KAPPA_FLAG is recomputed
+    // exactly.  nullptr: no check (FP64 tiles)
+    const float* kappa;
     // bounded waits: the staging wait gives up after spin_limit SM cycles and
     // then stores 1 to *err (host-visible); test_timeout is 0, and 1 only in
     // the test that makes the wait run out (a second wait, on the barrier's
@@ -628,7 +643,21 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     };
     constexpr bool early_cols = sizeof(real) == 4;
     if (early_cols) load_cols();
+    // the largest conditioning ratio among this thread's columns (FP32 tiles
+    // with the check)
+    const float* kap = A.kappa;
+    float kxm = 0.0f;
+    if constexpr (sizeof(real) == 4) {
+        if (kap) {
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (xb + v < Wb) kxm = fmaxf(kxm, kap[p0 + xb + v]);
+        }
+    }
+    __shared__ unsigned kap_rmax;  // the rows' largest ratio, as float bits (all >= 0)
+    if (tid == 0) kap_rmax = 0;
     const real c0h = A.muh[p0], c0l = A.mul[p0];  // mean of column 0, for the left seeds
+    const float far_lim = 4.0f * rsqrtf((float)ell);
     __syncthreads();  // the barrier is initialised before anyone waits on it
     // staged: the copies of this thread's wait completed (if not, they may still
     // be in flight; the tile drains them before it ends)
@@ -637,6 +666,14 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         bool ok = staged;
         if (ok && A.test_timeout) ok = mbar_wait_bounded(&stage_bar, 1, A.spin_limit);
         if (!ok) *(volatile int*)A.err = 1;
+    }
+    if constexpr (sizeof(real) == 4) {
+        if (kap) {
+            float km = 0.0f;
+            for (int r = rbase + tid; r < rend; r += BD) km = fmaxf(km, kap[i0 + r]);
+            const unsigned b = __reduce_max_sync(FULL, __float_as_uint(km));
+            if (lane == 0 && b) atomicMax(&kap_rmax, b);
+        }
     }
     // the groups' centred heads q = T[ig + u] - mu_ig, ig = i0 + rbase + gg Rg
     for (int e = tid; e < NG * ell; e += BD) {
@@ -713,14 +750,22 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             }
             int u0 = 0;
             for (; u0 + J <= ell; u0 += J) {
+                // J terms summed apart, then added: the rounding of a seed grows with
+                // J + ell / J terms rather than ell (an FP32 seed's error is carried,
+                // scaled by the conditioning ratios, down its whole diagonal)
+                real part[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) part[j] = 0;
 #pragma unroll
                 for (int u = 0; u < J; ++u) {
                     const real qt = qg[u0 + u];
 #pragma unroll
-                    for (int j = 0; j < J; ++j) acc[j] += qt * win[(j + u) % J];
+                    for (int j = 0; j < J; ++j) part[j] += qt * win[(j + u) % J];
                     const int e = x0 + u0 + u + J;
                     win[u] = (Tc[e] - cbh) + (Tcl[e] - cbl);
                 }
+#pragma unroll
+                for (int j = 0; j < J; ++j) acc[j] += part[j];
             }
             for (; u0 < ell; ++u0) {
                 const real qt = qg[u0];
@@ -732,15 +777,36 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             }
             const real sq = qg[ell];
             real* topg = top + (size_t)gg * NTc * V;
+            unsigned far = 0;  // FP32: columns whose mean lies far from the block's centre
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const int x = x0 + j;
                 if (x < Wb) {
                     const real dm = ((early ? mxh[j] : A.muh[p0 + x]) - cbh) + ((early ? mxl[j] : A.mul[p0 + x]) - cbl);
                     topg[x] = acc[j] - dm * sq;
+                    if constexpr (sizeof(real) == 4)
+                        if (fabsf(dm) * A.a[p0 + x] > far_lim) far |= 1u << j;
                 } else if (x < NTc * V) {
                     topg[x] = 0;
                 }
+            }
+            // the products above carry |mu_x - c| besides the window's own deviations;
+            // where that offset passes 4 / sqrt(ell) norms of the window (short windows,
+            // level steps) their rounding would pass the recurrence's, so the seed is
+            // taken again centred on the column's own mean
+            while (far) {
+                const int j = __ffs(far) - 1;
+                far &= far - 1;
+                const int x = x0 + j;
+                const real mh = A.muh[p0 + x], ml = A.mul[p0 + x];
+                real c0 = 0, c1 = 0;
+                int u = 0;
+                for (; u + 1 < ell; u += 2) {
+                    c0 += qg[u] * ((Tc[x + u] - mh) + (Tcl[x + u] - ml));
+                    c1 += qg[u + 1] * ((Tc[x + u + 1] - mh) + (Tcl[x + u + 1] - ml));
+                }
+                if (u < ell) c0 += qg[u] * ((Tc[x + u] - mh) + (Tcl[x + u] - ml));
+                topg[x] = c0 + c1;
             }
         }
     }
@@ -748,6 +814,9 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
 
     // ---------------------------------------------------------------- rows
     if (!early_cols) load_cols();
+    // whether any cell of this thread can pass the conditioning flag (in most
+    // tiles of most series none can, and the rows skip the check)
+    const bool kap_check = kxm * __uint_as_float(kap_rmax) > KAPPA_FLAG;
     const real NEG = RealLimits<real>::lowest();
     real hi[V], lo[V], cmx[V];
     const bool partial_cols = xb + V > Wb;  // only the last column thread of a tile
@@ -777,153 +846,209 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         cooperative_groups::this_cluster().sync();
     }
 
-    for (int c0 = 0; c0 < Rg; c0 += V) {
-#pragma unroll
-        for (int jj = 0; jj < V; ++jj) {
-            const int sidx = c0 + jj;          // row step within the group
-            const int r = r0 + sidx;
-            const bool active = sidx < nrows;  // uniform within the group
-            const int par = sidx & 1;
-            real* PREp = PRE + par * V * LP;
-            real* CMp = CM + par * (NTc + 1);
-            real* LVp = LV + par * 4 * NTc;
-            // logical column v of this thread lives in register (v - jj) mod V
-            real rho[V];
-            real pre = NEG;  // this thread's chunk maximum
-            if (active) {
-                if (sidx > 0) {
-                    const int Pout = (V - jj) % V;  // register of the previous row's last column
-                    real lhi = __shfl_up_sync(FULL, hi[Pout], 1);
-                    real llo = __shfl_up_sync(FULL, lo[Pout], 1);
-                    if (lane == 0 && wc > 0) {
-                        lhi = XCH[((par ^ 1) * 2 + 0) * NWc + wc - 1];
-                        llo = XCH[((par ^ 1) * 2 + 1) * NWc + wc - 1];
-                    }
-                    const real fr = rdf[r], gr = rdg[r];
-#pragma unroll
-                    for (int v = 1; v < V; ++v) {
-                        const int P = (v - jj + V) % V;
-                        lo[P] = fr * cdg[v] + (cdf[v] * gr + lo[P]);
-                    }
-                    if (t == 0) {
-                        hi[Pout] = lseed[r];
-                        lo[Pout] = 0;
-                    } else {
-                        hi[Pout] = lhi;
-                        lo[Pout] = fr * cdg[0] + (cdf[0] * gr + llo);
-                    }
-                }
-                if (lane == 31) {
-                    const int Plast = (V - 1 - jj + V) % V;
-                    XCH[(par * 2 + 0) * NWc + wc] = hi[Plast];
-                    XCH[(par * 2 + 1) * NWc + wc] = lo[Plast];
-                }
-                const real ar = ra[r];
-                if (ar != (real)0) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const int P = (v - jj + V) % V;
-                        rho[v] = ((hi[P] + lo[P]) * ar) * ca[v];
-                    }
-                } else {
-#pragma unroll
-                    for (int v = 0; v < V; ++v) rho[v] = ca[v] == (real)0 ? (real)1 : (real)0;
-                }
-                const unsigned xd = (unsigned)(xdiag0 + r);  // i == j: correlation 1 by definition
-                if (xd < (unsigned)V) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if (v == (int)xd) rho[v] = (real)1;
-                }
-                if (partial_cols) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        if (xb + v >= Wb) rho[v] = NEG;
-                }
-#pragma unroll
-                for (int v = 0; v < V; ++v) cmx[v] = rmax(cmx[v], rho[v]);
-                pre = rho[0];
-                PREp[t] = pre;
-#pragma unroll
-                for (int v = 1; v < V; ++v) {
-                    pre = rmax(pre, rho[v]);
-                    PREp[v * LP + t] = pre;
-                }
-                CMp[t] = pre;
-                if (t == 0) CMp[NTc] = NEG;
-                if (!small_R && q0 >= 2) {  // sparse table of the chunk maxima within each warp
-                    real d = pre;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {  // entries reaching past the warp's end are never read
-                        d = rmax(d, __shfl_down_sync(FULL, d, 1 << k));
-                        LVp[k * NTc + t] = d;
-                    }
-                }
-            }
-            __syncthreads();
-            // maximum of the whole chunks t+1 .. t+q0-1 strictly inside the windows of
-            // this thread's positions, from the sparse tables: two overlapping spans of
-            // 2^k chunks for the part in each warp the range touches, two spans of 16
-            // for every whole warp in between
-            real mid = NEG;
-            if (active && owns_positions && !small_R && q0 >= 2) {
-                auto span = [&](int x, int y) {  // x <= y in one warp
-                    const int k = 31 - __clz(y - x + 1);
-                    const real* Lk = k == 0 ? CMp : LVp + (k > 4 ? 3 : k - 1) * NTc;
-                    const int w = k > 4 ? 16 : 1 << k;
-                    return rmax(Lk[x], Lk[y - w + 1]);
-                };
-                const int a = t + 1, z = t + q0 - 1;
-                const int wa = a >> 5, wz = z >> 5;
-                if (wa == wz) {
-                    mid = span(a, z);
-                } else {
-                    mid = rmax(span(a, wa * 32 + 31), span(wz * 32, z));
-                    for (int w = wa + 1; w < wz; ++w) mid = rmax(mid, rmax(LVp[3 * NTc + w * 32], LVp[3 * NTc + w * 32 + 16]));
-                }
-            }
-            if (active && owns_positions) {
-                real suf[V];
-                suf[V - 1] = rho[V - 1];
-#pragma unroll
-                for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
-                key_t* ABr = ABo + (size_t)r * RS + (t - tofs);
-                if (!small_R) {
-                    // whole chunks strictly inside the window: t+1 .. t+q0-1 (mid) for small
-                    // i, one more (t+q0) once the window end moves into chunk t+q0+1
-                    const real mid1 = rmax(mid, CMp[t + q0]);
-#pragma unroll
-                    for (int i = 0; i < V; ++i) {
-                        const int e = i + R - 1;        // window end, relative to xb
-                        const int oi = e / V, si = e - oi * V;
-                        const real ab = rmax(rmax(suf[i], oi > q0 ? mid1 : mid), PREp[si * LP + t + oi]);
-                        if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < V; ++i) {
-                        real ab;
-                        if (i + R - 1 < V) {  // window inside this chunk
-                            ab = NEG;
-#pragma unroll
-                            for (int j = 0; j < V; ++j)
-                                if (j >= i && j < i + R) ab = rmax(ab, rho[j]);
-                        } else {
-                            const int e = i + R - 1;
-                            const int oi = e / V, si = e - oi * V;
-                            ab = rmax(suf[i], PREp[si * LP + t + oi]);
+    auto row_loop = [&](auto check_tag) {
+    constexpr bool CHECK = decltype(check_tag)::value;
+        for (int c0 = 0; c0 < Rg; c0 += V) {
+    #pragma unroll
+            for (int jj = 0; jj < V; ++jj) {
+                const int sidx = c0 + jj;          // row step within the group
+                const int r = r0 + sidx;
+                const bool active = sidx < nrows;  // uniform within the group
+                const int par = sidx & 1;
+                real* PREp = PRE + par * V * LP;
+                real* CMp = CM + par * (NTc + 1);
+                real* LVp = LV + par * 4 * NTc;
+                // logical column v of this thread lives in register (v - jj) mod V
+                real rho[V];
+                real pre = NEG;  // this thread's chunk maximum
+                if (active) {
+                    if (sidx > 0) {
+                        const int Pout = (V - jj) % V;  // register of the previous row's last column
+                        real lhi = __shfl_up_sync(FULL, hi[Pout], 1);
+                        real llo = __shfl_up_sync(FULL, lo[Pout], 1);
+                        if (lane == 0 && wc > 0) {
+                            lhi = XCH[((par ^ 1) * 2 + 0) * NWc + wc - 1];
+                            llo = XCH[((par ^ 1) * 2 + 1) * NWc + wc - 1];
                         }
-                        if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
+                        const real fr = rdf[r], gr = rdg[r];
+    #pragma unroll
+                        for (int v = 1; v < V; ++v) {
+                            const int P = (v - jj + V) % V;
+                            lo[P] = fr * cdg[v] + (cdf[v] * gr + lo[P]);
+                        }
+                        if (t == 0) {
+                            hi[Pout] = lseed[r];
+                            lo[Pout] = 0;
+                        } else {
+                            hi[Pout] = lhi;
+                            lo[Pout] = fr * cdg[0] + (cdf[0] * gr + llo);
+                        }
+                        if constexpr (sizeof(real) == 4) {
+                            // fold the carry into hi every row (Dekker's fast two-sum): lo
+                            // then holds one row's increments, not the diagonal's whole
+                            // change, and its rounding shrinks with it
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                const real s = hi[v] + lo[v];
+                                lo[v] = (hi[v] - s) + lo[v];
+                                hi[v] = s;
+                            }
+                        }
+                    }
+                    if constexpr (sizeof(real) == 4) {
+                        // ill-conditioned cells: the exact centred dot product instead of the
+                        // recurrence (which then goes on from it along the diagonal)
+                        if (CHECK && kap_check && sidx > 0) {
+                            const float kr = kap[i0 + r];
+                            if (kr * kxm > KAPPA_FLAG) {
+                                const real mh = rmu[r], ml = rmul[r];
+    #pragma unroll
+                                for (int v = 0; v < V; ++v) {
+                                    const int x = xb + v;
+                                    if (x < Wb && kr * kap[p0 + x] > KAPPA_FLAG) {
+                                        const real ch = A.muh[p0 + x], cl = A.mul[p0 + x];
+                                        real c0 = 0, c1 = 0;
+                                        int u = 0;
+                                        for (; u + 1 < ell; u += 2) {
+                                            c0 += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * ((Tc[x + u] - ch) + (Tcl[x + u] - cl));
+                                            c1 += ((Ts[r + u + 1] - mh) + (Tsl[r + u + 1] - ml)) *
+                                                  ((Tc[x + u + 1] - ch) + (Tcl[x + u + 1] - cl));
+                                        }
+                                        if (u < ell) c0 += ((Ts[r + u] - mh) + (Tsl[r + u] - ml)) * ((Tc[x + u] - ch) + (Tcl[x + u] - cl));
+                                        const int P = (v - jj + V) % V;
+                                        hi[P] = c0 + c1;
+                                        lo[P] = 0;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    if (lane == 31) {
+                        const int Plast = (V - 1 - jj + V) % V;
+                        XCH[(par * 2 + 0) * NWc + wc] = hi[Plast];
+                        XCH[(par * 2 + 1) * NWc + wc] = lo[Plast];
+                    }
+                    const real ar = ra[r];
+                    if (ar != (real)0) {
+    #pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const int P = (v - jj + V) % V;
+                            // FP32: hi is the rounded sum of the pair (lo is below half its ulp)
+                            rho[v] = ((sizeof(real) == 4 ? hi[P] : hi[P] + lo[P]) * ar) * ca[v];
+                        }
+                    } else {
+    #pragma unroll
+                        for (int v = 0; v < V; ++v) rho[v] = ca[v] == (real)0 ? (real)1 : (real)0;
+                    }
+                    const unsigned xd = (unsigned)(xdiag0 + r);  // i == j: correlation 1 by definition
+                    if (xd < (unsigned)V) {
+    #pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            if (v == (int)xd) rho[v] = (real)1;
+                    }
+                    if (partial_cols) {
+    #pragma unroll
+                        for (int v = 0; v < V; ++v)
+                            if (xb + v >= Wb) rho[v] = NEG;
+                    }
+    #pragma unroll
+                    for (int v = 0; v < V; ++v) cmx[v] = rmax(cmx[v], rho[v]);
+                    pre = rho[0];
+                    PREp[t] = pre;
+    #pragma unroll
+                    for (int v = 1; v < V; ++v) {
+                        pre = rmax(pre, rho[v]);
+                        PREp[v * LP + t] = pre;
+                    }
+                    CMp[t] = pre;
+                    if (t == 0) CMp[NTc] = NEG;
+                    if (!small_R && q0 >= 2) {  // sparse table of the chunk maxima within each warp
+                        real d = pre;
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k) {  // entries reaching past the warp's end are never read
+                            d = rmax(d, __shfl_down_sync(FULL, d, 1 << k));
+                            LVp[k * NTc + t] = d;
+                        }
+                    }
+                }
+                __syncthreads();
+                // maximum of the whole chunks t+1 .. t+q0-1 strictly inside the windows of
+                // this thread's positions, from the sparse tables: two overlapping spans of
+                // 2^k chunks for the part in each warp the range touches, two spans of 16
+                // for every whole warp in between
+                real mid = NEG;
+                if (active && owns_positions && !small_R && q0 >= 2) {
+                    auto span = [&](int x, int y) {  // x <= y in one warp
+                        const int k = 31 - __clz(y - x + 1);
+                        const real* Lk = k == 0 ? CMp : LVp + (k > 4 ? 3 : k - 1) * NTc;
+                        const int w = k > 4 ? 16 : 1 << k;
+                        return rmax(Lk[x], Lk[y - w + 1]);
+                    };
+                    const int a = t + 1, z = t + q0 - 1;
+                    const int wa = a >> 5, wz = z >> 5;
+                    if (wa == wz) {
+                        mid = span(a, z);
+                    } else {
+                        mid = rmax(span(a, wa * 32 + 31), span(wz * 32, z));
+                        for (int w = wa + 1; w < wz; ++w) mid = rmax(mid, rmax(LVp[3 * NTc + w * 32], LVp[3 * NTc + w * 32 + 16]));
+                    }
+                }
+                if (active && owns_positions) {
+                    real suf[V];
+                    suf[V - 1] = rho[V - 1];
+    #pragma unroll
+                    for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
+                    key_t* ABr = ABo + (size_t)r * RS + (t - tofs);
+                    if (!small_R) {
+                        // whole chunks strictly inside the window: t+1 .. t+q0-1 (mid) for small
+                        // i, one more (t+q0) once the window end moves into chunk t+q0+1
+                        const real mid1 = rmax(mid, CMp[t + q0]);
+    #pragma unroll
+                        for (int i = 0; i < V; ++i) {
+                            const int e = i + R - 1;        // window end, relative to xb
+                            const int oi = e / V, si = e - oi * V;
+                            const real ab = rmax(rmax(suf[i], oi > q0 ? mid1 : mid), PREp[si * LP + t + oi]);
+                            if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
+                        }
+                    } else {
+    #pragma unroll
+                        for (int i = 0; i < V; ++i) {
+                            real ab;
+                            if (i + R - 1 < V) {  // window inside this chunk
+                                ab = NEG;
+    #pragma unroll
+                                for (int j = 0; j < V; ++j)
+                                    if (j >= i && j < i + R) ab = rmax(ab, rho[j]);
+                            } else {
+                                const int e = i + R - 1;
+                                const int oi = e / V, si = e - oi * V;
+                                ab = rmax(suf[i], PREp[si * LP + t + oi]);
+                            }
+                            if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
+                        }
                     }
                 }
             }
-        }
-        // fold the small covariance term into the large one every V rows
+            // FP64: fold the small covariance term into the large one every V rows
+            // (FP32 folds it every row, keeping the remainder)
+            if constexpr (sizeof(real) == 8) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            hi[v] += lo[v];
-            lo[v] = 0;
+                for (int v = 0; v < V; ++v) {
+                    hi[v] += lo[v];
+                    lo[v] = 0;
+                }
+            }
         }
+    };
+    // The conditioning check is compiled into a second copy of the row loop,
+    // taken only by tiles where some thread can meet the flag: in the others
+    // the loop carries none of its code (a branch and an inner loop at every
+    // row cost them about 7 % of their time even when never taken).
+    if constexpr (sizeof(real) == 4) {
+        if (__syncthreads_or(kap_check)) row_loop(std::true_type{});
+        else row_loop(std::false_type{});
+    } else {
+        row_loop(std::false_type{});
     }
     // column maxima over all row groups
     {

@@ -33,7 +33,7 @@ class EngineConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("prec", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
                 ("max_active_jobs", ctypes.c_int32), ("wave_ed_cells", ctypes.c_double),
                 ("max_waves_in_flight", ctypes.c_int32), ("fail_alloc_at", ctypes.c_int32),
-                ("age_weight_s", ctypes.c_double), ("policy", ctypes.c_int32)]
+                ("age_weight_s", ctypes.c_double), ("policy", ctypes.c_int32), ("fp32_greedy", ctypes.c_int32)]
 
 
 POLICY_SHARE, POLICY_SRPT = 0, 1
@@ -100,6 +100,8 @@ def load(path: str | None = None):
         lib.pastila_profiles_device.restype = S
         lib.pastila_stage_status.argtypes = [_vp]
         lib.pastila_stage_status.restype = S
+        lib.pastila_set_fp64_ties.argtypes = [_vp, ctypes.c_int]
+        lib.pastila_set_fp64_ties.restype = S
         lib.pastila_snippets.argtypes = [_vp, ctypes.c_int32, MParams, ctypes.c_int32,
                                          ctypes.POINTER(Snippet), _vp, _vp]
         lib.pastila_snippets.restype = S
@@ -270,6 +272,11 @@ class Series:
         _check(load().pastila_profiles_device(self._h, m, MParams(ell, k), _vp(D_ptr),
                                               _vp(dmax_ptr) if dmax_ptr else None))
 
+    def set_fp64_ties(self, on: bool):
+        """``pastila_set_fp64_ties``: decide near-tied greedy steps of an FP32
+        handle on FP64 areas (the default) or on the FP32 areas alone."""
+        _check(load().pastila_set_fp64_ties(self._h, 1 if on else 0))
+
     def stage_status(self):
         """``pastila_stage_status``: raise if a staging wait of enqueued tile work ran
         out (call after synchronising the handle's stream)."""
@@ -333,10 +340,10 @@ class Engine:
 
     def __init__(self, device: int = 0, precision: int = FP32, mem_budget: int = 0, max_active: int = 0,
                  wave_ed_cells: float = 0.0, max_waves_in_flight: int = 0, fail_alloc_at: int = 0,
-                 age_weight_s: float = 0.0, policy: int = POLICY_SHARE):
+                 age_weight_s: float = 0.0, policy: int = POLICY_SHARE, fp32_greedy: bool = False):
         lib = load()
         cfg = EngineConfig(device, precision, mem_budget, max_active, wave_ed_cells, max_waves_in_flight,
-                           fail_alloc_at, age_weight_s, policy)
+                           fail_alloc_at, age_weight_s, policy, 1 if fp32_greedy else 0)
         h = _vp()
         _check(lib.pastila_engine_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h

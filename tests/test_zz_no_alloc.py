@@ -24,6 +24,9 @@ def test_greedy_noalloc_matches_snippets(lib):
     dev = torch.device("cuda", 0)
     K = 4
     with pastila.Series(s.T, precision=pastila.FP32) as h:
+        # the allocation-free search decides every step on FP32 areas, as
+        # pastila_snippets does with the FP64 re-evaluation of near-ties off
+        h.set_fp64_ties(False)
         # two calls in a row, with different sizes, through the one shared scratch array
         for m in (128, 96):
             S, P = h.n // m, h.n - m + 1
