@@ -165,7 +165,7 @@ struct ProfileArgs {
 
 // Shared-memory layout and thread layout of one tile; identical on host and device.
 struct TileGeom {
-    int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, LP, ell, m;
+    int R, W, Wb, V, NTc, NWc, NG, Rg, NT, LA, RS, ell, m;
     int GS;  // lanes per selection run (32: one warp per run of positions)
     // tiles of a thread-block cluster of CS CTAs (1, 2 or 4): CTA c computes rows
     // c Rh .. c Rh + Rh - 1 over every column of the tile and selects positions
@@ -174,7 +174,7 @@ struct TileGeom {
     // memory), CBp[c'] the partial column maxima of CTA c'
     int CS, Rh, Wc;
     int RSt;  // stride of the five row-statistic arrays (room for a 16-byte-aligned copy of R values)
-    size_t off_AB, off_CB, off_PRE, off_CM, off_LV, off_XCH, off_row, off_left, off_top, off_Tc, off_Tcl,
+    size_t off_AB, off_CB, off_PRE, off_LV, off_XCH, off_rst, off_row, off_left, off_top, off_Tc, off_Tcl,
         off_Ts, off_Tsl, off_q, off_CBp, bytes;
 };
 
@@ -205,16 +205,15 @@ __host__ __device__ inline TileGeom tile_geom(int m, int ell, int W, int V, int 
     // column reads of the selection (one position, many rows) in distinct banks
     g.LA = (g.Wc + V - 1) / V;
     g.RS = (V * g.LA) | 1;
-    g.LP = g.NTc + 1;  // chunk prefix maxima: [V][LP], thread t at t (+ chunk offset)
     g.GS = 32;  // lanes per selection run: one warp
     const size_t NG = (size_t)g.NG;
     size_t o = 0;
     g.off_AB = o;   o = align16(o + sizeof(key_t) * (size_t)g.R * g.RS);
     g.off_CB = o;   o = align16(o + sizeof(key_t) * (size_t)(g.Wb + 32));
-    g.off_PRE = o;  o = align16(o + sizeof(real) * NG * 2 * (size_t)V * g.LP);
-    g.off_CM = o;   o = align16(o + sizeof(real) * NG * 2 * (size_t)(g.NTc + 1));
-    g.off_LV = o;   o = align16(o + sizeof(real) * NG * 2 * 4 * (size_t)g.NTc);
+    g.off_PRE = o;  o = align16(o + sizeof(real) * (NG * 2 * (size_t)(g.NTc * V) + 16));  // + reads past the last chunk
+    g.off_LV = o;   o = align16(o + sizeof(real) * NG * 2 * 5 * (size_t)g.NTc);
     g.off_XCH = o;  o = align16(o + sizeof(real) * NG * 4 * (size_t)g.NWc);
+    g.off_rst = o;  o = align16(o + sizeof(real) * 4 * (size_t)g.R);
     // staged copies start at a 16-byte boundary at or below the data (up to
     // 16 / sizeof(real) - 1 elements early) and cover whole 16-byte units
     const int AE = 16 / (int)sizeof(real);
@@ -459,6 +458,27 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
     };
     // contribution of one value to the packed counts (#{>= tau} + 65536 #{> tau})
     auto cnt2 = [&](real x) { return (x >= tau ? 1 : 0) + (x > tau ? 65536 : 0); };
+    // packed counts of this lane's register-held AB values at tau (recounted
+    // only when tau moves): a position's count change is then the new values'
+    // counts less this
+    auto held = [&]() {
+        int c = 0;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) c += cnt2(cur[j]);
+        return c;
+    };
+    // the column of the next position, loaded one position ahead so that the
+    // loads overlap the current position's reductions
+    real nxt[NJ];
+    auto load_col = [&](int q, real* dst) {
+        const int c = (q & (V - 1)) * LA + q / V;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) dst[j] = rin[j] ? AB[roff[j] + c] : NEG;
+    };
+    int ccur = 0;
+    // the window slide: lane 0 adds the entering column maximum, lane 1 removes the leaving one
+    const int wofs = lane == 0 ? R - 1 : -1;
+    const int wsgn = lane == 0 ? 1 : (lane == 1 ? -1 : 0);
 
     for (int it = 0; it < npos; ++it) {
         p = p_begin + it;
@@ -466,40 +486,47 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
         const int q = p - pofs;
         cp = (q & (V - 1)) * LA + q / V;
         if (it == 0) {
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) cur[j] = rin[j] ? AB[roff[j] + cp] : NEG;
+            load_col(q, cur);
+            if (npos > 1) load_col(q + 1, nxt);
             search();
+            ccur = held();
         } else {
             // count changes of the values that changed: rows, then the window slide
-            int d = 0;
+            int nsum = 0;
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
-                const real nv = rin[j] ? AB[roff[j] + cp] : NEG;
-                d += cnt2(nv) - cnt2(cur[j]);
-                cur[j] = nv;
+                cur[j] = nxt[j];
+                nsum += cnt2(cur[j]);
             }
+            if (it + 1 < npos) load_col(q + 1, nxt);
+            int d = nsum - ccur;
+            ccur = nsum;
             for (int j = NJ; j < nrw; ++j) {
                 const int r = lane + 32 * j;
                 if (r < R) d += cnt2(AB[r * RS + cp]) - cnt2(AB[r * RS + cprev]);
             }
-            d = (int)__reduce_add_sync(FULL, (unsigned)d) + cnt2(CB[p + R - 1]) - cnt2(CB[p - 1]);
+            d += wsgn * cnt2(CB[p + wofs]);
+            d = (int)__reduce_add_sync(FULL, (unsigned)d);
             const int dge = (int)(int16_t)(d & 0xffff);
             cge += dge;
             cgt += (d - dge) >> 16;
-            // the answer moved: step to the nearest value on its side, with exact counts
-            for (int step = 0; step < SEL_STEPS && !(cgt < kk && kk <= cge); ++step) {
-                int mult;
-                if (cge < kk) {
-                    tau = nearest_below(tau, &mult);
-                    cgt = cge;
-                    cge += mult;
-                } else {
-                    tau = nearest_above(tau, false, &mult);
-                    cge = cgt;
-                    cgt -= mult;
+            if (!(cgt < kk && kk <= cge)) {
+                // the answer moved: step to the nearest value on its side, with exact counts
+                for (int step = 0; step < SEL_STEPS && !(cgt < kk && kk <= cge); ++step) {
+                    int mult;
+                    if (cge < kk) {
+                        tau = nearest_below(tau, &mult);
+                        cgt = cge;
+                        cge += mult;
+                    } else {
+                        tau = nearest_above(tau, false, &mult);
+                        cge = cgt;
+                        cgt -= mult;
+                    }
                 }
+                if (!(cgt < kk && kk <= cge)) search();
+                ccur = held();
             }
-            if (!(cgt < kk && kk <= cge)) search();
         }
         // lane (it mod 32) keeps this position's answer; 32 positions are written at once
         if (lane == (it & 31)) mine = tau;
@@ -522,7 +549,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int BD = blockDim.x;
     const bool worker = tid < G.NT;
     const int NTc = G.NTc, NWc = G.NWc;
-    const int RS = G.RS, LA = G.LA, LP = G.LP, NG = G.NG;  // read once: hot loops use registers
+    const int RS = G.RS, LA = G.LA, NG = G.NG;  // read once: hot loops use registers
     const int g = worker ? tid / NTc : 0, t = tid % NTc, wc = t >> 5;  // row group, column thread, warp in group
     const int R = A.R, ell = A.ell, m = A.m, Rg = G.Rg;
     // cluster tiles: this CTA's rows and positions (one CTA: all of them)
@@ -542,11 +569,12 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const bool keyed = false;  // AB and CB hold values (select_warp compares values)
     key_t* AB = (key_t*)(sm + G.off_AB);
     key_t* CB = (key_t*)(sm + G.off_CB);
-    real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * V * LP;  // this group's [parity][V][LP]
-    real* CM = (real*)(sm + G.off_CM) + (size_t)g * 2 * (NTc + 1);   // [parity][NTc + 1]
-    real* LV = (real*)(sm + G.off_LV) + (size_t)g * 2 * 4 * NTc;     // [parity][k-1][NTc]: max of the 2^k chunk
+    real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * NTc * V;  // this group's [parity][column]: maxima
+                                                                      // from the column's chunk start to it
+    real* LV = (real*)(sm + G.off_LV) + (size_t)g * 2 * 5 * NTc;     // [parity][k][NTc]: max of the 2^k chunk
                                                                       // maxima from a chunk on, within its warp
-    real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][hi/lo][warp]
+    real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][warp][hi, lo]
+    real* rst = (real*)(sm + G.off_rst);                              // [row][df, dg, a, 0]
     // segment data are staged from the 16-byte boundary at or below i0
     constexpr int AE = 16 / (int)sizeof(real);
     const int os = (int)(i0 % AE);
@@ -674,6 +702,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             const unsigned b = __reduce_max_sync(FULL, __float_as_uint(km));
             if (lane == 0 && b) atomicMax(&kap_rmax, b);
         }
+    }
+    // the rows' statistics side by side (one 16-byte load per row step)
+    for (int r = rbase + tid; r < rend; r += BD) {
+        rst[4 * r + 0] = rdf[r];
+        rst[4 * r + 1] = rdg[r];
+        rst[4 * r + 2] = ra[r];
+        rst[4 * r + 3] = (real)0;
     }
     // the groups' centred heads q = T[ig + u] - mu_ig, ig = i0 + rbase + gg Rg
     for (int e = tid; e < NG * ell; e += BD) {
@@ -846,8 +881,43 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         cooperative_groups::this_cluster().sync();
     }
 
+    // Loop-invariant parts of the row-window maxima of this thread's positions:
+    // the maximum of the whole chunks t+1 .. t+q0-1 comes from the sparse tables
+    // (two overlapping spans of 2^k chunks for the part in each warp the range
+    // touches, two spans of 16 for every whole warp in between); so[] are those
+    // table offsets.  The window of position xb + i ends at column xb + i + R - 1
+    // (its prefix within its chunk is PRE[that column]) and covers chunk t + q0
+    // entirely when i + rr >= V.
+    const int rr = (R - 1) - q0 * V;
+    int so[4] = {0, 0, 0, 0};
+    int wlo = 0, whi = -1;  // whole warps wlo .. whi between the spans
+    const bool use_mid = owns_positions && !small_R && q0 >= 2;
+    if (use_mid) {
+        const int a = t + 1, z = t + q0 - 1;
+        const int wa = a >> 5, wz = z >> 5;
+        auto span = [&](int x, int y, int* o) {  // x <= y in one warp
+            int k = 31 - __clz(y - x + 1);
+            k = k > 4 ? 4 : k;
+            o[0] = k * NTc + x;
+            o[1] = k * NTc + y - (1 << k) + 1;
+        };
+        if (wa == wz) {
+            span(a, z, so);
+            so[2] = so[0];
+            so[3] = so[1];
+        } else {
+            span(a, wa * 32 + 31, so);
+            span(wz * 32, z, so + 2);
+            wlo = wa + 1;
+            whi = wz - 1;
+        }
+    }
+    const int far0 = xb + R - 1;  // PRE column of the window end of position xb
+    const bool far_vec = sizeof(real) == 4 && V == 4 && rr == 0;  // 16-byte aligned: xb and R - 1 multiples of 4
+
     auto row_loop = [&](auto check_tag) {
     constexpr bool CHECK = decltype(check_tag)::value;
+        key_t* ABr = ABo + (size_t)r0 * RS + (t - tofs);
         for (int c0 = 0; c0 < Rg; c0 += V) {
     #pragma unroll
             for (int jj = 0; jj < V; ++jj) {
@@ -855,22 +925,30 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 const int r = r0 + sidx;
                 const bool active = sidx < nrows;  // uniform within the group
                 const int par = sidx & 1;
-                real* PREp = PRE + par * V * LP;
-                real* CMp = CM + par * (NTc + 1);
-                real* LVp = LV + par * 4 * NTc;
+                real* PREp = PRE + par * NTc * V;
+                real* LVp = LV + par * 5 * NTc;
                 // logical column v of this thread lives in register (v - jj) mod V
                 real rho[V];
-                real pre = NEG;  // this thread's chunk maximum
                 if (active) {
+                    real fr, gr, ar;
+                    if constexpr (sizeof(real) == 4) {
+                        const float4 q4 = *reinterpret_cast<const float4*>(rst + 4 * r);
+                        fr = q4.x;
+                        gr = q4.y;
+                        ar = q4.z;
+                    } else {
+                        fr = rst[4 * r];
+                        gr = rst[4 * r + 1];
+                        ar = rst[4 * r + 2];
+                    }
                     if (sidx > 0) {
                         const int Pout = (V - jj) % V;  // register of the previous row's last column
                         real lhi = __shfl_up_sync(FULL, hi[Pout], 1);
                         real llo = __shfl_up_sync(FULL, lo[Pout], 1);
                         if (lane == 0 && wc > 0) {
-                            lhi = XCH[((par ^ 1) * 2 + 0) * NWc + wc - 1];
-                            llo = XCH[((par ^ 1) * 2 + 1) * NWc + wc - 1];
+                            lhi = XCH[((par ^ 1) * NWc + wc - 1) * 2 + 0];
+                            llo = XCH[((par ^ 1) * NWc + wc - 1) * 2 + 1];
                         }
-                        const real fr = rdf[r], gr = rdg[r];
     #pragma unroll
                         for (int v = 1; v < V; ++v) {
                             const int P = (v - jj + V) % V;
@@ -925,10 +1003,9 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     }
                     if (lane == 31) {
                         const int Plast = (V - 1 - jj + V) % V;
-                        XCH[(par * 2 + 0) * NWc + wc] = hi[Plast];
-                        XCH[(par * 2 + 1) * NWc + wc] = lo[Plast];
+                        XCH[(par * NWc + wc) * 2 + 0] = hi[Plast];
+                        XCH[(par * NWc + wc) * 2 + 1] = lo[Plast];
                     }
-                    const real ar = ra[r];
                     if (ar != (real)0) {
     #pragma unroll
                         for (int v = 0; v < V; ++v) {
@@ -953,61 +1030,59 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     }
     #pragma unroll
                     for (int v = 0; v < V; ++v) cmx[v] = rmax(cmx[v], rho[v]);
-                    pre = rho[0];
-                    PREp[t] = pre;
+                    // prefix maxima within the chunk, stored by column
+                    real pre[V];
+                    pre[0] = rho[0];
     #pragma unroll
-                    for (int v = 1; v < V; ++v) {
-                        pre = rmax(pre, rho[v]);
-                        PREp[v * LP + t] = pre;
+                    for (int v = 1; v < V; ++v) pre[v] = rmax(pre[v - 1], rho[v]);
+                    if constexpr (sizeof(real) == 4 && V == 4) {
+                        *reinterpret_cast<float4*>(PREp + xb) = make_float4(pre[0], pre[1], pre[2], pre[3]);
+                    } else {
+    #pragma unroll
+                        for (int v = 0; v < V; ++v) PREp[xb + v] = pre[v];
                     }
-                    CMp[t] = pre;
-                    if (t == 0) CMp[NTc] = NEG;
-                    if (!small_R && q0 >= 2) {  // sparse table of the chunk maxima within each warp
-                        real d = pre;
+                    if (!small_R) {  // sparse table of the chunk maxima within each warp (level 0: the chunk maxima)
+                        real d = pre[V - 1];
+                        LVp[t] = d;
+                        if (q0 >= 2) {
     #pragma unroll
-                        for (int k = 0; k < 4; ++k) {  // entries reaching past the warp's end are never read
-                            d = rmax(d, __shfl_down_sync(FULL, d, 1 << k));
-                            LVp[k * NTc + t] = d;
+                            for (int k = 0; k < 4; ++k) {  // entries reaching past the warp's end are never read
+                                d = rmax(d, __shfl_down_sync(FULL, d, 1 << k));
+                                LVp[(k + 1) * NTc + t] = d;
+                            }
                         }
                     }
                 }
                 __syncthreads();
-                // maximum of the whole chunks t+1 .. t+q0-1 strictly inside the windows of
-                // this thread's positions, from the sparse tables: two overlapping spans of
-                // 2^k chunks for the part in each warp the range touches, two spans of 16
-                // for every whole warp in between
-                real mid = NEG;
-                if (active && owns_positions && !small_R && q0 >= 2) {
-                    auto span = [&](int x, int y) {  // x <= y in one warp
-                        const int k = 31 - __clz(y - x + 1);
-                        const real* Lk = k == 0 ? CMp : LVp + (k > 4 ? 3 : k - 1) * NTc;
-                        const int w = k > 4 ? 16 : 1 << k;
-                        return rmax(Lk[x], Lk[y - w + 1]);
-                    };
-                    const int a = t + 1, z = t + q0 - 1;
-                    const int wa = a >> 5, wz = z >> 5;
-                    if (wa == wz) {
-                        mid = span(a, z);
-                    } else {
-                        mid = rmax(span(a, wa * 32 + 31), span(wz * 32, z));
-                        for (int w = wa + 1; w < wz; ++w) mid = rmax(mid, rmax(LVp[3 * NTc + w * 32], LVp[3 * NTc + w * 32 + 16]));
-                    }
-                }
                 if (active && owns_positions) {
                     real suf[V];
                     suf[V - 1] = rho[V - 1];
     #pragma unroll
                     for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
-                    key_t* ABr = ABo + (size_t)r * RS + (t - tofs);
                     if (!small_R) {
-                        // whole chunks strictly inside the window: t+1 .. t+q0-1 (mid) for small
-                        // i, one more (t+q0) once the window end moves into chunk t+q0+1
-                        const real mid1 = rmax(mid, CMp[t + q0]);
+                        // whole chunks strictly inside the windows: t+1 .. t+q0-1 (mid), and
+                        // chunk t+q0 as well once the window end moves into chunk t+q0+1
+                        real mid = NEG;
+                        if (use_mid) {
+                            mid = rmax(rmax(LVp[so[0]], LVp[so[1]]), rmax(LVp[so[2]], LVp[so[3]]));
+                            for (int w = wlo; w <= whi; ++w)
+                                mid = rmax(mid, rmax(LVp[4 * NTc + w * 32], LVp[4 * NTc + w * 32 + 16]));
+                        }
+                        real far[V];
+                        if (far_vec) {
+                            const float4 f4 = *reinterpret_cast<const float4*>(PREp + far0);
+                            far[0] = f4.x;
+                            far[1] = f4.y;
+                            far[2] = f4.z;
+                            far[3] = f4.w;
+                        } else {
+    #pragma unroll
+                            for (int i = 0; i < V; ++i) far[i] = PREp[far0 + i];
+                        }
+                        const real mid1 = rr > 0 ? rmax(mid, LVp[t + q0]) : mid;
     #pragma unroll
                         for (int i = 0; i < V; ++i) {
-                            const int e = i + R - 1;        // window end, relative to xb
-                            const int oi = e / V, si = e - oi * V;
-                            const real ab = rmax(rmax(suf[i], oi > q0 ? mid1 : mid), PREp[si * LP + t + oi]);
+                            const real ab = rmax(rmax(suf[i], i + rr >= V ? mid1 : mid), far[i]);
                             if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
                         }
                     } else {
@@ -1020,14 +1095,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                                 for (int j = 0; j < V; ++j)
                                     if (j >= i && j < i + R) ab = rmax(ab, rho[j]);
                             } else {
-                                const int e = i + R - 1;
-                                const int oi = e / V, si = e - oi * V;
-                                ab = rmax(suf[i], PREp[si * LP + t + oi]);
+                                ab = rmax(suf[i], PREp[far0 + i]);
                             }
                             if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
                         }
                     }
                 }
+                ABr += RS;
             }
             // FP64: fold the small covariance term into the large one every V rows
             // (FP32 folds it every row, keeping the remainder)

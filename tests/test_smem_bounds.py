@@ -36,17 +36,16 @@ def geometry(prec, m, ell, lay):
     Wc = W // CS
     LA = (Wc + V - 1) // V
     RS = (V * LA) | 1
-    LP = NTc + 1
     AE = 16 // es
     RSt = (R + 2 * AE + AE - 1) // AE * AE
-    n = dict(AB=R * RS, CB=Wb + 32, PRE=NG * 2 * V * LP, CM=NG * 2 * (NTc + 1), LV=NG * 2 * 4 * NTc,
-             XCH=NG * 4 * NWc, row=5 * RSt, left=R, top=NG * NTc * V, Tc=NTc * V + ell + 64,
+    n = dict(AB=R * RS, CB=Wb + 32, PRE=NG * 2 * NTc * V + 16, LV=NG * 2 * 5 * NTc,
+             XCH=NG * 4 * NWc, rst=4 * R, row=5 * RSt, left=R, top=NG * NTc * V, Tc=NTc * V + ell + 64,
              Tcl=NTc * V + ell + 64, Ts=m + 2 * AE, Tsl=m + 2 * AE, q=NG * (ell + 1),
              CBp=CS * (Wb + 32) if CS > 1 else 0)
     o = 0
-    for k in ("AB", "CB", "PRE", "CM", "LV", "XCH", "row", "left", "top", "Tc", "Tcl", "Ts", "Tsl", "q", "CBp"):
+    for k in ("AB", "CB", "PRE", "LV", "XCH", "rst", "row", "left", "top", "Tc", "Tcl", "Ts", "Tsl", "q", "CBp"):
         o = _a16(o + es * n[k])
-    return dict(n, R=R, W=W, Wb=Wb, NTc=NTc, NWc=NWc, Wc=Wc, LA=LA, RS=RS, LP=LP, RSt=RSt, AE=AE, es=es,
+    return dict(n, R=R, W=W, Wb=Wb, NTc=NTc, NWc=NWc, Wc=Wc, LA=LA, RS=RS, RSt=RSt, AE=AE, es=es,
                 CS=CS, Rg=Rg, NG=NG, GS=lay["GS"], NT=lay["NT"], ell=ell, m=m, bytes=o)
 
 
@@ -103,33 +102,39 @@ def _assert_union(pieces, lo, hi):
 
 
 def rows_phase_check(G, Wp):
-    """Every shared-memory index of the rows phase of a tile with Wp positions (per row group: the chunk prefix maxima PRE [parity][V][LP], the
-    chunk maxima CM [parity][NTc + 1], the sparse tables LV [parity][4][NTc], the
-    warp exchange XCH [parity][2][NWc]; the row-window maxima written into the
-    owning CTA's AB) lies inside its array, each sparse-table read spans chunks
-    of one warp, and the pieces of every owned position's window (own suffix,
-    whole chunks in between, the far chunk's prefix) cover exactly its R columns."""
-    R, V_, NTc, NWc, LP = G["R"], V, G["NTc"], G["NWc"], G["LP"]
+    """Every shared-memory index of the rows phase of a tile with Wp positions
+    (per row group and parity: the prefix maxima within each chunk PRE, stored
+    by column; the sparse tables LV [5][NTc] of the chunk maxima (level 0) and
+    of 2, 4, 8, 16 consecutive chunks; the warp exchange XCH [NWc][2]; the row
+    statistics [R][4]; the row-window maxima written into the owning CTA's AB)
+    lies inside its array, each sparse-table read spans chunks of one warp, and
+    the pieces of every owned position's window (own suffix, whole chunks in
+    between, the far chunk's prefix) cover exactly its R columns."""
+    R, V_, NTc, NWc = G["R"], V, G["NTc"], G["NWc"]
     RS, LA, Wc, CS = G["RS"], G["LA"], G["Wc"], G["CS"]
+    per_par_pre = NTc * V_
     q0 = (R - 1) // V_
+    rr = (R - 1) - q0 * V_
     small_R = R - 1 < V_
     t = np.arange(NTc)
     xb = t * V_
     # writes of every active thread (all column threads take part in every row step)
-    assert (V_ - 1) * LP + t.max() < V_ * LP            # PRE
-    assert t.max() < NTc + 1 and NTc < NTc + 1           # CM, and its sentinel
-    assert 3 * NTc + t.max() < 4 * NTc                   # LV
-    assert 1 * NWc + (NWc - 1) < 2 * NWc                 # XCH within its parity
+    assert per_par_pre + xb.max() + V_ - 1 < G["PRE"] // G["NG"]  # PRE, parity 1
+    assert 5 * NTc + 4 * NTc + t.max() < 2 * 5 * NTc              # LV, parity 1, level 4
+    assert (1 * NWc + NWc - 1) * 2 + 1 < 4 * NWc                  # XCH, parity 1
+    assert 4 * (R - 1) + 3 < G["rst"]
     owners = xb < Wp
     for tt in (int(x) for x in t[owners]):
         x0 = tt * V_
+        # every far read (all V of the thread, owned or not) stays inside PRE
+        assert per_par_pre + x0 + V_ - 1 + R - 1 < G["PRE"] // G["NG"]
         # window pieces, as column ranges relative to the tile
         for i in range(V_):
             if x0 + i >= Wp:
                 continue
             e = i + R - 1
             oi, si = e // V_, e % V_
-            assert (si * LP + tt + oi) < V_ * LP and tt + oi <= NTc - 1
+            assert x0 + e == (tt + oi) * V_ + si and tt + oi <= NTc - 1  # PRE column of the far prefix
             lo, hi = x0 + i, x0 + i + R - 1
             if small_R and e < V_:
                 cover = [(lo, hi)]                       # inside this chunk
@@ -137,25 +142,27 @@ def rows_phase_check(G, Wp):
                 cover = [(x0 + i, x0 + V_ - 1)]          # own suffix
                 if not small_R and q0 >= 2:
                     cover.append(((tt + 1) * V_, (tt + q0) * V_ - 1))  # whole chunks t+1 .. t+q0-1
-                if not small_R and oi > q0:
+                if not small_R and i + rr >= V_:
+                    assert oi > q0
                     cover.append(((tt + q0) * V_, (tt + q0 + 1) * V_ - 1))  # chunk t+q0
                 cover.append(((tt + oi) * V_, (tt + oi) * V_ + si))  # far chunk's prefix
             _assert_union(cover, lo, hi)
-        if not small_R:
-            assert tt + q0 <= NTc                        # CM[t + q0] (the sentinel at NTc)
+        if not small_R and rr > 0:
+            assert tt + q0 <= NTc - 1                    # LV level 0 at t + q0
         if not small_R and q0 >= 2:
             a_, z_ = tt + 1, tt + q0 - 1
             wa, wz = a_ >> 5, z_ >> 5
             spans = [(a_, z_)] if wa == wz else [(a_, wa * 32 + 31), (wz * 32, z_)]
             pieces = []
             for x, y in spans:
-                k = int(y - x + 1).bit_length() - 1
-                w = 16 if k > 4 else 1 << k
+                k = min(int(y - x + 1).bit_length() - 1, 4)
+                w = 1 << k
                 for s0 in (x, y - w + 1):
                     assert s0 >> 5 == (s0 + w - 1) >> 5 and 0 <= s0 and s0 + w - 1 < NTc
+                    assert k * NTc + s0 < 5 * NTc
                     pieces.append((s0, s0 + w - 1))
             for wv in range(wa + 1, wz):
-                assert 3 * NTc + wv * 32 + 16 < 4 * NTc
+                assert 4 * NTc + wv * 32 + 16 < 5 * NTc
                 pieces += [(wv * 32, wv * 32 + 15), (wv * 32 + 16, wv * 32 + 31)]
             _assert_union(pieces, a_, z_)
         # the row-window maxima of this thread's positions, into the owner's AB
@@ -199,7 +206,7 @@ def check_layout(prec, m, ell, lay):
     nblk = (G["NTc"] * V + J - 1) // J
     assert (nblk - 1) * J + ell - 1 + J < G["Tc"]
     # row-window maxima of owned positions end inside the chunk prefix arrays
-    assert (G["W"] - 1 + R - 1) // V <= G["NTc"] - 1
+    assert G["W"] - 1 + R - 1 <= G["NTc"] * V - 1
 
 
 def _cases():
