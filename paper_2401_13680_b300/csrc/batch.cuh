@@ -31,7 +31,6 @@ namespace pastila {
 // segment come from the FP64 tile kernel, and the curve M of FP64 rows gives
 // the FP64 areas (lowest segment index on ties).
 constexpr int REF_NCAND = 16;
-constexpr int REF_TODO_GRID = 4;   // grid rows of the FP64 row launch (each loops over the to-do list)
 // layout of an item's refinement state (int32):
 constexpr int REF_TODO_N = 0;      // rows the next FP64 row launch computes
 constexpr int REF_NC = 1;          // contenders of the current step (0: decided in FP32)
@@ -260,20 +259,26 @@ __global__ void batched_select_kernel(const BatchItem<real>* __restrict__ items,
 }
 
 // FP64 rows of an item's to-do list (one item per launch): grid (ntiles64 CS64,
-// REF_TODO_GRID); each CTA computes tile blockIdx.x / CS64 of to-do rows
-// blockIdx.y, blockIdx.y + REF_TODO_GRID, ...  Row y goes to rows64 slot
-// todo_slot[y] (the profile tile writes row s - row_base of its D).
+// K + REF_NCAND, at least the longest to-do list); each CTA computes tile
+// blockIdx.x / CS64 of to-do row blockIdx.y (CTAs past the list's end return at
+// once).  Row y goes to rows64 slot todo_slot[y] (the profile tile writes row
+// s - row_base of its D).
 template <int V>
 __global__ void __launch_bounds__(512) refine_rows_kernel(const BatchItem<float>* __restrict__ item, int t) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ProfileArgs<double> sA;
+    __shared__ TileGeom sG;
     if (t >= item->K || !item->rows64) return;
     const int32_t* rst = item->rst;
     const int n = rst[REF_TODO_N];
-    for (int y = blockIdx.y; y < n; y += gridDim.y) {
-        const int seg = rst[REF_TODO_SEG + y], slot = rst[REF_TODO_SLOT + y];
-        profile_tile<double, V>(item->A64, item->G64, seg, (int)blockIdx.x / item->G64.CS, smem, seg - slot);
-        __syncthreads();
+    if ((int)blockIdx.y >= n) return;
+    if (threadIdx.x == 0) {
+        sA = item->A64;
+        sG = item->G64;
     }
+    __syncthreads();
+    const int seg = rst[REF_TODO_SEG + blockIdx.y], slot = rst[REF_TODO_SLOT + blockIdx.y];
+    profile_tile<double, V>(sA, sG, seg, (int)blockIdx.x / sG.CS, smem, seg - slot);
 }
 
 // FP64 areas of the contenders of step t: cand_area[c] = sum_p min(M64_p,

@@ -56,4 +56,13 @@ template <> struct KeyOf<double> {
     }
 };
 
+// The keys of FP64 values are selected as they are (the FP64 tiles keep their
+// maxima as keys, so that every comparison is an integer compare rather than an
+// FP64 one): a key is its own key.
+template <> struct KeyOf<unsigned long long> {
+    typedef unsigned long long type;
+    __host__ __device__ static inline unsigned long long enc(unsigned long long k) { return k; }
+    __host__ __device__ static inline unsigned long long dec(unsigned long long k) { return k; }
+};
+
 }  // namespace pastila

@@ -663,7 +663,7 @@ int enqueue_greedy(cudaStream_t s, const BatchItem<real>* d_items, const std::ve
                 if (!it.rows64 || t >= it.K) continue;
                 const TileGeom& g = it.G64;
                 const cudaError_t e = launch_tiles(refine_rows_kernel<V_F64>,
-                                                   dim3((unsigned)(it.A64.ntiles * g.CS), REF_TODO_GRID), g.NT,
+                                                   dim3((unsigned)(it.A64.ntiles * g.CS), (unsigned)(it.K + REF_NCAND)), g.NT,
                                                    g.bytes, s, g.CS, d_items + i, t);
                 if (e != cudaSuccess) {
                     *err = fail(PASTILA_ECUDA, "FP64 rows launch: %s", cudaGetErrorString(e));

@@ -123,6 +123,38 @@ template <> struct RealLimits<double> {
     __host__ __device__ static constexpr double lowest() { return -DBL_MAX; }
     __host__ __device__ static constexpr double max() { return DBL_MAX; }
 };
+template <> struct RealLimits<unsigned long long> {  // keys of FP64 values
+    __host__ __device__ static constexpr unsigned long long lowest() { return 0ull; }
+    __host__ __device__ static constexpr unsigned long long max() { return ~0ull; }
+};
+
+// Maxima and the selection compare FP32 values directly, and FP64 values by
+// their order-preserving integer keys (B300 runs FP64 comparisons at a small
+// fraction of the integer rate).  -0 is taken as +0 so that equal values have
+// equal keys.
+template <typename real> struct CmpOf { typedef real type; };
+template <> struct CmpOf<double> { typedef unsigned long long type; };
+__device__ __forceinline__ float to_cmp(float v) { return v; }
+__device__ __forceinline__ unsigned long long to_cmp(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    u = u == KeyOf<double>::TOP ? 0ull : u;
+    return (u & KeyOf<double>::TOP) ? ~u : (u | KeyOf<double>::TOP);
+}
+__device__ __forceinline__ float cmp_value(float c) { return c; }
+__device__ __forceinline__ double cmp_value(unsigned long long c) { return KeyOf<double>::dec(c); }
+// the bits a shared-memory key slot holds for a compared quantity
+__device__ __forceinline__ uint32_t cmp_bits(float c) { return __float_as_uint(c); }
+__device__ __forceinline__ unsigned long long cmp_bits(unsigned long long c) { return c; }
+// a key between kL and kH by interpolating the values at fraction f
+__device__ __forceinline__ uint32_t interp_key(uint32_t kL, uint32_t kH, float f, uint32_t) {
+    const float vL = KeyOf<float>::dec(kL), vH = KeyOf<float>::dec(kH);
+    return KeyOf<float>::enc(vL + (vH - vL) * f);
+}
+__device__ __forceinline__ unsigned long long interp_key(unsigned long long kL, unsigned long long kH, float f,
+                                                         unsigned long long) {
+    const double vL = KeyOf<double>::dec(kL), vH = KeyOf<double>::dec(kH);
+    return KeyOf<double>::enc(vL + (vH - vL) * (double)f);
+}
 
 template <typename real>
 struct ProfileArgs {
@@ -280,17 +312,6 @@ __device__ __forceinline__ T grp_max(T v, int G) {
     return v;
 }
 
-// The bits of a value in a key-typed shared-memory slot (AB and CB hold values;
-// the selector reads them back as values).
-template <typename real>
-__device__ __forceinline__ typename KeyOf<real>::type as_key(real v);
-template <>
-__device__ __forceinline__ uint32_t as_key<float>(float v) { return __float_as_uint(v); }
-template <>
-__device__ __forceinline__ unsigned long long as_key<double>(double v) {
-    return (unsigned long long)__double_as_longlong(v);
-}
-
 // Whole-warp reductions of working-precision values.
 __device__ __forceinline__ float warp_max(float v) {
     return KeyOf<float>::dec(__reduce_max_sync(0xffffffffu, KeyOf<float>::enc(v)));
@@ -300,6 +321,8 @@ __device__ __forceinline__ float warp_min(float v) {
 }
 __device__ __forceinline__ double warp_max(double v) { return grp_max(v, 32); }
 __device__ __forceinline__ double warp_min(double v) { return grp_min(v, 32); }
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) { return grp_max(v, 32); }
+__device__ __forceinline__ unsigned long long warp_min(unsigned long long v) { return grp_min(v, 32); }
 
 constexpr int SEL_CAP = 12;  // most AB values of a column held per lane in registers (R <= 384)
 constexpr int SEL_STEPS = 4;  // nearest-value steps before a position falls back to the bracketed search
@@ -341,7 +364,7 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
     const int lane = threadIdx.x & 31;
     const int nrw = (R + 31) >> 5;  // entries per lane and half (the last may be partly empty)
     const real NEG = RealLimits<real>::lowest();
-    const real POS = -NEG;
+    const real POS = RealLimits<real>::max();
     // this lane's rows lane + 32 j: offsets into AB and whether the row exists
     int roff[NJ];
     bool rin[NJ];
@@ -437,9 +460,8 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
             }
             key_t kp = kL + (key_t)((kH - kL) >> 1);
             if (it < 8) {
-                const real vL = K::dec(kL), vH = K::dec(kH);
-                const real f = ((real)(cL - kk) + (real)0.5) / (real)(cL - cH);
-                const key_t ki = K::enc(vL + (vH - vL) * f);
+                const float f = ((float)(cL - kk) + 0.5f) / (float)(cL - cH);
+                const key_t ki = interp_key(kL, kH, f, key_t{});
                 if (ki > kL && ki < kH) kp = ki;
             }
             const int c = count_ge(K::dec(kp));
@@ -542,6 +564,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                                              int tt, unsigned char* __restrict__ sm, int row_base = 0) {
     typedef KeyOf<real> K;
     typedef typename K::type key_t;
+    typedef typename CmpOf<real>::type cmp_t;  // what maxima and the selection compare
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31;
     // a CTA may have more threads than the tile's layout uses (a batched launch
@@ -563,16 +586,14 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const int Wb = Wp + R - 1;
     const int64_t i0 = (int64_t)s * m;
 
-    // row-window maxima (eq. 11), [row][position], and column maxima (eq. 10): as
-    // order-preserving keys for the grouped selector (R <= 288), as values for the
-    // warp selector
-    const bool keyed = false;  // AB and CB hold values (select_warp compares values)
+    // row-window maxima (eq. 11), [row][position], and column maxima (eq. 10): FP32
+    // tiles hold the values, FP64 tiles their order-preserving keys
     key_t* AB = (key_t*)(sm + G.off_AB);
     key_t* CB = (key_t*)(sm + G.off_CB);
-    real* PRE = (real*)(sm + G.off_PRE) + (size_t)g * 2 * NTc * V;  // this group's [parity][column]: maxima
-                                                                      // from the column's chunk start to it
-    real* LV = (real*)(sm + G.off_LV) + (size_t)g * 2 * 5 * NTc;     // [parity][k][NTc]: max of the 2^k chunk
-                                                                      // maxima from a chunk on, within its warp
+    cmp_t* PRE = (cmp_t*)(sm + G.off_PRE) + (size_t)g * 2 * NTc * V;  // this group's [parity][column]: maxima
+                                                                        // from the column's chunk start to it
+    cmp_t* LV = (cmp_t*)(sm + G.off_LV) + (size_t)g * 2 * 5 * NTc;     // [parity][k][NTc]: max of the 2^k chunk
+                                                                        // maxima from a chunk on, within its warp
     real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][warp][hi, lo]
     real* rst = (real*)(sm + G.off_rst);                              // [row][df, dg, a, 0]
     // segment data are staged from the 16-byte boundary at or below i0
@@ -853,14 +874,16 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // tiles of most series none can, and the rows skip the check)
     const bool kap_check = kxm * __uint_as_float(kap_rmax) > KAPPA_FLAG;
     const real NEG = RealLimits<real>::lowest();
-    real hi[V], lo[V], cmx[V];
+    const cmp_t NEGc = RealLimits<cmp_t>::lowest();
+    real hi[V], lo[V];
+    cmp_t cmx[V];
     const bool partial_cols = xb + V > Wb;  // only the last column thread of a tile
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const int x = xb + v;
         hi[v] = worker ? top[(size_t)g * NTc * V + x] : (real)0;
         lo[v] = 0;
-        cmx[v] = NEG;
+        cmx[v] = NEGc;
     }
     const int q0 = (R - 1) / V;       // chunk offset of the window end for i = 0
     const bool small_R = R - 1 < V;   // some windows end inside their own chunk
@@ -925,10 +948,10 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 const int r = r0 + sidx;
                 const bool active = sidx < nrows;  // uniform within the group
                 const int par = sidx & 1;
-                real* PREp = PRE + par * NTc * V;
-                real* LVp = LV + par * 5 * NTc;
+                cmp_t* PREp = PRE + par * NTc * V;
+                cmp_t* LVp = LV + par * 5 * NTc;
                 // logical column v of this thread lives in register (v - jj) mod V
-                real rho[V];
+                cmp_t rc[V];
                 if (active) {
                     real fr, gr, ar;
                     if constexpr (sizeof(real) == 4) {
@@ -1006,35 +1029,40 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                         XCH[(par * NWc + wc) * 2 + 0] = hi[Plast];
                         XCH[(par * NWc + wc) * 2 + 1] = lo[Plast];
                     }
-                    if (ar != (real)0) {
+                    {
+                        real rho[V];
+                        if (ar != (real)0) {
     #pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            const int P = (v - jj + V) % V;
-                            // FP32: hi is the rounded sum of the pair (lo is below half its ulp)
-                            rho[v] = ((sizeof(real) == 4 ? hi[P] : hi[P] + lo[P]) * ar) * ca[v];
+                            for (int v = 0; v < V; ++v) {
+                                const int P = (v - jj + V) % V;
+                                // FP32: hi is the rounded sum of the pair (lo is below half its ulp)
+                                rho[v] = ((sizeof(real) == 4 ? hi[P] : hi[P] + lo[P]) * ar) * ca[v];
+                            }
+                        } else {
+    #pragma unroll
+                            for (int v = 0; v < V; ++v) rho[v] = ca[v] == (real)0 ? (real)1 : (real)0;
                         }
-                    } else {
+                        const unsigned xd = (unsigned)(xdiag0 + r);  // i == j: correlation 1 by definition
+                        if (xd < (unsigned)V) {
     #pragma unroll
-                        for (int v = 0; v < V; ++v) rho[v] = ca[v] == (real)0 ? (real)1 : (real)0;
-                    }
-                    const unsigned xd = (unsigned)(xdiag0 + r);  // i == j: correlation 1 by definition
-                    if (xd < (unsigned)V) {
+                            for (int v = 0; v < V; ++v)
+                                if (v == (int)xd) rho[v] = (real)1;
+                        }
     #pragma unroll
-                        for (int v = 0; v < V; ++v)
-                            if (v == (int)xd) rho[v] = (real)1;
+                        for (int v = 0; v < V; ++v) rc[v] = to_cmp(rho[v]);
                     }
                     if (partial_cols) {
     #pragma unroll
                         for (int v = 0; v < V; ++v)
-                            if (xb + v >= Wb) rho[v] = NEG;
+                            if (xb + v >= Wb) rc[v] = NEGc;
                     }
     #pragma unroll
-                    for (int v = 0; v < V; ++v) cmx[v] = rmax(cmx[v], rho[v]);
+                    for (int v = 0; v < V; ++v) cmx[v] = rmax(cmx[v], rc[v]);
                     // prefix maxima within the chunk, stored by column
-                    real pre[V];
-                    pre[0] = rho[0];
+                    cmp_t pre[V];
+                    pre[0] = rc[0];
     #pragma unroll
-                    for (int v = 1; v < V; ++v) pre[v] = rmax(pre[v - 1], rho[v]);
+                    for (int v = 1; v < V; ++v) pre[v] = rmax(pre[v - 1], rc[v]);
                     if constexpr (sizeof(real) == 4 && V == 4) {
                         *reinterpret_cast<float4*>(PREp + xb) = make_float4(pre[0], pre[1], pre[2], pre[3]);
                     } else {
@@ -1042,7 +1070,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                         for (int v = 0; v < V; ++v) PREp[xb + v] = pre[v];
                     }
                     if (!small_R) {  // sparse table of the chunk maxima within each warp (level 0: the chunk maxima)
-                        real d = pre[V - 1];
+                        cmp_t d = pre[V - 1];
                         LVp[t] = d;
                         if (q0 >= 2) {
     #pragma unroll
@@ -1055,49 +1083,54 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 }
                 __syncthreads();
                 if (active && owns_positions) {
-                    real suf[V];
-                    suf[V - 1] = rho[V - 1];
+                    cmp_t suf[V];
+                    suf[V - 1] = rc[V - 1];
     #pragma unroll
-                    for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rho[v]);
+                    for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rc[v]);
                     if (!small_R) {
                         // whole chunks strictly inside the windows: t+1 .. t+q0-1 (mid), and
                         // chunk t+q0 as well once the window end moves into chunk t+q0+1
-                        real mid = NEG;
+                        cmp_t mid = NEGc;
                         if (use_mid) {
                             mid = rmax(rmax(LVp[so[0]], LVp[so[1]]), rmax(LVp[so[2]], LVp[so[3]]));
                             for (int w = wlo; w <= whi; ++w)
                                 mid = rmax(mid, rmax(LVp[4 * NTc + w * 32], LVp[4 * NTc + w * 32 + 16]));
                         }
-                        real far[V];
-                        if (far_vec) {
-                            const float4 f4 = *reinterpret_cast<const float4*>(PREp + far0);
-                            far[0] = f4.x;
-                            far[1] = f4.y;
-                            far[2] = f4.z;
-                            far[3] = f4.w;
-                        } else {
+                        cmp_t far[V];
+                        bool far_done = false;
+                        if constexpr (sizeof(cmp_t) == 4 && V == 4) {
+                            if (far_vec) {
+                                const float4 f4 = *reinterpret_cast<const float4*>(PREp + far0);
+                                far[0] = f4.x;
+                                far[1] = f4.y;
+                                far[2] = f4.z;
+                                far[3] = f4.w;
+                                far_done = true;
+                            }
+                        }
+                        if (!far_done) {
     #pragma unroll
                             for (int i = 0; i < V; ++i) far[i] = PREp[far0 + i];
                         }
-                        const real mid1 = rr > 0 ? rmax(mid, LVp[t + q0]) : mid;
+                        const cmp_t mid1 = rr > 0 ? rmax(mid, LVp[t + q0]) : mid;
     #pragma unroll
                         for (int i = 0; i < V; ++i) {
-                            const real ab = rmax(rmax(suf[i], i + rr >= V ? mid1 : mid), far[i]);
-                            if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
+                            const cmp_t ab = rmax(rmax(suf[i], i + rr >= V ? mid1 : mid), far[i]);
+                            if (full_positions || xb + i < Wp) ABr[i * LA] = cmp_bits(ab);
                         }
                     } else {
     #pragma unroll
                         for (int i = 0; i < V; ++i) {
-                            real ab;
+                            cmp_t ab;
                             if (i + R - 1 < V) {  // window inside this chunk
-                                ab = NEG;
+                                ab = NEGc;
     #pragma unroll
                                 for (int j = 0; j < V; ++j)
-                                    if (j >= i && j < i + R) ab = rmax(ab, rho[j]);
+                                    if (j >= i && j < i + R) ab = rmax(ab, rc[j]);
                             } else {
                                 ab = rmax(suf[i], PREp[far0 + i]);
                             }
-                            if (full_positions || xb + i < Wp) ABr[i * LA] = keyed ? K::enc(ab) : as_key<real>(ab);
+                            if (full_positions || xb + i < Wp) ABr[i * LA] = cmp_bits(ab);
                         }
                     }
                 }
@@ -1125,8 +1158,9 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         row_loop(std::false_type{});
     }
     // column maxima over all row groups
+    cmp_t* topc = (cmp_t*)top;  // the seeds are consumed: the groups' column maxima go here
     {
-        real* cmg = top + (size_t)g * NTc * V;
+        cmp_t* cmg = topc + (size_t)g * NTc * V;
         if (worker) {
 #pragma unroll
             for (int v = 0; v < V; ++v) cmg[xb + v] = cmx[v];
@@ -1135,31 +1169,31 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     __syncthreads();
     if (CS == 1) {
         for (int x = tid; x < Wb; x += BD) {
-            real mx = top[x];
-            for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
-            CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
+            cmp_t mx = topc[x];
+            for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, topc[(size_t)gg * NTc * V + x]);
+            CB[x] = cmp_bits(mx);
         }
     } else {
         // this CTA's column maxima into slot crank of every CTA's CBp; after the
         // cluster barrier (which also completes every AB write into this CTA),
         // the maximum over the slots, in slot order
-        real* CBp = (real*)(sm + G.off_CBp);
+        cmp_t* CBp = (cmp_t*)(sm + G.off_CBp);
         const int slot = Wb + 32;
         for (int x = tid; x < Wb; x += BD) {
-            real mx = top[x];
-            for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, top[(size_t)gg * NTc * V + x]);
+            cmp_t mx = topc[x];
+            for (int gg = 1; gg < NG; ++gg) mx = rmax(mx, topc[(size_t)gg * NTc * V + x]);
             CBp[crank * slot + x] = mx;
         }
         for (int c = 0; c < CS; ++c) {
             if (c == crank) continue;
-            real* CBq = cooperative_groups::this_cluster().map_shared_rank(CBp, c) + crank * slot;
+            cmp_t* CBq = cooperative_groups::this_cluster().map_shared_rank(CBp, c) + crank * slot;
             for (int x = tid; x < Wb; x += BD) CBq[x] = CBp[crank * slot + x];
         }
         cooperative_groups::this_cluster().sync();
         for (int x = tid; x < Wb; x += BD) {
-            real mx = CBp[x];
+            cmp_t mx = CBp[x];
             for (int c = 1; c < CS; ++c) mx = rmax(mx, CBp[c * slot + x]);
-            CB[x] = keyed ? K::enc(mx) : as_key<real>(mx);
+            CB[x] = cmp_bits(mx);
         }
     }
     __syncthreads();
@@ -1172,7 +1206,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     real* Drow = A.D + (int64_t)(s - row_base) * A.P + p0;  // row s - row_base of the output
     const bool streaming = A.part != nullptr;
     double sacc = 0.0;
-    auto emit = [&](int p, real rs) {
+    auto emit = [&](int p, cmp_t rc_) {
+        const real rs = cmp_value(rc_);
         real u = (real)1 - rs;
         u = u > (real)0 ? u : (real)0;
         const real d = sqrt(two_ell * u);
@@ -1194,13 +1229,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         const int PW = (Wn + nwarps - 1) / nwarps;
         const int pb = (tid >> 5) * PW;
         const int npos = pb >= Wn ? 0 : (pb + PW <= Wn ? PW : Wn - pb);
-        const real* ABv = (const real*)AB;
-        const real* CBv = (const real*)CB;
-        if (R <= 64) select_warp<2, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 96) select_warp<3, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 160) select_warp<5, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 288) select_warp<9, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else select_warp<SEL_CAP, V, real>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        const cmp_t* ABv = (const cmp_t*)AB;
+        const cmp_t* CBv = (const cmp_t*)CB;
+        if (R <= 64) select_warp<2, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 96) select_warp<3, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 160) select_warp<5, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 288) select_warp<9, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else select_warp<SEL_CAP, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
     }
     const double wmax = warp_max(tmax);
     if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(wmax));
