@@ -51,14 +51,49 @@ SM_MAX_MHZ = 2032.0
 # recurrence (4 FLOP), 2 multiplications by the inverse norms (2 FLOP), and the
 # exact seed of every diagonal (ell FMA per R cells, about 2 FLOP at ell = m/2)
 FLOP_PER_ED_CELL = 8.0
-# dram__bytes_read.sum + dram__bytes_write.sum of the tile launches of one sweep
-# step (one-CTA tiles of m = 64 .. 256: 43 MB + 2.09 GB; two-CTA cluster tiles of
-# m = 288 .. 512: 39 MB + 0.78 GB), from an ncu capture of this kernel version
-SWEEP_TILE_DRAM_BYTES = 2.95e9
-# smsp__issue_active.avg.pct_of_peak_sustained_active of the tile kernel at two
-# lengths of the sweep (ncu --set full on this kernel version): the share of the
-# SMs' instruction-issue slots the kernel fills, beside the FLOP fraction
-TILE_ISSUE_ACTIVE = {"m128": 0.550, "m512": 0.519}
+# DRAM traffic of one sweep step's tile launches: read from profiles/tile_traffic.json,
+# an ncu capture of the kernel sources whose SHA-256 it records; reported only while
+# those sources are unchanged (null otherwise)
+TRAFFIC_FILE = os.path.join(HERE, "profiles", "tile_traffic.json")
+TILE_SOURCES = [os.path.join(HERE, "paper_2401_13680_b300", "csrc", f) for f in ("tile.cuh", "batch.cuh", "keys.cuh")]
+
+
+def tile_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TILE_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """(bytes per sweep step, provenance) from the recorded capture, or (None, why)."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None, "no recorded capture"
+    if rec.get("kernel_sources_sha256") != tile_sources_sha():
+        return None, "the recorded capture predates the current kernel sources"
+    return float(rec["dram_bytes_per_sweep_step"]), rec.get("capture", "")
+
+
+def d_floor(ell):
+    return 0.1 * np.sqrt(2.0 * ell)
+
+
+def profile_error_ratio(d, d_ref, ell):
+    """Per-cell error under the tolerance rule (relative above d_floor = 0.1 sqrt(2 ell),
+    |d^2 - d_ref^2| / (2 d_floor^2) below it); compare with 1e-4 for FP32."""
+    d = np.asarray(d, dtype=np.float64)
+    d_ref = np.asarray(d_ref, dtype=np.float64)
+    fl = d_floor(ell)
+    above = d_ref >= fl
+    r = np.empty_like(d_ref)
+    r[above] = np.abs(d[above] - d_ref[above]) / d_ref[above]
+    r[~above] = np.abs(d[~above] ** 2 - d_ref[~above] ** 2) / (2.0 * fl ** 2)
+    return r
 
 
 def workload(m_list=None):
@@ -333,6 +368,125 @@ def run_multivariate(pastila, device, ms, K, d=3, seeds=(1, 5, 9)):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def sample_cells(S, P, W, count, rng):
+    """Seeded (segment, position) cells of one length: random ones plus the
+    first and last segment, the first and last position and both sides of
+    every tile boundary (multiples of the tile width W) the sample reaches."""
+    segs = list(rng.integers(0, S, count))
+    pos = list(rng.integers(0, P, count))
+    edges = [0, P - 1] + [q for b in range(W, P, W) for q in (b - 1, b)][:count]
+    for i, q in enumerate(edges):
+        segs.append([0, S - 1][i % 2] if i < 4 else int(rng.integers(0, S)))
+        pos.append(q)
+    return np.array(segs, dtype=np.int32), np.array(pos, dtype=np.int64)
+
+
+def fp32_errors(h, T, ms, res32, res64, dev, count=24, seed=11):
+    """Errors of the FP32 results: per length, sampled profile cells (the
+    single-length launch with the sweep's tile layout, which computes every cell
+    exactly as the batched launch does) against the oracle's pair definition,
+    under the tolerance rule; the criterion and m_best against the FP64 GPU path
+    (select_length on an FP64 handle), and m_best's snippets."""
+    import torch
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    n = T.shape[0]
+    per_m, worst = [], 0.0
+    Dbuf = torch.empty(max((n // m) * (n - m + 1) for m in ms), dtype=torch.float32, device=dev)
+    dmax = torch.zeros(1, dtype=torch.float64, device=dev)
+    for m in ms:
+        ell, k = m // 2, (m + 9) // 10
+        S, P = n // m, n - m + 1
+        W = h.tile_layout(m)["W"]
+        segs, pos = sample_cells(S, P, W, count, rng)
+        h.profiles_device(m, Dbuf.data_ptr(), dmax.data_ptr())
+        torch.cuda.synchronize()  # the handle's stream is not torch's
+        idx = torch.from_numpy(segs.astype(np.int64) * P + pos).to(dev)
+        d32 = Dbuf[idx].double().cpu().numpy()
+        dref = oracle.profile_cells(T, m, ell, k, segs, pos)
+        r = profile_error_ratio(d32, dref, ell)
+        drho = np.abs(d32 ** 2 - dref ** 2) / (2.0 * ell)
+        worst = max(worst, float(r.max()) / 1e-4)
+        per_m.append({"m": m, "cells": int(r.size), "max_err_over_tol": float(r.max()) / 1e-4,
+                      "max_abs_drho": float(drho.max())})
+    out = {"tol": 1e-4, "rule": "relative above d_floor = 0.1 sqrt(2 ell), |d^2 - d_ref^2| / (2 d_floor^2) below",
+           "profile_cells": {"reference": "oracle pair definition (FP64, CPU)",
+                             "sample": f"{count} seeded cells and up to {count} tile-boundary cells per length",
+                             "max_err_over_tol": worst, "per_m": per_m}}
+    if res64 is not None:
+        c32, c64 = np.asarray(res32[1], dtype=np.float64), np.asarray(res64[1], dtype=np.float64)
+        rel = np.abs(c32 - c64) / np.maximum(np.abs(c64), 1e-300)
+        out["criterion"] = {"reference": "FP64 GPU path", "max_rel_diff": float(rel.max()),
+                            "per_m": [float(x) for x in rel]}
+        out["m_best"] = {"fp32": int(res32[0]), "fp64": int(res64[0]), "equal": int(res32[0]) == int(res64[0])}
+        s32 = [int(r[0]) for r in res32[2]]
+        s64 = [int(r[0]) for r in res64[2]]
+        out["m_best_snippets"] = {"fp32": s32, "fp64": s64, "equal": s32 == s64}
+    return out
+
+
+def run_drift(pastila, device, dev, m=256, K=6, nseg=32, block=512, seed=12):
+    """The million-point drift series (8 planted regimes of 50k-250k points plus
+    a random walk, m = 256, ell = 128, K = 6): FP32 profiles + greedy snippets
+    through the C ABI, timed; the FP64 GPU path timed on the series' first
+    125,000 points (1/64 of the ED cells; the full-size FP64 run takes about a
+    minute), the FP32 path on the same prefix beside it; FP32 profile cells of
+    nseg seeded segments x block consecutive positions against the oracle."""
+    import torch
+    import oracle
+    s = synth.large_drift()
+    T = s.T
+    n = T.shape[0]
+    ell, k = m // 2, (m + 9) // 10
+    S, P, R = n // m, n - m + 1, m - ell + 1
+    out = {"workload": "drift series, n=1000000, 8 planted regimes + random walk sd 0.01, seed 2; m=256, ell=128, "
+                       "k=26, K=6"}
+    with pastila.Series(T, device=device, precision=pastila.FP32) as h:
+        h.snippets(m, K)  # warm-up: statistics, allocations
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs, _, _ = h.snippets(m, K)
+        torch.cuda.synchronize()
+        t32 = time.perf_counter() - t0
+        out["fp32"] = {"seconds": t32, "profile_cells_per_s": S * P / t32,
+                       "ed_cells_per_s": S * R * (n - ell + 1) / t32, "snippets": [int(r[0]) for r in recs]}
+        rng = np.random.default_rng(seed)
+        segs = np.sort(rng.choice(S, nseg, replace=False)).astype(np.int32)
+        p_lo = int(rng.integers(0, P - block))
+        Dbuf = torch.empty(S * P, dtype=torch.float32, device=dev)
+        dmax = torch.zeros(1, dtype=torch.float64, device=dev)
+        h.profiles_device(m, Dbuf.data_ptr(), dmax.data_ptr())
+        torch.cuda.synchronize()  # the handle's stream is not torch's
+        rows = Dbuf.view(S, P)[torch.from_numpy(segs.astype(np.int64)).to(dev), p_lo:p_lo + block]
+        d32 = rows.double().cpu().numpy()
+        del Dbuf
+    oracle.build()
+    t0 = time.perf_counter()
+    dref = oracle.profiles_range(T, m, ell, k, segs, p_lo, p_lo + block)
+    out["oracle_seconds"] = time.perf_counter() - t0
+    r = profile_error_ratio(d32, dref, ell)
+    out["errors"] = {"cells": int(r.size), "sample": f"{nseg} seeded segments x {block} consecutive positions",
+                     "max_err_over_tol": float(r.max()) / 1e-4,
+                     "max_abs_drho": float((np.abs(d32 ** 2 - dref ** 2) / (2.0 * ell)).max())}
+    # FP32 and FP64 on the first 125,000 points
+    Tp = np.ascontiguousarray(T[:125_000])
+    np_ = Tp.shape[0]
+    ed_p = (np_ // m) * R * (np_ - ell + 1)
+    pref = {"n": np_, "ed_cells": ed_p}
+    for name, prec in (("fp32", pastila.FP32), ("fp64", pastila.FP64)):
+        with pastila.Series(Tp, device=device, precision=prec) as hp:
+            hp.profiles(m, want_D=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hp.profiles(m, want_D=False)
+            torch.cuda.synchronize()
+            pref[name + "_seconds"] = time.perf_counter() - t0
+    pref["fp32_over_fp64"] = pref["fp64_seconds"] / pref["fp32_seconds"]
+    out["prefix_125k"] = pref
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2401_13680_b300 import pastila
@@ -431,11 +585,12 @@ def run_ours(args):
     achieved = FLOP_PER_ED_CELL * ed_cells * args.steps / tile_s / 1e12
     peak = SM_COUNT_B300 * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     fma32, fma64 = pastila.probe_fma(local)  # measured FMA rates, outside every timed region
-    # DRAM bytes of one sweep's tile launches, from an ncu capture of the current
-    # kernel (read + write; the algorithmic bytes are the profile set D, 2.97 GB)
-    traffic = SWEEP_TILE_DRAM_BYTES if ms == synth.sweep_lengths() else None
+    # DRAM bytes of one sweep's tile launches (read + write; the algorithmic bytes are
+    # the profile set D, 2.97 GB), from a capture of the current kernel sources only
+    traffic, traffic_src = measured_traffic() if ms == synth.sweep_lengths() else (None, "not the full sweep")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per sweep step's tile launches",
+                "traffic_source": traffic_src,
                 "kernel": "batched_tiles_kernel<float,4> (every length of the sweep; one launch per layout class, "
                           "timed together)",
                 "peak_basis": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (max SM clock), derived",
@@ -443,8 +598,6 @@ def run_ours(args):
                 "ed_cells_per_s": ed_cells * args.steps / tile_s,
                 "tile_share_of_step": tile_s / tot_s if world == 1 else None,
                 "halo_factor": tile_cells_halo / (ed_cells * args.steps),
-                "issue_active_ncu": dict(TILE_ISSUE_ACTIVE, source="profiles/tile_kernel_six_regime_m128.md, "
-                                                                   "profiles/tile_kernel_six_regime_m512_cluster.md"),
                 "fma_measured_tflops": {"fp32": fma32, "fp64": fma64,
                                         "basis": "pastila_probe_fma: 8 independent FMA chains per thread, "
                                                  "8 CTAs of 256 threads per SM, events"},
@@ -471,6 +624,16 @@ def run_ours(args):
                 "speedup_fp32_over_fp64": (prof_cells / (tot_s / args.steps)) / (prof_cells / t64)}
         h64.close()
 
+    # ---- the FP32 path's error, stated per result: profile cells against the oracle,
+    # the criterion, m_best and m_best's snippets against the FP64 GPU path
+    errors = None
+    if not args.no_errors and world == 1:
+        errors = fp32_errors(h, T, ms, result, r64 if fp64 else None, dev)
+
+    drift = None
+    if not args.no_drift and world == 1:
+        drift = run_drift(pastila, local, dev)
+
     serving = None
     if args.serve_jobs > 0 and world == 1:
         serving = run_serving(args, pastila, local, ed_cells * args.steps / tot_s,
@@ -495,7 +658,8 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps, "roofline": roofline,
             "ed_cells_per_s": world * ed_cells * args.steps / tot_s,
             "m_best": result[0], "criterion": [float(x) for x in result[1]],
-            "step_ms": step_ms, "fp64_path": fp64, "serving": serving, "multivariate": multi, "autotune": tune}
+            "step_ms": step_ms, "fp64_path": fp64, "errors": errors, "drift_series": drift, "serving": serving,
+            "multivariate": multi, "autotune": tune}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     h.close()
@@ -526,6 +690,8 @@ def main():
     ap.add_argument("--serve-plain", action="store_true",
                     help="also run the serving stream one job at a time on FP32 and FP64 handles (slow)")
     ap.add_argument("--no-multi", action="store_true", help="skip the multivariate leg")
+    ap.add_argument("--no-errors", action="store_true", help="skip the FP32 error block")
+    ap.add_argument("--no-drift", action="store_true", help="skip the million-point drift-series leg")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="offered load of the serving leg, as a fraction of the measured ED-cell rate")
     args = ap.parse_args()

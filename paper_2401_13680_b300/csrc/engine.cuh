@@ -606,6 +606,7 @@ struct Chunk {
 // Plans and enqueues one wave; returns false when there is nothing to do.
 template <typename real, int V>
 pastila_status form_wave_t(pastila_engine* e, bool* did) {
+    NvtxRange range("pastila: engine wave");
     *did = false;
     const int64_t wave_id = e->next_wave;
     std::vector<EJob*> admitted;

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/pastila.h"
+#include <nvtx3/nvToolsExt.h>  // header-only: ranges cost a branch unless a profiler is attached
 #include "batch.cuh"
 #include "keys.cuh"
 #include "probe.cuh"
@@ -27,6 +28,15 @@
 using namespace pastila;
 
 namespace {
+
+// A named NVTX range over a scope (host side: marks when each phase is enqueued;
+// profilers show it beside the kernels it launched).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 thread_local std::string g_err;
 
@@ -1398,7 +1408,10 @@ pastila_status select_length_batched_t(pastila_series* h, const int32_t* m_list,
         gr.gen = h->alloc_gen;
     }
     const uint64_t l_before = h->launches;
+    static const char* const phase_name[3] = {"pastila: window statistics", "pastila: profile tiles",
+                                              "pastila: greedy snippets and length criterion"};
     for (int ph = 0; ph < 3; ++ph) {
+        NvtxRange range(phase_name[ph]);
         if (ph == 1 && h->timing) CK(cudaEventRecord(gr.ev0, h->stream));
         if (gr.exec[ph]) {
             CK(cudaGraphLaunch(gr.exec[ph], h->stream));

@@ -90,3 +90,46 @@ def test_multivariate_leg_compares_every_coordinate():
     # a criterion value differs
     other[2] = (res[2][0], res[2][1] + 1e-12, res[2][2])
     assert not bench.run_multivariate(_stub(res, other), 0, ms, 2)["results_identical"]
+
+
+def test_error_ratio_follows_the_tolerance_rule():
+    """Above d_floor = 0.1 sqrt(2 ell) the ratio is relative; below, |d^2 -
+    d_ref^2| / (2 d_floor^2); the two agree at the floor (continuity)."""
+    ell = 50
+    fl = bench.d_floor(ell)
+    assert fl == np.sqrt(100.0) * 0.1
+    r = bench.profile_error_ratio([2.2, 0.0], [2.0, 0.5], ell)
+    assert r[0] == np.abs(2.2 - 2.0) / 2.0
+    assert r[1] == 0.25 / (2.0 * fl ** 2)
+    eps = 1e-6
+    above = bench.profile_error_ratio([fl * (1 + eps)], [fl], ell)[0]
+    below = bench.profile_error_ratio([fl * (1 - 1e-12) * (1 + eps)], [fl * (1 - 1e-12)], ell)[0]
+    assert abs(above - below) < 1e-9
+
+
+def test_sample_cells_cover_tile_boundaries():
+    """Every sampled cell is in range; the sample holds the first and last
+    position and both sides of the first tile boundaries."""
+    rng = np.random.default_rng(0)
+    S, P, W = 300, 99_000, 480
+    segs, pos = bench.sample_cells(S, P, W, 24, rng)
+    assert segs.shape == pos.shape
+    assert segs.min() >= 0 and segs.max() < S and pos.min() >= 0 and pos.max() < P
+    got = set(pos.tolist())
+    assert {0, P - 1, W - 1, W, 2 * W - 1, 2 * W} <= got
+    assert 0 in segs.tolist() and S - 1 in segs.tolist()
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(tmp_path, monkeypatch):
+    """The recorded DRAM traffic counts only while the kernel sources hash to the
+    value the capture recorded."""
+    import json
+    f = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.measured_traffic()[0] is None  # no file
+    f.write_text(json.dumps({"kernel_sources_sha256": bench.tile_sources_sha(),
+                             "dram_bytes_per_sweep_step": 3.0e9, "capture": "ncu ..."}))
+    assert bench.measured_traffic() == (3.0e9, "ncu ...")
+    f.write_text(json.dumps({"kernel_sources_sha256": "0" * 64, "dram_bytes_per_sweep_step": 3.0e9}))
+    v, why = bench.measured_traffic()
+    assert v is None and "predates" in why
