@@ -138,6 +138,24 @@ pastila_status pastila_profiles(pastila_series* h, int32_t m, pastila_mparams mp
 pastila_status pastila_profiles_device(pastila_series* h, int32_t m, pastila_mparams mp,
                                        void* D_dev, double* D_max_dev);
 
+/* The profile sets of several lengths at once (eqs. 9-15 for each m of a
+ * Section 4.2 length sweep), computed by the launch that pastila_select_length
+ * makes for its sweep: on FP32 handles one batched tile launch per tile shape
+ * covers every length; FP64 handles run the lengths one after another.
+ * m_list: n_m lengths, each resolved with `rule` as pastila_select_length does
+ *         (ell = 0: m/2; k = 0: ceil(m/10)).
+ * D_dev:  n_m device pointers (a host array of them); D_dev[i] receives the
+ *         S_i x P_i profile set of m_list[i], row-major, float (FP32 handles)
+ *         or double (FP64 handles), S_i = floor(n / m_i), P_i = n - m_i + 1.
+ * D_max_dev: NULL or n_m device doubles, the largest value of each set.
+ * Every value equals the one pastila_profiles_device writes for that length
+ * with the same tile layout, bit for bit.  Enqueued on the handle's stream,
+ * like pastila_profiles_device (call pastila_stage_status after
+ * synchronising).  Errors: EINVAL (empty list, a NULL buffer, m, ell or k out
+ * of range), ENOMEM, ECUDA. */
+pastila_status pastila_profiles_batch_device(pastila_series* h, const int32_t* m_list, int32_t n_m,
+                                             pastila_mparams rule, void* const* D_dev, double* D_max_dev);
+
 /* Status of the handle's tile work enqueued so far, for callers of the
  * enqueue-only entry points: call it after the handle's stream has been
  * synchronised.  Returns PASTILA_ETIMEOUT (and clears the flag) if a tile's

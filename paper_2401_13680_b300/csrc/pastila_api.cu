@@ -1352,6 +1352,42 @@ pastila_status sweep_enqueue_t(pastila_series* h, const std::vector<MParams>& qs
     return PASTILA_OK;
 }
 
+// The profile sets of several lengths from the sweep's batched tile launch (FP32
+// handles): the sweep's items with each D pointing at the caller's buffer, then
+// its statistics phase and its tile phase, and each length's D maximum decoded.
+template <typename real, int V>
+pastila_status profiles_batch_t(pastila_series* h, const std::vector<MParams>& qs, void* const* D_dev,
+                                double* D_max_dev) {
+    SweepBufs sb;
+    std::vector<BatchItem<real>> items, tiles;
+    int64_t maxS, maxP;
+    TRY(sweep_prepare_t<real, V>(h, qs, 2, &sb, &items, &tiles, &maxS, &maxP));
+    const int n = (int)qs.size();
+    for (BatchItem<real>& t : tiles)
+        for (int i = 0; i < n; ++i)
+            if (t.A.D == items[i].A.D) t.A.D = (real*)D_dev[i];
+    for (int i = 0; i < n; ++i) items[i].A.D = (real*)D_dev[i];
+    CK(cudaMemcpyAsync(sb.items, items.data(), sizeof(BatchItem<real>) * items.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(sb.tiles, tiles.data(), sizeof(BatchItem<real>) * tiles.size(), cudaMemcpyHostToDevice,
+                       h->stream));
+    {
+        NvtxRange range("pastila: window statistics");
+        TRY(sweep_enqueue_t<real, V>(h, qs, 2, sb, items, maxS, maxP, 0));
+    }
+    {
+        NvtxRange range("pastila: profile tiles");
+        TRY(sweep_enqueue_t<real, V>(h, qs, 2, sb, items, maxS, maxP, 1));
+    }
+    if (D_max_dev) {
+        for (int i = 0; i < n; ++i)
+            dec_dmax_kernel<<<1, 1, 0, h->stream>>>(items[i].A.dmax_key, D_max_dev + i);
+        CK(cudaGetLastError());
+        h->launches += (uint64_t)n;
+    }
+    return PASTILA_OK;
+}
+
 // select_length on FP32 handles: batched, captured into a CUDA graph on the
 // second call with the same configuration and replayed from then on.
 template <typename real, int V>
@@ -1739,6 +1775,32 @@ pastila_status pastila_profiles_device(pastila_series* h, int32_t m, pastila_mpa
         dec_dmax_kernel<<<1, 1, 0, h->stream>>>((const unsigned long long*)dk, D_max_dev);
         CK(cudaGetLastError());
         h->launches += 1;
+    }
+    return PASTILA_OK;
+}
+
+pastila_status pastila_profiles_batch_device(pastila_series* h, const int32_t* m_list, int32_t n_m,
+                                             pastila_mparams rule, void* const* D_dev, double* D_max_dev) {
+    g_err.clear();
+    if (!h) return fail(PASTILA_EINVAL, "handle is NULL");
+    if (!m_list || n_m < 1) return fail(PASTILA_EINVAL, "m_list is empty");
+    if (!D_dev) return fail(PASTILA_EINVAL, "D_dev is NULL");
+    for (int i = 0; i < n_m; ++i)
+        if (!D_dev[i]) return fail(PASTILA_EINVAL, "D_dev[%d] is NULL", i);
+    TRY(set_device(h));
+    std::vector<MParams> qs(n_m);
+    for (int i = 0; i < n_m; ++i) TRY(resolve(h, m_list[i], rule, &qs[i]));
+    if (h->prec == PASTILA_FP32) return profiles_batch_t<float, V_F32>(h, qs, D_dev, D_max_dev);
+    // FP64: the plain path, one length after the other
+    void* dk;
+    TRY(scratch(h, "dmax", 8, &dk));
+    for (int i = 0; i < n_m; ++i) {
+        TRY(launch_profiles(h, qs[i], D_dev[i], (unsigned long long*)dk));
+        if (D_max_dev) {
+            dec_dmax_kernel<<<1, 1, 0, h->stream>>>((const unsigned long long*)dk, D_max_dev + i);
+            CK(cudaGetLastError());
+            h->launches += 1;
+        }
     }
     return PASTILA_OK;
 }

@@ -98,6 +98,8 @@ def load(path: str | None = None):
         lib.pastila_profiles.restype = S
         lib.pastila_profiles_device.argtypes = [_vp, ctypes.c_int32, MParams, _vp, _vp]
         lib.pastila_profiles_device.restype = S
+        lib.pastila_profiles_batch_device.argtypes = [_vp, _vp, ctypes.c_int32, MParams, _vp, _vp]
+        lib.pastila_profiles_batch_device.restype = S
         lib.pastila_stage_status.argtypes = [_vp]
         lib.pastila_stage_status.restype = S
         lib.pastila_set_fp64_ties.argtypes = [_vp, ctypes.c_int]
@@ -271,6 +273,14 @@ class Series:
         """Enqueue D into a device buffer (``pastila_profiles_device``)."""
         _check(load().pastila_profiles_device(self._h, m, MParams(ell, k), _vp(D_ptr),
                                               _vp(dmax_ptr) if dmax_ptr else None))
+
+    def profiles_batch_device(self, ms, D_ptrs, dmax_ptr: int | None = None, ell: int = 0, k: int = 0):
+        """``pastila_profiles_batch_device``: the profile sets of every m in ms from
+        the sweep's batched launch, into the device buffers D_ptrs (one per m)."""
+        ms = np.ascontiguousarray(ms, dtype=np.int32)
+        ptrs = (ctypes.c_void_p * len(D_ptrs))(*D_ptrs)
+        _check(load().pastila_profiles_batch_device(self._h, _ptr(ms), ms.shape[0], MParams(ell, k), ptrs,
+                                                    dmax_ptr))
 
     def set_fp64_ties(self, on: bool):
         """``pastila_set_fp64_ties``: decide near-tied greedy steps of an FP32

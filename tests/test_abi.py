@@ -37,6 +37,7 @@ def test_host_side_argument_validation():
     # a NULL handle is an argument error on every entry point
     assert lib.pastila_profiles(None, 64, pastila.MParams(0, 0), None, None) == pastila.EINVAL
     assert lib.pastila_stage_status(None) == pastila.EINVAL
+    assert lib.pastila_profiles_batch_device(None, None, 0, pastila.MParams(0, 0), None, None) == pastila.EINVAL
     assert lib.pastila_snippets(None, 64, pastila.MParams(0, 0), 2, None, None, None) == pastila.EINVAL
     assert lib.pastila_select_length(None, None, 0, pastila.MParams(0, 0), 2, None, None, None) \
         == pastila.EINVAL

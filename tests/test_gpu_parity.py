@@ -286,6 +286,58 @@ def test_sweep_full_size_sampled_cells(lib):
             assert dmax == pytest.approx(float(D.max()), rel=1e-7)
 
 
+def test_batched_sweep_launch_full_size(lib):
+    """The launch the benchmark times, at full size: the six-regime sweep
+    (n = 100,000, all 15 lengths, tile layouts tuned as the benchmark tunes them)
+    through pastila_profiles_batch_device, which runs select_length's batched
+    tile launch into caller buffers.  Every length's profile set equals the
+    single-length launch's bit for bit, and on every length seeded cells plus
+    both sides of tile boundaries, the first and last position and the first and
+    last segment meet the FP32 rule against the oracle (and |d rho| <= 2e-6)."""
+    import torch
+    from paper_2401_13680_b300 import pastila
+    s = synth.six_regime_sweep()
+    T = s.T
+    n = T.shape[0]
+    ms = synth.sweep_lengths()
+    rng = np.random.default_rng(2024)
+    dev = torch.device("cuda", 0)
+    pastila.tune_clear()
+    try:
+        with pastila.Series(T, precision=0) as h:
+            h.tune(ms, max_candidates=4)
+            bufs = [torch.empty((n // m) * (n - m + 1), dtype=torch.float32, device=dev) for m in ms]
+            dmax = torch.zeros(len(ms), dtype=torch.float64, device=dev)
+            h.profiles_batch_device(ms, [b.data_ptr() for b in bufs], dmax.data_ptr())
+            torch.cuda.synchronize()
+            h.stage_status()
+            one = torch.empty_like(bufs[0])
+            one_max = torch.zeros(1, dtype=torch.float64, device=dev)
+            for i, m in enumerate(ms):
+                ell, k = m // 2, (m + 9) // 10
+                S, P = n // m, n - m + 1
+                h.profiles_device(m, one.data_ptr(), one_max.data_ptr())
+                torch.cuda.synchronize()
+                assert torch.equal(one[:S * P], bufs[i]), m
+                assert one_max.item() == dmax[i].item()
+                W = h.tile_layout(m)["W"]
+                segs = list(rng.integers(0, S, 24)) + [0, S - 1, 0, S - 1]
+                pos = list(rng.integers(0, P, 24)) + [0, P - 1, P - 1, 0]
+                for b in range(W, min(P, 9 * W), W):
+                    segs += [int(rng.integers(0, S))] * 2
+                    pos += [b - 1, b]
+                segs = np.array(segs, dtype=np.int32)
+                pos = np.array(pos, dtype=np.int64)
+                idx = torch.from_numpy(segs.astype(np.int64) * P + pos).to(dev)
+                got = bufs[i][idx].double().cpu().numpy()
+                ref = oracle.profile_cells(T, m, ell, k, segs, pos)
+                assert_profiles_close(got, ref, ell, TOL[0])
+                assert_rho_close(got, ref, ell)
+                assert dmax[i].item() == pytest.approx(float(bufs[i][:S * P].max()), rel=1e-7)
+    finally:
+        pastila.tune_clear()
+
+
 def test_select_length_batched_graph_replay(lib):
     """FP32 select_length runs every length in batched launches, is captured in a
     CUDA graph on its second call and replayed after: three calls agree bit for
