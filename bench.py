@@ -279,13 +279,30 @@ def run_serving(args, pastila, device, ed_rate, fp64_ed_rate, age_weight=0.0, po
     assert all(i["state"] == pastila.JOB_DONE for i in infos), "a serving job did not finish"
     lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
     span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    # latency by job size: thirds of the stream by ED cells
+    order = np.argsort(ed, kind="stable")
+    by_size = []
+    for part in np.array_split(order, 3):
+        if part.size == 0:
+            continue
+        by_size.append({"jobs": int(part.size), "ed_cells_min": float(ed[part].min()),
+                        "ed_cells_max": float(ed[part].max()),
+                        "latency_p50_s": float(np.percentile(lat[part], 50)),
+                        "latency_p99_s": float(np.percentile(lat[part], 99))})
+    # the documented stream offers 20 jobs/s; at the measured ED-cell rate the engine
+    # can take ed_rate / mean job size jobs/s, so the leg runs the same jobs with the
+    # arrival clock scaled to the offered load asked
+    capacity = ed_rate / ed.mean()
     out = {"jobs": len(jobs), "arrival_rate_jobs_per_s": rate, "offered_load": args.serve_load,
            "age_weight_s": age_weight, "policy": policy,
            "workload": "serving stream seed 3: n log-uniform [1e4, 5e5], 3-8 planted regimes + N(0, 0.05^2), "
                        "3-10 lengths from {64, 96, ..., 768}, ell = m/2, K in [3, 6]; Poisson arrivals, "
                        "time-scaled from 20 jobs/s to the offered load",
+           "documented_rate_jobs_per_s": 20.0, "capacity_jobs_per_s": capacity,
+           "documented_rate_over_capacity": 20.0 / capacity,
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
            "latency_mean_s": float(lat.mean()), "latency_max_s": float(lat.max()),
+           "latency_by_job_size": by_size,
            "makespan_s": span, "profile_cells_per_s": float(prof.sum() / span),
            "ed_cells_per_s": float(ed.sum() / span), "waves": st["waves"], "launches": st["launches"],
            "device_busy_frac": st["busy_ms"] / 1e3 / span, "mem_peak_gb": st["mem_peak"] / 1e9,
@@ -304,7 +321,7 @@ def run_serving_plain(args, pastila, device, rate, precision):
     """The serving stream run one job at a time, in arrival order, on handles of
     the given precision (select_length per job, no engine): arrival -> results
     latency measured against the same arrival clock as the engine's run."""
-    jobs = synth.serving_jobs(n_jobs=args.serve_jobs, rate=20.0, seed=3)
+    jobs = synth.serving_jobs(n_jobs=args.serve_jobs, rate=20.0, seed=3)[:args.serve_plain_jobs]
     series = [j.series() for j in jobs]
     arrivals = [j.arrival * 20.0 / rate for j in jobs]
     lat = []
@@ -320,7 +337,8 @@ def run_serving_plain(args, pastila, device, rate, precision):
     return {"precision": "f64" if precision == pastila.FP64 else "f32", "jobs": len(jobs),
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
             "latency_mean_s": float(lat.mean()), "makespan_s": float(time.perf_counter() - t0),
-            "basis": "measured: one job at a time in arrival order, select_length on a handle per job"}
+            "basis": f"measured: the first {len(jobs)} jobs of the serving leg's stream at its arrival times, "
+                     "one job at a time in arrival order, select_length on a handle per job"}
 
 
 def run_multivariate(pastila, device, ms, K, d=3, seeds=(1, 5, 9)):
@@ -487,6 +505,35 @@ def run_drift(pastila, device, dev, m=256, K=6, nseg=32, block=512, seed=12):
     return out
 
 
+def run_stress(pastila, device, n, m=128, K=8):
+    """The ECG-like stress series (PQRST beats, RR intervals N(800, 40), 12
+    morphology regimes, N(0, 0.02^2) noise, seed 4) at n points, one length
+    (m = 128, ell = 64, K = 8) through the greedy search without the profile set
+    (pastila_snippets_streamed): full passes over the segments, rows recomputed,
+    wall time.  At the documented n = 10^7 the profile set of m = 128 would be
+    3.1 TB."""
+    import torch
+    s = synth.ecg_like(n=n)
+    T = s.T
+    ell = m // 2
+    S, R, C = n // m, m - ell + 1, n - ell + 1
+    with pastila.Series(T, device=device, precision=pastila.FP32) as h:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs, _, _, (passes, rows) = h.snippets_streamed(m, K)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+    pass_ed = S * R * C
+    return {"workload": f"ECG-like series, n={n}, 12 regimes, seed 4; m={m}, ell={ell}, k={(m + 9) // 10}, K={K}",
+            "seconds": sec, "full_passes": int(passes), "rows_recomputed": int(rows),
+            "ed_cells_per_pass": pass_ed,
+            "ed_cells_computed": float(pass_ed * passes + rows * R * C),
+            "ed_cells_per_s": float(pass_ed * passes + rows * R * C) / sec,
+            "snippets": [int(r[0]) for r in recs],
+            "documented_n": 10_000_000,
+            "projected_pass_seconds_at_documented_n": sec / max(1, passes) * (10_000_000 / n) ** 2}
+
+
 def run_ours(args):
     import torch
     from paper_2401_13680_b300 import pastila
@@ -634,6 +681,10 @@ def run_ours(args):
     if not args.no_drift and world == 1:
         drift = run_drift(pastila, local, dev)
 
+    stress = None
+    if args.stress and world == 1:
+        stress = run_stress(pastila, local, args.stress)
+
     serving = None
     if args.serve_jobs > 0 and world == 1:
         serving = run_serving(args, pastila, local, ed_cells * args.steps / tot_s,
@@ -658,7 +709,8 @@ def run_ours(args):
             "gpu_launches_per_step": launches / args.steps, "roofline": roofline,
             "ed_cells_per_s": world * ed_cells * args.steps / tot_s,
             "m_best": result[0], "criterion": [float(x) for x in result[1]],
-            "step_ms": step_ms, "fp64_path": fp64, "errors": errors, "drift_series": drift, "serving": serving,
+            "step_ms": step_ms, "fp64_path": fp64, "errors": errors, "drift_series": drift, "stress": stress,
+            "serving": serving,
             "multivariate": multi, "autotune": tune}
     if cpu is not None:
         line["cpu_baseline"] = cpu
@@ -688,10 +740,15 @@ def main():
                     help="engine policy of the serving leg: processor sharing, shortest predicted remaining "
                          "first, or both one after the other (same arrivals)")
     ap.add_argument("--serve-plain", action="store_true",
-                    help="also run the serving stream one job at a time on FP32 and FP64 handles (slow)")
+                    help="also run the first --serve-plain-jobs jobs of the serving stream one job at a time on "
+                         "FP32 and FP64 handles (slow)")
+    ap.add_argument("--serve-plain-jobs", type=int, default=8)
     ap.add_argument("--no-multi", action="store_true", help="skip the multivariate leg")
     ap.add_argument("--no-errors", action="store_true", help="skip the FP32 error block")
     ap.add_argument("--no-drift", action="store_true", help="skip the million-point drift-series leg")
+    ap.add_argument("--stress", type=int, default=0,
+                    help="points of an ECG-like stress series run through the greedy search without the profile "
+                         "set at m = 128, K = 8 (0: skip; the documented size is 10^7)")
     ap.add_argument("--serve-load", type=float, default=0.7,
                     help="offered load of the serving leg, as a fraction of the measured ED-cell rate")
     args = ap.parse_args()
