@@ -198,7 +198,7 @@ def run_reference(args):
         return 0
     s, ms = workload(args.m_list)
     cores = os.cpu_count() or 1
-    block = 512
+    block = 2048  # the same sample block as the cpu_baseline leg of the GPU arm (about 6 s per step on 16 cores)
     for w in range(args.warmup):
         oracle_sample(s.T, ms, block, 1000 + w, cores)
     times, tot_cells, desc = [], 0, ""
