@@ -34,6 +34,8 @@ constexpr int REF_NCAND = 16;
 // layout of an item's refinement state (int32):
 constexpr int REF_TODO_N = 0;      // rows the next FP64 row launch computes
 constexpr int REF_NC = 1;          // contenders of the current step (0: decided in FP32)
+constexpr int REF_PARTIAL = 2;     // bit c: contender c's FP64 row skips tiles (see batched_refine_need_kernel)
+constexpr int REF_DROPPED = 3;     // 1: some tile is needed by no contender; the areas compared leave it out
 constexpr int REF_HAS = 4;         // [64]: 1 when rows64 slot t holds chosen segment t's FP64 row
 constexpr int REF_TODO_SEG = 68;   // [64 + REF_NCAND]: segments of the to-do rows
 constexpr int REF_TODO_SLOT = REF_TODO_SEG + 64 + REF_NCAND;  // and their rows64 slots
@@ -55,6 +57,7 @@ struct BatchItem {
     double* rows64;
     float* bound;
     double* cand_area;
+    uint8_t* need;         // [REF_NCAND][A64.ntiles]: 1 where contender c's FP64 tile is computed
     int32_t* rst;
     float bc;
     long long cta_begin;   // first CTA of this item in the flattened tile grid (even for cluster tiles)
@@ -209,6 +212,8 @@ __global__ void batched_select_kernel(const BatchItem<real>* __restrict__ items,
             it.area_after[t] = Ab;
             rst[REF_TODO_N] = 0;
             rst[REF_NC] = 0;
+            rst[REF_PARTIAL] = 0;
+            rst[REF_DROPPED] = 0;
             rst[REF_HAS + t] = 0;
         }
         return;
@@ -254,7 +259,56 @@ __global__ void batched_select_kernel(const BatchItem<real>* __restrict__ items,
         }
         rst[REF_TODO_N] = n;
         rst[REF_NC] = nc;
+        rst[REF_PARTIAL] = 0;
+        rst[REF_DROPPED] = 0;
         rst[REF_HAS + t] = 0;
+    }
+}
+
+// Which FP64 tiles of the contenders' rows a step needs.  From step 1 on, where
+// a contender's FP32 value less its error bound is at least the FP32 curve plus
+// its bound, at every position of a tile, the FP64 value there is at least the
+// FP64 curve M64 (each FP32 value is within value_bound of its FP64 value, and
+// M64 <= the chosen row that attains the FP32 curve), so min(M64, D64) = M64 on
+// the whole tile and its FP64 values are not needed; the tile is skipped and
+// the area sums take M64 there.  A tile that no contender needs adds the same
+// sum of M64 to every contender's area, so the comparison leaves it out and the
+// chosen segments' FP64 rows are computed only on the tiles some contender
+// needs (row REF_NCAND of the flags).  At step 0 (M = +inf) every tile is
+// needed.  Grid (largest FP64 tile count, n items), NEED_THREADS threads.
+constexpr int NEED_THREADS = 256;
+template <typename real>
+__global__ void __launch_bounds__(NEED_THREADS) batched_refine_need_kernel(const BatchItem<real>* __restrict__ items,
+                                                                           int t) {
+    const BatchItem<real>& it = items[blockIdx.y];
+    if (t >= it.K || !it.rows64) return;
+    const int nc = it.rst[REF_NC];
+    const int nt = it.A64.ntiles, W = it.A64.W;
+    const int tile = blockIdx.x;
+    if (nc == 0 || tile >= nt) return;
+    const int64_t P = it.A.P;
+    const int64_t p0 = (int64_t)tile * W;
+    const int64_t p1 = p0 + W < P ? p0 + W : P;
+    bool any = false;
+    for (int c = 0; c < nc; ++c) {
+        bool need = t == 0;
+        if (!need) {
+            const real* row = it.A.D + (int64_t)it.rst[REF_CAND + c] * P;
+            for (int64_t p = p0 + threadIdx.x; p < p1 && !need; p += NEED_THREADS) {
+                const float d = (float)row[p], mm = (float)it.M[p];
+                need = d - 1.02f * value_bound(d, it.bc) < mm + 1.02f * value_bound(mm, it.bc) + 1e-5f * (1.0f + mm);
+            }
+        }
+        need = __syncthreads_or(need);
+        any |= need;
+        if (threadIdx.x == 0) {
+            it.need[c * nt + tile] = need ? 1 : 0;
+            if (!need) atomicOr(&it.rst[REF_PARTIAL], 1 << c);
+        }
+    }
+    if (threadIdx.x == 0) {
+        it.need[REF_NCAND * nt + tile] = any ? 1 : 0;
+        if (!any) it.rst[REF_DROPPED] = 1;
     }
 }
 
@@ -278,7 +332,10 @@ __global__ void __launch_bounds__(512) refine_rows_kernel(const BatchItem<float>
     }
     __syncthreads();
     const int seg = rst[REF_TODO_SEG + blockIdx.y], slot = rst[REF_TODO_SLOT + blockIdx.y];
-    profile_tile<double, V>(sA, sG, seg, (int)blockIdx.x / sG.CS, smem, seg - slot);
+    const int tile = (int)blockIdx.x / sG.CS;
+    // a tile the step does not need: a contender's skipped tile, or one no contender needs
+    if (!item->need[(slot >= item->K ? slot - item->K : REF_NCAND) * sA.ntiles + tile]) return;
+    profile_tile<double, V>(sA, sG, seg, tile, smem, seg - slot);
 }
 
 // FP64 areas of the contenders of step t: cand_area[c] = sum_p min(M64_p,
@@ -294,10 +351,15 @@ __global__ void __launch_bounds__(AREA_THREADS) batched_refine_area_kernel(const
     const int64_t P = it.A.P;
     const double* R64 = it.rows64;
     const double* row = R64 + (int64_t)(it.K + c) * P;
+    const uint8_t* nd = it.need + (size_t)c * it.A64.ntiles;  // skipped tiles: min(M64, D64) = M64
+    const uint8_t* any = it.need + (size_t)REF_NCAND * it.A64.ntiles;  // tiles no contender needs: left out
+    const int W64 = it.A64.W;
     double a0 = 0.0, a1 = 0.0;
     int64_t p = threadIdx.x;
     auto term = [&](int64_t q) {
-        double v = row[q];
+        const int tq = (int)(q / W64);
+        if (!any[tq]) return 0.0;
+        double v = nd[tq] ? row[q] : __longlong_as_double(0x7ff0000000000000ll);
         for (int u = 0; u < t; ++u) {
             const double w = R64[(int64_t)u * P + q];
             v = w < v ? w : v;
@@ -335,8 +397,19 @@ __global__ void batched_choose_update_kernel(const BatchItem<real>* __restrict__
     }
     if (refined && blockIdx.x == 0 && threadIdx.x == 0) {
         it.chosen[t] = seg;
-        it.area_after[t] = it.cand_area[best];
-        it.rst[REF_HAS + t] = 1;
+        // the FP64 area when every tile was summed, else the FP32 one (within the
+        // FP32 rule of it); the chosen segment's FP64 row is complete unless tiles
+        // were skipped (then a later step computes it again)
+        const bool dropped = it.rst[REF_DROPPED] != 0;
+        it.area_after[t] = dropped ? it.area[seg] : it.cand_area[best];
+        it.rst[REF_HAS + t] = dropped || ((it.rst[REF_PARTIAL] >> best) & 1) ? 0 : 1;
+        if (dropped) {  // the chosen rows this step computed cover only the tiles it needed
+            const int nt = it.rst[REF_TODO_N];
+            for (int y = 0; y < nt; ++y) {
+                const int slot = it.rst[REF_TODO_SLOT + y];
+                if (slot < it.K) it.rst[REF_HAS + slot] = 0;
+            }
+        }
     }
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;

@@ -583,6 +583,8 @@ BatchItem<real> item_desc(const pastila_engine* e, const EJob& j, const EItem& i
         bi.cand_area = (double*)r;
         r += up256e(8 * REF_NCAND);
         A64.dmax_key = (unsigned long long*)r;
+        r += up256e(8);
+        bi.need = (uint8_t*)r;
         A64.D = bi.rows64;
         bi.A64 = A64;
         bi.G64 = it.g64;

@@ -586,7 +586,8 @@ constexpr double REF_DRHO = 2e-6;  // the FP32 profiles' accuracy in rho at ever
 
 inline size_t refine_bytes(const MParams& q, int K) {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return up(8 * (size_t)(K + REF_NCAND) * (size_t)q.P) + up(4 * (size_t)q.S) + up(8 * REF_NCAND) + up(8);
+    return up(8 * (size_t)(K + REF_NCAND) * (size_t)q.P) + up(4 * (size_t)q.S) + up(8 * REF_NCAND) + up(8) +
+           up((size_t)(REF_NCAND + 1) * (size_t)((q.P + 31) / 32));  // tile flags (FP64 tiles are >= 32 wide)
 }
 
 // Fills it's refinement fields from region (refine_bytes) and rst (REF_STATE_INTS
@@ -628,6 +629,8 @@ pastila_status refine_attach(pastila_series* h, const MParams& q, int K, BatchIt
     it->cand_area = (double*)r;
     r += up(8 * REF_NCAND);
     A.dmax_key = (unsigned long long*)r;  // the FP64 rows' D max (unused)
+    r += up(8);
+    it->need = (uint8_t*)r;
     A.D = it->rows64;
     it->A64 = A;
     it->G64 = g;
@@ -667,6 +670,13 @@ int enqueue_greedy(cudaStream_t s, const BatchItem<real>* d_items, const std::ve
         }
         batched_select_kernel<real><<<n, 1024, 0, s>>>(d_items, t);
         launches += 2;
+        if constexpr (std::is_same<real, float>::value) {
+            int nt64 = 1;
+            for (const auto& it : hi)
+                if (it.rows64 && it.A64.ntiles > nt64) nt64 = it.A64.ntiles;
+            batched_refine_need_kernel<real><<<dim3((unsigned)nt64, n), NEED_THREADS, 0, s>>>(d_items, t);
+            ++launches;
+        }
         if constexpr (std::is_same<real, float>::value) {
             for (int i = 0; i < n; ++i) {
                 const BatchItem<real>& it = hi[i];

@@ -96,6 +96,13 @@ __device__ __forceinline__ double row_min_partial(const real* __restrict__ row, 
 // the two sides), max(x, sqrt(x^2 + c) - x) otherwise.  In FP32: a bound, not
 // an area; its own rounding, below 1 % for the sizes here, is covered by the
 // caller's margin.
+__device__ __forceinline__ float value_bound(float x, float c) {
+    const float x2 = x * x;
+    if (x2 > c) return c / (x + sqrtf(x2 - c));
+    const float up = c / (sqrtf(x2 + c) + x);
+    return x > up ? x : up;
+}
+
 template <typename real>
 __device__ __forceinline__ float row_bound_partial(const real* __restrict__ row, const real* __restrict__ M,
                                                    int64_t P, float c) {
@@ -108,10 +115,7 @@ __device__ __forceinline__ float row_bound_partial(const real* __restrict__ row,
             const float mm = (float)M[q];
             x = x < mm ? x : mm;
         }
-        const float x2 = x * x;
-        if (x2 > c) return c / (x + sqrtf(x2 - c));
-        const float up = c / (sqrtf(x2 + c) + x);
-        return x > up ? x : up;
+        return value_bound(x, c);
     };
     for (; p + st < P; p += 2 * st) {
         a0 += term(p);
