@@ -441,7 +441,22 @@ def fp32_errors(h, T, ms, res32, res64, dev, count=24, seed=11):
         s32 = [int(r[0]) for r in res32[2]]
         s64 = [int(r[0]) for r in res64[2]]
         out["m_best_snippets"] = {"fp32": s32, "fp64": s64, "equal": s32 == s64}
+        # every length's snippets in greedy order (single-length snippets on both handles)
+        with pastila_module().Series(T, device=dev.index or 0, precision=pastila_module().FP64) as h64:
+            agree = []
+            for m in ms:
+                a = [int(r[0]) for r in sorted(h.snippets(m, K_SNIPPETS)[0], key=lambda r: r[1])]
+                b = [int(r[0]) for r in sorted(h64.snippets(m, K_SNIPPETS)[0], key=lambda r: r[1])]
+                agree.append({"m": m, "fp32": a, "fp64": b, "equal": a == b})
+        out["snippets_per_m"] = {"reference": "FP64 GPU path, pastila_snippets per length",
+                                 "equal_lengths": sum(x["equal"] for x in agree), "lengths": len(agree),
+                                 "per_m": agree}
     return out
+
+
+def pastila_module():
+    from paper_2401_13680_b300 import pastila
+    return pastila
 
 
 def run_drift(pastila, device, dev, m=256, K=6, nseg=32, block=512, seed=12):
