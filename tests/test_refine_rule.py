@@ -18,8 +18,10 @@ def value_bound(x, c):
     c / (2 ell) (the device's value_bound, c = 2.2 ell * 2e-6)."""
     x = np.asarray(x, dtype=np.float64)
     x2 = x * x
-    up = c / (np.sqrt(x2 + c) + x)
-    return np.where(x2 > c, c / (x + np.sqrt(np.maximum(x2 - c, 0.0))), np.maximum(x, up))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        up = c / (np.sqrt(x2 + c) + x)
+        hi = c / (x + np.sqrt(np.maximum(x2 - c, 0.0)))
+    return np.where(x2 > c, hi, np.maximum(x, up))
 
 
 def perturbed(D64, ell, rng):
