@@ -939,7 +939,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     const bool far_vec = sizeof(real) == 4 && V == 4 && rr == 0;  // 16-byte aligned: xb and R - 1 multiples of 4
 
     auto row_loop = [&](auto check_tag) {
-    constexpr bool CHECK = decltype(check_tag)::value;
+    [[maybe_unused]] constexpr bool CHECK = decltype(check_tag)::value;
         key_t* ABr = ABo + (size_t)r0 * RS + (t - tofs);
         for (int c0 = 0; c0 < Rg; c0 += V) {
     #pragma unroll
