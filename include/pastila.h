@@ -291,6 +291,13 @@ typedef struct {
                                     as select_length does (pastila_set_fp64_ties); 1 decides every step on
                                     the FP32 areas alone (no FP64 rows: wave times then depend only on the
                                     wave's work, not on how many steps are near-ties) */
+    const char* job_log_path;    /* NULL (default): no log; else a file the engine appends one JSON line to
+                                    per job that ends (done, failed or cancelled): id, state, status,
+                                    message, n, lengths, K, submit / admit / done times (engine clock, s),
+                                    latency, first and last wave, ED and profile cells, memory, the
+                                    runtime model's prediction, and m_best of a finished job.  The
+                                    engine opens it at creation (EINVAL if it cannot) and closes it when
+                                    destroyed; lines are flushed as they are written */
 } pastila_engine_config;
 
 typedef enum {

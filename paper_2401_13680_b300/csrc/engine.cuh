@@ -286,6 +286,10 @@ struct pastila_engine {
     double age_weight = 0.0;
     int policy = PASTILA_POLICY_SHARE;
     bool refine = true;  // FP32: near-tied greedy steps decided on FP64 areas
+    FILE* job_log = nullptr;  // one JSON line per job that ends (pastila_engine_config.job_log_path)
+    ~pastila_engine() {
+        if (job_log) fclose(job_log);
+    }
     int fail_at = 0;
     int* err = nullptr;  // host-mapped flag the tile kernels set when a bounded wait runs out
     long long spin_limit = 1ll << 31;
@@ -360,6 +364,30 @@ pastila_status eng_event(pastila_engine* e, cudaEvent_t* ev) {
     return PASTILA_OK;
 }
 
+// The job's JSON line in the engine's log (messages keep printable ASCII only,
+// quotes and backslashes escaped).
+void log_job(pastila_engine* e, const EJob& j) {
+    if (!e->job_log) return;
+    static const char* const names[5] = {"queued", "active", "done", "failed", "cancelled"};
+    std::string msg;
+    for (char ch : j.msg) {
+        if (ch == '"' || ch == '\\') msg += '\\';
+        if (ch >= 32 && ch < 127) msg += ch;
+    }
+    std::string ms;
+    for (size_t i = 0; i < j.ms.size(); ++i) ms += (i ? ", " : "") + std::to_string(j.ms[i]);
+    fprintf(e->job_log,
+            "{\"job\": %lld, \"state\": \"%s\", \"status\": %d, \"message\": \"%s\", \"n\": %lld, "
+            "\"m_list\": [%s], \"K\": %d, \"t_submit\": %.6f, \"t_admit\": %.6f, \"t_done\": %.6f, "
+            "\"latency_s\": %.6f, \"first_wave\": %lld, \"last_wave\": %lld, \"ed_cells\": %.6g, "
+            "\"profile_cells\": %.6g, \"mem_bytes\": %zu, \"predicted_ms\": %.3f, \"m_best\": %d}\n",
+            (long long)j.id, names[j.state < 0 || j.state > 4 ? 0 : j.state], (int)j.status, msg.c_str(),
+            (long long)j.n, ms.c_str(), j.K, j.t_submit, j.t_admit, j.t_done, j.t_done - j.t_submit,
+            (long long)j.first_wave, (long long)j.last_wave, j.ed_cells, j.profile_cells,
+            j.res_bytes + j.max_dbytes, j.pred_ms, j.state == PASTILA_JOB_DONE ? (int)j.m_best : 0);
+    fflush(e->job_log);
+}
+
 void job_final_state(pastila_engine* e, EJob& j, int state, pastila_status st, const std::string& msg) {
     j.state = state;
     j.status = st;
@@ -368,6 +396,7 @@ void job_final_state(pastila_engine* e, EJob& j, int state, pastila_status st, c
     if (state == PASTILA_JOB_DONE) e->n_done++;
     if (state == PASTILA_JOB_FAILED) e->n_failed++;
     if (state == PASTILA_JOB_CANCELLED) e->n_cancelled++;
+    log_job(e, j);
     j.T.clear();
     j.T.shrink_to_fit();
     e->cv_done.notify_all();
@@ -1166,6 +1195,10 @@ pastila_status pastila_engine_create(pastila_engine** out, const pastila_engine_
     e->age_weight = c.age_weight_s;
     e->policy = c.policy;
     e->refine = c.prec == PASTILA_FP32 && c.fp32_greedy == 0;
+    if (c.job_log_path && *c.job_log_path) {
+        e->job_log = fopen(c.job_log_path, "a");
+        if (!e->job_log) return fail(PASTILA_EINVAL, "cannot open the job log %s", c.job_log_path);
+    }
     int smem = 0;
     CK(cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
     e->smem_optin = smem - 1024;

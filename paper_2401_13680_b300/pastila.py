@@ -33,7 +33,8 @@ class EngineConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("prec", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
                 ("max_active_jobs", ctypes.c_int32), ("wave_ed_cells", ctypes.c_double),
                 ("max_waves_in_flight", ctypes.c_int32), ("fail_alloc_at", ctypes.c_int32),
-                ("age_weight_s", ctypes.c_double), ("policy", ctypes.c_int32), ("fp32_greedy", ctypes.c_int32)]
+                ("age_weight_s", ctypes.c_double), ("policy", ctypes.c_int32), ("fp32_greedy", ctypes.c_int32),
+                ("job_log_path", ctypes.c_char_p)]
 
 
 POLICY_SHARE, POLICY_SRPT = 0, 1
@@ -350,10 +351,12 @@ class Engine:
 
     def __init__(self, device: int = 0, precision: int = FP32, mem_budget: int = 0, max_active: int = 0,
                  wave_ed_cells: float = 0.0, max_waves_in_flight: int = 0, fail_alloc_at: int = 0,
-                 age_weight_s: float = 0.0, policy: int = POLICY_SHARE, fp32_greedy: bool = False):
+                 age_weight_s: float = 0.0, policy: int = POLICY_SHARE, fp32_greedy: bool = False,
+                 job_log: str | None = None):
         lib = load()
         cfg = EngineConfig(device, precision, mem_budget, max_active, wave_ed_cells, max_waves_in_flight,
-                           fail_alloc_at, age_weight_s, policy, 1 if fp32_greedy else 0)
+                           fail_alloc_at, age_weight_s, policy, 1 if fp32_greedy else 0,
+                           job_log.encode() if job_log else None)
         h = _vp()
         _check(lib.pastila_engine_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h

@@ -351,3 +351,31 @@ def test_multivariate_coordinates_match_the_oracle(lib):
         assert res[c][0] == m_best
         np.testing.assert_allclose(res[c][1], crit, rtol=1e-3)
         assert [x[0] for x in sorted(res[c][2], key=lambda x: x[1])] == [int(c_) for c_ in chosen[m_best]]
+
+
+def test_job_log_has_one_line_per_finished_job(lib, tmp_path):
+    """With a job log the engine appends one JSON line per job that ends: ids,
+    states and m_best agree with polling; a cancelled queued job is logged as
+    cancelled."""
+    import json
+    from paper_2401_13680_b300 import pastila
+    path = tmp_path / "jobs.jsonl"
+    jobs = _jobs()[:2]
+    with pastila.Engine(job_log=str(path), max_active=1) as e:
+        ids = [e.submit(T, ms, K) for T, ms, K in jobs]
+        extra = e.submit(*jobs[0])
+        e.cancel(extra)
+        infos = [e.wait(i) for i in ids]
+        results = [e.result(i) for i in ids]
+        e.wait(extra)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    by_id = {x["job"]: x for x in lines}
+    assert len(lines) == 3 and set(by_id) == set(ids) | {extra}
+    for i, info, res, (T, ms, K) in zip(ids, infos, results, jobs):
+        rec = by_id[i]
+        assert rec["state"] == "done" and rec["status"] == pastila.OK
+        assert rec["m_best"] == res[0] and rec["m_list"] == list(ms) and rec["K"] == K and rec["n"] == T.shape[0]
+        assert rec["t_submit"] <= rec["t_admit"] <= rec["t_done"]
+        assert abs(rec["latency_s"] - (info["t_done"] - info["t_submit"])) < 1e-5
+        assert rec["ed_cells"] > 0 and rec["first_wave"] <= rec["last_wave"]
+    assert by_id[extra]["state"] == "cancelled"
