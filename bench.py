@@ -67,8 +67,9 @@ def tile_sources_sha():
     return h.hexdigest()
 
 
-def measured_traffic():
-    """(bytes per sweep step, provenance) from the recorded capture, or (None, why)."""
+def recorded_capture():
+    """The recorded ncu figures of the tile kernel if they were taken on the current
+    kernel sources: (record, None), else (None, why)."""
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)
@@ -76,6 +77,14 @@ def measured_traffic():
         return None, "no recorded capture"
     if rec.get("kernel_sources_sha256") != tile_sources_sha():
         return None, "the recorded capture predates the current kernel sources"
+    return rec, None
+
+
+def measured_traffic():
+    """(bytes per sweep step, provenance) from the recorded capture, or (None, why)."""
+    rec, why = recorded_capture()
+    if rec is None:
+        return None, why
     return float(rec["dram_bytes_per_sweep_step"]), rec.get("capture", "")
 
 
@@ -660,6 +669,7 @@ def run_ours(args):
                 "ed_cells_per_s": ed_cells * args.steps / tile_s,
                 "tile_share_of_step": tile_s / tot_s if world == 1 else None,
                 "halo_factor": tile_cells_halo / (ed_cells * args.steps),
+                "issue_active_ncu": (recorded_capture()[0] or {}).get("issue_active"),
                 "fma_measured_tflops": {"fp32": fma32, "fp64": fma64,
                                         "basis": "pastila_probe_fma: 8 independent FMA chains per thread, "
                                                  "8 CTAs of 256 threads per SM, events"},
