@@ -387,11 +387,13 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
             f(cur[j], rin[j]);
             f(rin[j] ? CBl[p + 32 * j] : NEG, rin[j]);
         }
-        for (int j = NJ; j < nrw; ++j) {
-            const int r = lane + 32 * j;
-            const bool in = r < R;
-            f(in ? AB[r * RS + cp] : NEG, in);
-            f(in ? CBl[p + 32 * j] : NEG, in);
+        if constexpr (NJ == SEL_CAP) {  // below the cap, NJ rows per lane cover R
+            for (int j = NJ; j < nrw; ++j) {
+                const int r = lane + 32 * j;
+                const bool in = r < R;
+                f(in ? AB[r * RS + cp] : NEG, in);
+                f(in ? CBl[p + 32 * j] : NEG, in);
+            }
         }
     };
     auto count_ge = [&](real t) {  // t > NEG: absent entries never count
@@ -523,9 +525,11 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
             if (it + 1 < npos) load_col(q + 1, nxt);
             int d = nsum - ccur;
             ccur = nsum;
-            for (int j = NJ; j < nrw; ++j) {
-                const int r = lane + 32 * j;
-                if (r < R) d += cnt2(AB[r * RS + cp]) - cnt2(AB[r * RS + cprev]);
+            if constexpr (NJ == SEL_CAP) {
+                for (int j = NJ; j < nrw; ++j) {
+                    const int r = lane + 32 * j;
+                    if (r < R) d += cnt2(AB[r * RS + cp]) - cnt2(AB[r * RS + cprev]);
+                }
             }
             d += wsgn * cnt2(CB[p + wofs]);
             d = (int)__reduce_add_sync(FULL, (unsigned)d);
@@ -592,9 +596,9 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     key_t* CB = (key_t*)(sm + G.off_CB);
     cmp_t* PRE = (cmp_t*)(sm + G.off_PRE) + (size_t)g * 2 * NTc * V;  // this group's [parity][column]: maxima
                                                                         // from the column's chunk start to it
-    cmp_t* LV = (cmp_t*)(sm + G.off_LV) + (size_t)g * 2 * 5 * NTc;     // [parity][k][NTc]: max of the 2^k chunk
+    cmp_t* LV = (cmp_t*)(sm + G.off_LV) + (size_t)g * 2 * 5 * NTc;     // [parity][NTc][k]: max of the 2^k chunk
                                                                         // maxima from a chunk on, within its warp
-    real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [parity][warp][hi, lo]
+    real* XCH = (real*)(sm + G.off_XCH) + (size_t)g * 4 * NWc;       // [warp][parity][hi, lo]
     real* rst = (real*)(sm + G.off_rst);                              // [row][df, dg, a, 0]
     // segment data are staged from the 16-byte boundary at or below i0
     constexpr int AE = 16 / (int)sizeof(real);
@@ -725,11 +729,13 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         }
     }
     // the rows' statistics side by side (one 16-byte load per row step)
+    bool flat_row = false;  // a row of this thread with a constant window (a_i = 0)
     for (int r = rbase + tid; r < rend; r += BD) {
         rst[4 * r + 0] = rdf[r];
         rst[4 * r + 1] = rdg[r];
         rst[4 * r + 2] = ra[r];
         rst[4 * r + 3] = (real)0;
+        flat_row = flat_row || ra[r] == (real)0;
     }
     // the groups' centred heads q = T[ig + u] - mu_ig, ig = i0 + rbase + gg Rg
     for (int e = tid; e < NG * ell; e += BD) {
@@ -912,7 +918,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // (its prefix within its chunk is PRE[that column]) and covers chunk t + q0
     // entirely when i + rr >= V.
     const int rr = (R - 1) - q0 * V;
-    int so[4] = {0, 0, 0, 0};
+    int so[6] = {0, 0, 0, 0, 0, 0};  // so[4], so[5]: the first whole warp (else so[0] again)
     int wlo = 0, whi = -1;  // whole warps wlo .. whi between the spans
     const bool use_mid = owns_positions && !small_R && q0 >= 2;
     if (use_mid) {
@@ -921,8 +927,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         auto span = [&](int x, int y, int* o) {  // x <= y in one warp
             int k = 31 - __clz(y - x + 1);
             k = k > 4 ? 4 : k;
-            o[0] = k * NTc + x;
-            o[1] = k * NTc + y - (1 << k) + 1;
+            o[0] = x * 5 + k;
+            o[1] = (y - (1 << k) + 1) * 5 + k;
         };
         if (wa == wz) {
             span(a, z, so);
@@ -934,19 +940,54 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             wlo = wa + 1;
             whi = wz - 1;
         }
+        so[4] = wlo <= whi ? wlo * 160 + 4 : so[0];
+        so[5] = wlo <= whi ? wlo * 160 + 84 : so[0];
     }
     const int far0 = xb + R - 1;  // PRE column of the window end of position xb
     const bool far_vec = sizeof(real) == 4 && V == 4 && rr == 0;  // 16-byte aligned: xb and R - 1 multiples of 4
+    // the common shape (every length of a sweep with ell = m / 2, m a multiple of
+    // 8 and at most 520): windows of 3 to 66 chunks that end at a chunk boundary,
+    // window ends read as one 16-byte load, at most one whole warp of chunks
+    // between the two spans of the sparse tables.
+    const bool common_rw = !small_R && far_vec && q0 >= 2 && q0 <= 65;  // at most one whole warp between the spans
+
+    // A chunk of V row steps is FAST when the conditions that the row steps test
+    // at every row are known for the whole tile: the common shape, all V rows of
+    // every row group active, every owner's V positions in the tile and every
+    // lane's columns wholly inside or wholly past the window (Wp a multiple of V:
+    // the values past it are never read), no cell of the tile on the diagonal
+    // i == j, and no row of the CTA with a constant window.  Fast chunks run a copy
+    // of the row steps compiled with those conditions constant (their tests and
+    // branches are a large share of a row step's instructions); the others run the
+    // general copy.  The choice depends only on the tile and the chunk, so every
+    // thread of the CTA (threads outside the layout included, which skip the row
+    // work) runs the same copy and meets the same barriers.
+    int nrows_min = Rg;  // rows of the shortest row group of the layout
+    {
+        const int last = rbase + (NG - 1) * Rg;
+        const int nl = last >= rend ? 0 : (last + Rg <= rend ? Rg : rend - last);
+        nrows_min = nl < Rg ? nl : Rg;
+    }
+    const int64_t dlo = i0 - p0 + rbase, dhi = i0 - p0 + rend - 1;  // diagonal columns of the CTA's rows
+    bool tile_fast = common_rw && Wp % V == 0 && (dhi < 0 || dlo >= (int64_t)NTc * V);
 
     auto row_loop = [&](auto check_tag) {
     [[maybe_unused]] constexpr bool CHECK = decltype(check_tag)::value;
         key_t* ABr = ABo + (size_t)r0 * RS + (t - tofs);
-        for (int c0 = 0; c0 < Rg; c0 += V) {
+        auto chunk = [&](int c0, auto fast_tag) {
+        constexpr bool FAST = decltype(fast_tag)::value;
+        const bool sR = FAST ? false : small_R;
+        [[maybe_unused]] const bool fvec = FAST ? true : far_vec;
+        const bool tables = FAST ? true : q0 >= 2;
+        const bool mid_on = FAST ? true : use_mid;  // read where the thread owns positions
+        const int rrc = FAST ? 0 : rr;
+        const bool pcols = FAST ? false : partial_cols;
+        const bool fullp = FAST ? true : full_positions;  // read where the thread owns positions
     #pragma unroll
             for (int jj = 0; jj < V; ++jj) {
                 const int sidx = c0 + jj;          // row step within the group
                 const int r = r0 + sidx;
-                const bool active = sidx < nrows;  // uniform within the group
+                const bool active = FAST ? worker : sidx < nrows;  // uniform within the group
                 const int par = sidx & 1;
                 cmp_t* PREp = PRE + par * NTc * V;
                 cmp_t* LVp = LV + par * 5 * NTc;
@@ -969,8 +1010,8 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                         real lhi = __shfl_up_sync(FULL, hi[Pout], 1);
                         real llo = __shfl_up_sync(FULL, lo[Pout], 1);
                         if (lane == 0 && wc > 0) {
-                            lhi = XCH[((par ^ 1) * NWc + wc - 1) * 2 + 0];
-                            llo = XCH[((par ^ 1) * NWc + wc - 1) * 2 + 1];
+                            lhi = XCH[(wc - 1) * 4 + (par ^ 1) * 2 + 0];
+                            llo = XCH[(wc - 1) * 4 + (par ^ 1) * 2 + 1];
                         }
     #pragma unroll
                         for (int v = 1; v < V; ++v) {
@@ -1026,12 +1067,12 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     }
                     if (lane == 31) {
                         const int Plast = (V - 1 - jj + V) % V;
-                        XCH[(par * NWc + wc) * 2 + 0] = hi[Plast];
-                        XCH[(par * NWc + wc) * 2 + 1] = lo[Plast];
+                        XCH[wc * 4 + par * 2 + 0] = hi[Plast];
+                        XCH[wc * 4 + par * 2 + 1] = lo[Plast];
                     }
                     {
                         real rho[V];
-                        if (ar != (real)0) {
+                        if (FAST || ar != (real)0) {
     #pragma unroll
                             for (int v = 0; v < V; ++v) {
                                 const int P = (v - jj + V) % V;
@@ -1043,7 +1084,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                             for (int v = 0; v < V; ++v) rho[v] = ca[v] == (real)0 ? (real)1 : (real)0;
                         }
                         const unsigned xd = (unsigned)(xdiag0 + r);  // i == j: correlation 1 by definition
-                        if (xd < (unsigned)V) {
+                        if (!FAST && xd < (unsigned)V) {
     #pragma unroll
                             for (int v = 0; v < V; ++v)
                                 if (v == (int)xd) rho[v] = (real)1;
@@ -1051,7 +1092,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     #pragma unroll
                         for (int v = 0; v < V; ++v) rc[v] = to_cmp(rho[v]);
                     }
-                    if (partial_cols) {
+                    if (pcols) {
     #pragma unroll
                         for (int v = 0; v < V; ++v)
                             if (xb + v >= Wb) rc[v] = NEGc;
@@ -1069,14 +1110,14 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     #pragma unroll
                         for (int v = 0; v < V; ++v) PREp[xb + v] = pre[v];
                     }
-                    if (!small_R) {  // sparse table of the chunk maxima within each warp (level 0: the chunk maxima)
+                    if (!sR) {  // sparse table of the chunk maxima within each warp (level 0: the chunk maxima)
                         cmp_t d = pre[V - 1];
-                        LVp[t] = d;
-                        if (q0 >= 2) {
+                        LVp[t * 5] = d;
+                        if (tables) {
     #pragma unroll
                             for (int k = 0; k < 4; ++k) {  // entries reaching past the warp's end are never read
                                 d = rmax(d, __shfl_down_sync(FULL, d, 1 << k));
-                                LVp[(k + 1) * NTc + t] = d;
+                                LVp[t * 5 + k + 1] = d;
                             }
                         }
                     }
@@ -1087,19 +1128,23 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     suf[V - 1] = rc[V - 1];
     #pragma unroll
                     for (int v = V - 2; v >= 0; --v) suf[v] = rmax(suf[v + 1], rc[v]);
-                    if (!small_R) {
+                    if (!sR) {
                         // whole chunks strictly inside the windows: t+1 .. t+q0-1 (mid), and
                         // chunk t+q0 as well once the window end moves into chunk t+q0+1
                         cmp_t mid = NEGc;
-                        if (use_mid) {
+                        if (mid_on) {
                             mid = rmax(rmax(LVp[so[0]], LVp[so[1]]), rmax(LVp[so[2]], LVp[so[3]]));
-                            for (int w = wlo; w <= whi; ++w)
-                                mid = rmax(mid, rmax(LVp[4 * NTc + w * 32], LVp[4 * NTc + w * 32 + 16]));
+                            if (FAST) {
+                                if (q0 > 33) mid = rmax(mid, rmax(LVp[so[4]], LVp[so[5]]));
+                            } else {
+                                for (int w = wlo; w <= whi; ++w)
+                                    mid = rmax(mid, rmax(LVp[w * 160 + 4], LVp[w * 160 + 84]));
+                            }
                         }
                         cmp_t far[V];
                         bool far_done = false;
                         if constexpr (sizeof(cmp_t) == 4 && V == 4) {
-                            if (far_vec) {
+                            if (fvec) {
                                 const float4 f4 = *reinterpret_cast<const float4*>(PREp + far0);
                                 far[0] = f4.x;
                                 far[1] = f4.y;
@@ -1112,11 +1157,17 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     #pragma unroll
                             for (int i = 0; i < V; ++i) far[i] = PREp[far0 + i];
                         }
-                        const cmp_t mid1 = rr > 0 ? rmax(mid, LVp[t + q0]) : mid;
+                        const cmp_t mid1 = rrc > 0 ? rmax(mid, LVp[(t + q0) * 5]) : mid;
+                        cmp_t ab[V];
     #pragma unroll
-                        for (int i = 0; i < V; ++i) {
-                            const cmp_t ab = rmax(rmax(suf[i], i + rr >= V ? mid1 : mid), far[i]);
-                            if (full_positions || xb + i < Wp) ABr[i * LA] = cmp_bits(ab);
+                        for (int i = 0; i < V; ++i) ab[i] = rmax(rmax(suf[i], i + rrc >= V ? mid1 : mid), far[i]);
+                        if (fullp) {
+    #pragma unroll
+                            for (int i = 0; i < V; ++i) ABr[i * LA] = cmp_bits(ab[i]);
+                        } else {
+    #pragma unroll
+                            for (int i = 0; i < V; ++i)
+                                if (xb + i < Wp) ABr[i * LA] = cmp_bits(ab[i]);
                         }
                     } else {
     #pragma unroll
@@ -1130,7 +1181,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                             } else {
                                 ab = rmax(suf[i], PREp[far0 + i]);
                             }
-                            if (full_positions || xb + i < Wp) ABr[i * LA] = cmp_bits(ab);
+                            if (fullp || xb + i < Wp) ABr[i * LA] = cmp_bits(ab);
                         }
                     }
                 }
@@ -1145,6 +1196,14 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     lo[v] = 0;
                 }
             }
+        };
+        for (int c0 = 0; c0 < Rg; c0 += V) {
+            if constexpr (sizeof(real) == 4 && V == 4) {
+                if (tile_fast && c0 + V <= nrows_min) chunk(c0, std::true_type{});  // the same for the whole CTA
+                else chunk(c0, std::false_type{});
+            } else {
+                chunk(c0, std::false_type{});
+            }
         }
     };
     // The conditioning check is compiled into a second copy of the row loop,
@@ -1152,6 +1211,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // the loop carries none of its code (a branch and an inner loop at every
     // row cost them about 7 % of their time even when never taken).
     if constexpr (sizeof(real) == 4) {
+        tile_fast = tile_fast && !__syncthreads_or(flat_row);
         if (__syncthreads_or(kap_check)) row_loop(std::true_type{});
         else row_loop(std::false_type{});
     } else {

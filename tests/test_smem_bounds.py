@@ -104,8 +104,8 @@ def _assert_union(pieces, lo, hi):
 def rows_phase_check(G, Wp):
     """Every shared-memory index of the rows phase of a tile with Wp positions
     (per row group and parity: the prefix maxima within each chunk PRE, stored
-    by column; the sparse tables LV [5][NTc] of the chunk maxima (level 0) and
-    of 2, 4, 8, 16 consecutive chunks; the warp exchange XCH [NWc][2]; the row
+    by column; the sparse tables LV [NTc][5] of the chunk maxima (level 0) and
+    of 2, 4, 8, 16 consecutive chunks; the warp exchange XCH [NWc][parity][2]; the row
     statistics [R][4]; the row-window maxima written into the owning CTA's AB)
     lies inside its array, each sparse-table read spans chunks of one warp, and
     the pieces of every owned position's window (own suffix, whole chunks in
@@ -120,8 +120,8 @@ def rows_phase_check(G, Wp):
     xb = t * V_
     # writes of every active thread (all column threads take part in every row step)
     assert per_par_pre + xb.max() + V_ - 1 < G["PRE"] // G["NG"]  # PRE, parity 1
-    assert 5 * NTc + 4 * NTc + t.max() < 2 * 5 * NTc              # LV, parity 1, level 4
-    assert (1 * NWc + NWc - 1) * 2 + 1 < 4 * NWc                  # XCH, parity 1
+    assert 5 * NTc + t.max() * 5 + 4 < 2 * 5 * NTc                # LV, parity 1, level 4
+    assert (NWc - 1) * 4 + 1 * 2 + 1 < 4 * NWc                    # XCH, last warp, parity 1
     assert 4 * (R - 1) + 3 < G["rst"]
     owners = xb < Wp
     for tt in (int(x) for x in t[owners]):
@@ -148,7 +148,7 @@ def rows_phase_check(G, Wp):
                 cover.append(((tt + oi) * V_, (tt + oi) * V_ + si))  # far chunk's prefix
             _assert_union(cover, lo, hi)
         if not small_R and rr > 0:
-            assert tt + q0 <= NTc - 1                    # LV level 0 at t + q0
+            assert (tt + q0) * 5 < 5 * NTc               # LV level 0 at t + q0
         if not small_R and q0 >= 2:
             a_, z_ = tt + 1, tt + q0 - 1
             wa, wz = a_ >> 5, z_ >> 5
@@ -159,12 +159,19 @@ def rows_phase_check(G, Wp):
                 w = 1 << k
                 for s0 in (x, y - w + 1):
                     assert s0 >> 5 == (s0 + w - 1) >> 5 and 0 <= s0 and s0 + w - 1 < NTc
-                    assert k * NTc + s0 < 5 * NTc
+                    assert s0 * 5 + k < 5 * NTc
                     pieces.append((s0, s0 + w - 1))
             for wv in range(wa + 1, wz):
-                assert 4 * NTc + wv * 32 + 16 < 5 * NTc
+                assert (wv * 32 + 16) * 5 + 4 < 5 * NTc
                 pieces += [(wv * 32, wv * 32 + 15), (wv * 32 + 16, wv * 32 + 31)]
             _assert_union(pieces, a_, z_)
+            if rr == 0 and 2 <= q0 <= 65:
+                # the fast row steps read one whole warp at most, and only past
+                # q0 = 33; no read reaches a chunk past the window of the tile
+                whole = max(0, wz - wa - 1)
+                assert whole <= 1 and (whole == 0 or q0 > 33)
+                if Wp % V_ == 0:
+                    assert z_ <= (Wp + R - 1) // V_ - 1
         # the row-window maxima of this thread's positions, into the owner's AB
         owner = x0 // Wc if CS > 1 else 0
         tofs = owner * (Wc // V_) if CS > 1 else 0
