@@ -353,8 +353,9 @@ constexpr int SEL_STEPS = 4;  // nearest-value steps before a position falls bac
 // out(p, tau) is called by one lane per position, for 32 positions at a time.
 // NJ: AB rows held per lane in registers (rows lane + 32 j, j < NJ); the caller
 // picks the smallest NJ with 32 NJ >= R, or SEL_CAP (rows beyond are then read
-// from shared memory).  V: positions per AB row chunk (a power of two).
-template <int NJ, int V, typename real, typename Out>
+// from shared memory).  NJV: rows j < NJV exist on every lane (R >= 32 NJV), so
+// their tests compile away.  V: positions per AB row chunk (a power of two).
+template <int NJ, int NJV, int V, typename real, typename Out>
 __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS, int LA,
                                             const real* __restrict__ CB, int R, int kk, int p_begin,
                                             int npos, int pofs, Out out) {
@@ -371,7 +372,7 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
         const int r = lane + 32 * j;
-        rin[j] = r < R;
+        rin[j] = j < NJV || r < R;  // the caller guarantees R >= 32 NJV
         roff[j] = (rin[j] ? r : 0) * RS;
     }
     const real* CBl = CB + lane;    // window entry j of position p: CBl[p + 32 j]
@@ -744,28 +745,31 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         q[gg * (ell + 1) + u] = (Ts[rb + u] - rmu[rb]) + (Tsl[rb + u] - rmul[rb]);
     }
     __syncthreads();
-    if ((tid >> 5) < NG) {  // warp gg: sum of group gg's rounded q, in FP64
-        const int gg = tid >> 5;
-        double acc = 0;
-        for (int u = lane; u < ell; u += 32) acc += (double)q[gg * (ell + 1) + u];
+    // the sum of group gg's rounded q, in FP64, by warp gg of the caller's warps
+    auto head_sums = [&](int w, int nw) {
+        for (int gg = w; gg < NG; gg += nw) {
+            double acc = 0;
+            for (int u = lane; u < ell; u += 32) acc += (double)q[gg * (ell + 1) + u];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (lane == 0) q[gg * (ell + 1) + ell] = (real)acc;
-    }
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+            if (lane == 0) q[gg * (ell + 1) + ell] = (real)acc;
+        }
+    };
 
     // ---------------------------------------------------------------- seeds
     // left edge: cov(r, 0) = sum_t (T[i+t] - mu_i) * (T[p0+t] - mu_p0), both
-    // factors centred term by term from their hi + lo parts
-    {
+    // factors centred term by term from their hi + lo parts; computed by the
+    // threads lt = 0 .. nthr - 1 (a multiple of 32) of the caller's choice
+    auto left_seeds = [&](int lt, int nthr) {
         // SPLIT consecutive lanes per row, lane sp summing the terms sp, sp + SPLIT,
         // ... (consecutive lanes, consecutive words), then a fixed-order shuffle sum:
-        // short dependent chains, every thread busy
+        // short dependent chains
         const int rfirst = rbase > 1 ? rbase : 1;
         const int nrow = rend - rfirst;
         int SPLIT = 1;  // from the tile's own thread count: the same sums in every launch
         while (SPLIT < 32 && nrow > 0 && nrow * SPLIT * 2 <= G.NT) SPLIT *= 2;
-        for (int base = 0; base < nrow * SPLIT; base += BD) {
-            const int idx = base + tid;
+        for (int base = 0; base < nrow * SPLIT; base += nthr) {
+            const int idx = base + lt;
             const int r = rfirst + idx / SPLIT, sp = idx % SPLIT;
             real acc = 0;
             if (r < rend) {
@@ -776,8 +780,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             for (int o = SPLIT >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o, SPLIT);
             if (r < rend && sp == 0) lseed[r] = acc;
         }
-    }
-    __syncthreads();
+    };
     // first row of every group: cov(r0, x) = sum_t q[t] * (T[x+t] - c) - (mu_x - c) * sum_t q[t]
     // for any constant c (the centred q sums to 0 up to rounding, and its rounded
     // sum is taken exactly).  c is the mean of each block's first column: the
@@ -785,31 +788,36 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     // those of c, as they enter a sliding register window, so the products
     // never carry the level of the series, only its local deviations.  Lane-contiguous blocks of
     // 9 columns (odd stride: conflict-free sliding loads).
-    {
-        constexpr int J = 9;
-        const int nblk = (NTc * V + J - 1) / J;
-        for (int b = tid; b < NG * nblk; b += BD) {
-            const int gg = b / nblk;
-            const int x0 = (b - gg * nblk) * J;
-            const real* qg = q + gg * (ell + 1);
-            // every mean of the block loaded together (FP32 path; the FP64 path has
-            // no registers to spare and loads them where they are used)
-            constexpr bool early = sizeof(real) == 4;
-            real mxh[J], mxl[J];
+    constexpr int J = 9;
+    const int nblk = (NTc * V + J - 1) / J;
+    // by threads gt = 0 .. nthr - 1 (nthr >= NG nblk: one block per thread); with
+    // wait_sums, every one of them waits on barrier 1 for the groups' sums of q
+    // (written by other warps, which arrive there) before the last step
+    auto group_seeds = [&](int gt, int nthr, bool wait_sums) {
+        const bool has = gt < NG * nblk;
+        const int gg = has ? gt / nblk : 0;
+        const int x0 = (gt - gg * nblk) * J;
+        const real* qg = q + gg * (ell + 1);
+        // every mean of the block loaded together (FP32 path; the FP64 path has
+        // no registers to spare and loads them where they are used)
+        constexpr bool early = sizeof(real) == 4;
+        real mxh[J], mxl[J];
+        real cbh = 0, cbl = 0;
+        real acc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[j] = 0;
+        if (has) {
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 const bool in = early && x0 + j < Wb;
                 mxh[j] = in ? A.muh[p0 + x0 + j] : (real)0;
                 mxl[j] = in ? A.mul[p0 + x0 + j] : (real)0;
             }
-            const real cbh = x0 < Wb ? (early ? mxh[0] : A.muh[p0 + x0]) : (real)0;
-            const real cbl = x0 < Wb ? (early ? mxl[0] : A.mul[p0 + x0]) : (real)0;
-            real acc[J], win[J];
+            cbh = x0 < Wb ? (early ? mxh[0] : A.muh[p0 + x0]) : (real)0;
+            cbl = x0 < Wb ? (early ? mxl[0] : A.mul[p0 + x0]) : (real)0;
+            real win[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                acc[j] = 0;
-                win[j] = (Tc[x0 + j] - cbh) + (Tcl[x0 + j] - cbl);
-            }
+            for (int j = 0; j < J; ++j) win[j] = (Tc[x0 + j] - cbh) + (Tcl[x0 + j] - cbl);
             int u0 = 0;
             for (; u0 + J <= ell; u0 += J) {
                 // J terms summed apart, then added: the rounding of a seed grows with
@@ -837,6 +845,9 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                     acc[j] += qt * ((Tc[e] - cbh) + (Tcl[e] - cbl));
                 }
             }
+        }
+        if (wait_sums) asm volatile("bar.sync 1, %0;" ::"r"(BD) : "memory");
+        if (has) {
             const real sq = qg[ell];
             real* topg = top + (size_t)gg * NTc * V;
             unsigned far = 0;  // FP32: columns whose mean lies far from the block's centre
@@ -870,6 +881,30 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
                 if (u < ell) c0 += qg[u] * ((Tc[x + u] - mh) + (Tcl[x + u] - ml));
                 topg[x] = c0 + c1;
             }
+        }
+    };
+    // The group seeds take one block of J columns per thread (fewer than half of
+    // the CTA's threads); the left edge runs at the same time on the warps past
+    // them, instead of before them on all threads.  Every sum is formed as it
+    // would be by either arrangement.
+    // The groups' sums of q come first, from the warps past the group seeds, which
+    // then arrive on barrier 1; the group seeds wait there only before their last
+    // step, which reads the sums.
+    {
+        const int tA = (NG * nblk + 31) / 32 * 32;
+        if (tA + 32 <= BD) {  // the same for the whole CTA
+            if (tid < tA) {
+                group_seeds(tid, tA, true);
+            } else {
+                head_sums((tid - tA) >> 5, (BD - tA) >> 5);
+                asm volatile("bar.arrive 1, %0;" ::"r"(BD) : "memory");
+                left_seeds(tid - tA, BD - tA);
+            }
+        } else {
+            head_sums(tid >> 5, BD >> 5);
+            left_seeds(tid, BD);
+            __syncthreads();
+            group_seeds(tid, BD, false);
         }
     }
     __syncthreads();
@@ -1291,11 +1326,12 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         const int npos = pb >= Wn ? 0 : (pb + PW <= Wn ? PW : Wn - pb);
         const cmp_t* ABv = (const cmp_t*)AB;
         const cmp_t* CBv = (const cmp_t*)CB;
-        if (R <= 64) select_warp<2, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 96) select_warp<3, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 160) select_warp<5, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 288) select_warp<9, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else select_warp<SEL_CAP, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        if (R <= 32) select_warp<1, 0, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 64) select_warp<2, 1, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 96) select_warp<3, 2, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 160) select_warp<5, 3, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 288) select_warp<9, 5, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else select_warp<SEL_CAP, 9, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
     }
     const double wmax = warp_max(tmax);
     if (lane == 0) atomicMax(A.dmax_key, KeyOf<double>::enc(wmax));
