@@ -272,9 +272,19 @@ def run_serving(args, pastila, device, ed_rate, fp64_ed_rate, age_weight=0.0, po
     series = [j.series() for j in jobs]  # drawn before the clock starts
     ed = np.array([job_ed_cells(j) for j in jobs], dtype=np.float64)
     prof = np.array([job_profile_cells(j) for j in jobs], dtype=np.float64)
-    rate = args.serve_load * ed_rate / ed.mean()  # jobs/s
-    arrivals = [j.arrival * 20.0 / rate for j in jobs]
     pol = pastila.POLICY_SRPT if policy == "srpt" else pastila.POLICY_SHARE
+    # the engine's capacity on this job mix: every job submitted at once, jobs per
+    # second of makespan (the mix's lengths reach 768 and its series are short, so
+    # it runs below the sweep's cell rate)
+    with pastila.Engine(device=device, age_weight_s=age_weight, policy=pol) as e:
+        t0 = time.perf_counter()
+        ids = [e.submit(T, j.ms, j.K) for T, j in zip(series, jobs)]
+        for i in ids:
+            e.wait(i)
+        closed_s = time.perf_counter() - t0
+    capacity = len(jobs) / closed_s
+    rate = args.serve_load * capacity  # jobs/s
+    arrivals = [j.arrival * 20.0 / rate for j in jobs]
     with pastila.Engine(device=device, age_weight_s=age_weight, policy=pol) as e, ClockSampler(device) as clk:
         t0 = time.perf_counter()
         ids = []
@@ -298,16 +308,17 @@ def run_serving(args, pastila, device, ed_rate, fp64_ed_rate, age_weight=0.0, po
                         "ed_cells_max": float(ed[part].max()),
                         "latency_p50_s": float(np.percentile(lat[part], 50)),
                         "latency_p99_s": float(np.percentile(lat[part], 99))})
-    # the documented stream offers 20 jobs/s; at the measured ED-cell rate the engine
-    # can take ed_rate / mean job size jobs/s, so the leg runs the same jobs with the
-    # arrival clock scaled to the offered load asked
-    capacity = ed_rate / ed.mean()
+    # the documented stream offers 20 jobs/s; the engine takes `capacity` jobs/s of
+    # this mix, so the leg runs the same jobs with the arrival clock scaled to the
+    # offered load asked
     out = {"jobs": len(jobs), "arrival_rate_jobs_per_s": rate, "offered_load": args.serve_load,
            "age_weight_s": age_weight, "policy": policy,
            "workload": "serving stream seed 3: n log-uniform [1e4, 5e5], 3-8 planted regimes + N(0, 0.05^2), "
                        "3-10 lengths from {64, 96, ..., 768}, ell = m/2, K in [3, 6]; Poisson arrivals, "
                        "time-scaled from 20 jobs/s to the offered load",
            "documented_rate_jobs_per_s": 20.0, "capacity_jobs_per_s": capacity,
+           "capacity_basis": "all jobs submitted at once: jobs / makespan (%.1f s)" % closed_s,
+           "sweep_rate_capacity_jobs_per_s": ed_rate / ed.mean(),
            "documented_rate_over_capacity": 20.0 / capacity,
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
            "latency_mean_s": float(lat.mean()), "latency_max_s": float(lat.max()),
