@@ -505,17 +505,30 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
     const int wofs = lane == 0 ? R - 1 : -1;
     const int wsgn = lane == 0 ? 1 : (lane == 1 ? -1 : 0);
 
-    for (int it = 0; it < npos; ++it) {
+    // lane (it mod 32) keeps position it's answer; 32 positions are written at once
+    auto keep = [&](int it) {
+        if (lane == (it & 31)) mine = tau;
+        if ((it & 31) == 31 || it == npos - 1) {
+            const int base = it & ~31;
+            if (base + lane <= it) out(p_begin + base + lane, mine);
+        }
+    };
+    if (npos > 0) {  // the run's first position: the bracketed search
+        p = p_begin;
+        const int q = p - pofs;
+        cp = (q & (V - 1)) * LA + q / V;
+        load_col(q, cur);
+        if (npos > 1) load_col(q + 1, nxt);
+        search();
+        ccur = held();
+        keep(0);
+    }
+    for (int it = 1; it < npos; ++it) {
         p = p_begin + it;
         cprev = cp;
         const int q = p - pofs;
         cp = (q & (V - 1)) * LA + q / V;
-        if (it == 0) {
-            load_col(q, cur);
-            if (npos > 1) load_col(q + 1, nxt);
-            search();
-            ccur = held();
-        } else {
+        {
             // count changes of the values that changed: rows, then the window slide
             int nsum = 0;
 #pragma unroll
@@ -555,12 +568,7 @@ __device__ __forceinline__ void select_warp(const real* __restrict__ AB, int RS,
                 ccur = held();
             }
         }
-        // lane (it mod 32) keeps this position's answer; 32 positions are written at once
-        if (lane == (it & 31)) mine = tau;
-        if ((it & 31) == 31 || it == npos - 1) {
-            const int base = it & ~31;
-            if (base + lane <= it) out(p_begin + base + lane, mine);
-        }
+        keep(it);
     }
 }
 
