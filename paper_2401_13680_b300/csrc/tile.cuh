@@ -1017,8 +1017,11 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
     auto row_loop = [&](auto check_tag) {
     [[maybe_unused]] constexpr bool CHECK = decltype(check_tag)::value;
         key_t* ABr = ABo + (size_t)r0 * RS + (t - tofs);
-        auto chunk = [&](int c0, auto fast_tag) {
-        constexpr bool FAST = decltype(fast_tag)::value;
+        // mode 0: the general copy; 1: the fast copy; 2: the fast copy for a CTA
+        // whose threads are all in the layout (every row step active)
+        auto chunk = [&](int c0, auto mode_tag) {
+        constexpr int MODE = decltype(mode_tag)::value;
+        constexpr bool FAST = MODE > 0;
         const bool sR = FAST ? false : small_R;
         [[maybe_unused]] const bool fvec = FAST ? true : far_vec;
         const bool tables = FAST ? true : q0 >= 2;
@@ -1030,7 +1033,7 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
             for (int jj = 0; jj < V; ++jj) {
                 const int sidx = c0 + jj;          // row step within the group
                 const int r = r0 + sidx;
-                const bool active = FAST ? worker : sidx < nrows;  // uniform within the group
+                const bool active = MODE == 2 ? true : (FAST ? worker : sidx < nrows);  // uniform within the group
                 const int par = sidx & 1;
                 cmp_t* PREp = PRE + par * NTc * V;
                 cmp_t* LVp = LV + par * 5 * NTc;
@@ -1242,10 +1245,14 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         };
         for (int c0 = 0; c0 < Rg; c0 += V) {
             if constexpr (sizeof(real) == 4 && V == 4) {
-                if (tile_fast && c0 + V <= nrows_min) chunk(c0, std::true_type{});  // the same for the whole CTA
-                else chunk(c0, std::false_type{});
+                if (tile_fast && c0 + V <= nrows_min) {  // the same for the whole CTA
+                    if (BD == G.NT) chunk(c0, std::integral_constant<int, 2>{});
+                    else chunk(c0, std::integral_constant<int, 1>{});
+                } else {
+                    chunk(c0, std::integral_constant<int, 0>{});
+                }
             } else {
-                chunk(c0, std::false_type{});
+                chunk(c0, std::integral_constant<int, 0>{});
             }
         }
     };

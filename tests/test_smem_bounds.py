@@ -212,6 +212,20 @@ def check_layout(prec, m, ell, lay):
     J = 9
     nblk = (G["NTc"] * V + J - 1) // J
     assert (nblk - 1) * J + ell - 1 + J < G["Tc"]
+    # the group seeds take one block per thread on the first tA threads (whole
+    # warps); where a warp is left over, the rest form the head sums, arrive on
+    # barrier 1 (count: every thread of the CTA, a multiple of 32) and compute
+    # the left edge, while the group seeds wait there once each
+    tA = (G["NG"] * nblk + 31) // 32 * 32
+    for BD in sorted({G["NT"], min(512, G["NT"] + 32), 512}):
+        if BD < G["NT"]:
+            continue
+        assert BD % 32 == 0 and tA >= G["NG"] * nblk
+        if tA + 32 <= BD:
+            warps_b = (BD - tA) // 32
+            assert warps_b >= 1 and tA % 32 == 0
+            # every group's head sum has a warp (warp w takes groups w, w + warps_b, ...)
+            assert all(any(gg % warps_b == w for w in range(warps_b)) for gg in range(G["NG"]))
     # row-window maxima of owned positions end inside the chunk prefix arrays
     assert G["W"] - 1 + R - 1 <= G["NTc"] * V - 1
 
