@@ -80,22 +80,49 @@ __global__ void __launch_bounds__(512) batched_tiles_kernel(const BatchItem<real
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ProfileArgs<real> sA;
     __shared__ TileGeom sG;
+    __shared__ long long s_first, s_ctas;
+    __shared__ int s_sbegin;
+    static_assert(sizeof(ProfileArgs<real>) % 4 == 0 && sizeof(TileGeom) % 4 == 0, "copied as 4-byte words");
     const long long b = blockIdx.x;
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (items[mid].cta_begin <= b) lo = mid; else hi = mid - 1;
-    }
-    if (threadIdx.x == 0) {
+    // the item of this CTA: the last one whose first CTA is at or before it (the
+    // first item starts at CTA 0).  Up to 32 items, warp 0 reads every item's
+    // first CTA at once and copies the item's arguments word by word, so the CTA
+    // waits for two rounds of loads instead of a chain of them
+    if (n <= 32) {
+        if (threadIdx.x < 32) {
+            const int l = threadIdx.x;
+            const unsigned m = __ballot_sync(0xffffffffu, l < n && items[l].cta_begin <= b);
+            const int lo = 31 - __clz(m);
+            const uint32_t* srcA = reinterpret_cast<const uint32_t*>(&items[lo].A);
+            uint32_t* dstA = reinterpret_cast<uint32_t*>(&sA);
+            for (int w = l; w < (int)(sizeof(ProfileArgs<real>) / 4); w += 32) dstA[w] = srcA[w];
+            const uint32_t* srcG = reinterpret_cast<const uint32_t*>(&items[lo].G);
+            uint32_t* dstG = reinterpret_cast<uint32_t*>(&sG);
+            for (int w = l; w < (int)(sizeof(TileGeom) / 4); w += 32) dstG[w] = srcG[w];
+            if (l == 0) {
+                s_first = items[lo].cta_begin;
+                s_ctas = items[lo].ctas;
+                s_sbegin = items[lo].s_begin;
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].cta_begin <= b) lo = mid; else hi = mid - 1;
+        }
         sA = items[lo].A;
         sG = items[lo].G;
+        s_first = items[lo].cta_begin;
+        s_ctas = items[lo].ctas;
+        s_sbegin = items[lo].s_begin;
     }
     __syncthreads();
-    const long long local = b - items[lo].cta_begin;
-    if (local >= items[lo].ctas) return;  // padding: its cluster partner is a one-CTA tile
+    const long long local = b - s_first;
+    if (local >= s_ctas) return;  // padding: its cluster partner is a one-CTA tile
     const int cs = sG.CS;  // an item of cluster tiles starts at an even CTA of a cluster launch
     const long long per_seg = (long long)sA.ntiles * cs;
-    const int s = items[lo].s_begin + (int)(local / per_seg), tt = (int)((local % per_seg) / cs);
+    const int s = s_sbegin + (int)(local / per_seg), tt = (int)((local % per_seg) / cs);
     profile_tile<real, V>(sA, sG, s, tt, smem);
 }
 
