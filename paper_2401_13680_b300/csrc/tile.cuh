@@ -1341,11 +1341,16 @@ __device__ __forceinline__ void profile_tile(const ProfileArgs<real>& A, const T
         const int npos = pb >= Wn ? 0 : (pb + PW <= Wn ? PW : Wn - pb);
         const cmp_t* ABv = (const cmp_t*)AB;
         const cmp_t* CBv = (const cmp_t*)CB;
+        // NJ = ceil(R / 32) register rows per lane (R >= 32 (NJ - 1): all but the last on every lane)
         if (R <= 32) select_warp<1, 0, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
         else if (R <= 64) select_warp<2, 1, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
         else if (R <= 96) select_warp<3, 2, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 160) select_warp<5, 3, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
-        else if (R <= 288) select_warp<9, 5, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 128) select_warp<4, 3, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 160) select_warp<5, 4, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 192) select_warp<6, 5, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 224) select_warp<7, 6, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 256) select_warp<8, 7, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
+        else if (R <= 288) select_warp<9, 8, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
         else select_warp<SEL_CAP, 9, V, cmp_t>(ABv, RS, LA, CBv, R, kk, pofs + pb, npos, pofs, emit);
     }
     const double wmax = warp_max(tmax);
