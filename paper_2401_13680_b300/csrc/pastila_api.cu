@@ -389,8 +389,9 @@ pastila_status resolve(const pastila_series* h, int32_t m, pastila_mparams mp, M
 
 // Tile width W and row groups NG: the smallest modelled cost per ED cell of the
 // eq. 9 matrix among the layouts that fit the shared memory and 512 threads.
-// Rows and seeds are paid on the Wb = W + R - 1 columns of a tile (the R - 1
-// halo columns are recomputed by the next tile), the selection on its W
+// Rows and seeds are paid on the NTc V columns of a tile (Wb = W + R - 1 rounded
+// up to whole warps of column threads; the R - 1 halo columns are recomputed by
+// the next tile), the selection on its W
 // positions; NG row groups add NG seed rows of ell products per column, and
 // fewer than 12 resident warps leave latency exposed.
 // Two CTAs of a layout share an SM when each takes at most half of its shared
@@ -435,7 +436,8 @@ void tile_candidates(size_t limit, const MParams& q, std::vector<TileCand>* out,
                 const bool pair = pair_layout(t, limit);
                 const double eff = pair ? std::min(1.0, 2.0 * t.NT / 512.0) : (t.NT >= 384 ? 1.0 : t.NT / 384.0);
                 const double cl = cs > 1 ? 1.1 : 1.0;  // partner writes and cluster barriers
-                out->push_back(TileCand{cl * ((double)Wb / W * rows + sel) / eff, W, ngw, t, pair});
+                // (every column thread computes its V columns: NTc V of them, Wb rounded up)
+                out->push_back(TileCand{cl * ((double)(NTc * V) / W * rows + sel) / eff, W, ngw, t, pair});
             }
         }
     }
