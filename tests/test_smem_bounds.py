@@ -294,3 +294,16 @@ def test_checker_catches_a_window_slide_at_a_run_start():
     _, bad = selection_reads(G, G["NT"], 0, Wp, slide_at_start=True)
     assert good[0] >= 0
     assert bad[0] < 0
+
+
+def test_cost_model_counts_the_columns_the_threads_compute():
+    """The layout model pays the rows on the NTc V columns the column threads
+    compute (W + R - 1 rounded up to whole warps), so its choice for every length
+    of the benchmark sweep computes few columns past W + R - 1."""
+    pastila.tune_clear()
+    for m in range(64, 513, 32):
+        ell = m // 2
+        lay = pastila.plan_layout(pastila.FP32, 100_000, m, SMEM, ell=ell)
+        G = geometry(pastila.FP32, m, ell, lay)
+        Wb = G["W"] + G["R"] - 1
+        assert G["NTc"] * V <= 1.1 * Wb, (m, lay, G["NTc"] * V, Wb)
